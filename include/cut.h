@@ -1,0 +1,216 @@
+/*
+ * cut.h -- C ABI of the compile-once CUT operation-graph engine (B300, sm_103a).
+ *
+ * The library evaluates the projected continuous-unitary-transformation flow
+ *     dH/ds = P[eta(H), H],   dX/ds = P[eta(H), X],   eta = [H_d, H_od]
+ * (paper Sec. 2.1, Eqs. coflow, block-generator, projected-flow) by applying
+ * a stored operation graph (Sec. 2.2, Eq. graph-actions):
+ *     xi_a(h)  = sum_{e in E_eta(a)} alpha_e (Dh)_{i_e} ((I-D)h)_{j_e}
+ *     F_k(h,x) = sum_{e in E_L(k)}   beta_e  xi_{a_e}(h) x_{j_e}
+ * Records are grouped by output (Sec. 2.2, last paragraph), stored once on
+ * disk (Sec. 2.3) and traversed forward and in reverse (Sec. 2.4).
+ *
+ * Conventions shared by every entry point
+ *   - Coefficients are real doubles.  For Pauli strings H = sum_k h_k P_k with
+ *     Hermitian P_k and eta = i sum_a xi_a G_a; for fermion monomials
+ *     H = sum_k h_k O_k and eta = sum_a xi_a G_a.  All stored factors are
+ *     exact integers (or rationals num/den), never rounded.
+ *   - A coefficient vector has n entries in the order of the registry the
+ *     graph was built from (cut_graph_labels); xi has n_g entries in the
+ *     order of the generator registry.
+ *   - "device" pointers are CUDA device memory on the graph's device,
+ *     owned by the caller; the library keeps no pointer after a call
+ *     returns, but kernels it queued on `stream` may still read or write
+ *     them until the stream reaches that point.  "host" pointers are
+ *     ordinary CPU memory, read or written before the call returns.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *   - No entry point throws; each returns a cut_status and, on failure,
+ *     leaves a message for cut_last_error() (thread-local).  Arguments are
+ *     validated before anything is queued: on CUT_ERR_INVALID_ARG nothing
+ *     was written.
+ */
+#ifndef CUT_H
+#define CUT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cut_graph cut_graph; /* opaque; owned by the library until cut_graph_free */
+typedef void *cut_stream_t;         /* cudaStream_t */
+
+typedef enum {
+    CUT_OK = 0,
+    CUT_ERR_INVALID_ARG = 1,
+    CUT_ERR_IO = 2,
+    CUT_ERR_FORMAT = 3,
+    CUT_ERR_CHECKSUM = 4,
+    CUT_ERR_OUT_OF_MEMORY = 5,
+    CUT_ERR_CUDA = 6,
+    CUT_ERR_NONFINITE = 7,
+    CUT_ERR_STEP_UNDERFLOW = 8,
+    CUT_ERR_MAX_STEPS = 9,
+    CUT_ERR_TIMEOUT = 10,
+    CUT_ERR_UNSUPPORTED = 11
+} cut_status;
+
+enum { CUT_ALG_PAULI = 0, CUT_ALG_FERMION = 1 };
+enum { CUT_RK4 = 0, CUT_DP45 = 1 };
+enum { CUT_FP64 = 0, CUT_FP32REC_FP64STATE = 1 };
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *cut_last_error(void);
+const char *cut_version(void);
+
+/* ------------------------------------------------------------------ */
+/* Compile (Sec. 2.2-2.3): registry -> two-traversal build -> bundle    */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int algebra;   /* CUT_ALG_PAULI or CUT_ALG_FERMION */
+    int nmodes;    /* qubits / spin-orbitals, 1..32 */
+    int max_rank;  /* fermion: highest rank of generator coordinates kept
+                      (terms of eta of higher rank cannot reach a registry of
+                      that rank); 0 = the registry's highest rank */
+    int threads;   /* host threads, 0 = all cores */
+} cut_build_opts;
+
+typedef struct {
+    int64_t n, n_g, R_g, R_L; /* registry size, generator size, records */
+    int n_codes;              /* distinct exact factors */
+    double seconds_count, seconds_write, seconds_total;
+    int64_t bytes_stored;     /* bundle size on disk */
+    int64_t peak_rss_bytes;   /* process peak resident set after the build */
+} cut_build_stats;
+
+/* Build the operation graph of the registry `labels` (host, n entries,
+ * distinct, every label number-conserving for fermions) and write the bundle
+ * to `path`.  Two deterministic traversals: the first counts records per
+ * output, the second writes each record into its final slot (Sec. 2.3).
+ * Records of one output are sorted by (input a, input b); the same input
+ * gives a bitwise-identical file.  `stats` (host) may be NULL.
+ * Errors: INVALID_ARG (bad options, duplicate or malformed label, an index
+ * beyond 2^24), IO (cannot write), OUT_OF_MEMORY. */
+cut_status cut_build(const cut_build_opts *opts, int64_t n, const uint64_t *labels,
+                     const char *path, cut_build_stats *stats);
+
+/* ------------------------------------------------------------------ */
+/* Load / query (Sec. 2.3: validated reload in any process)            */
+/* ------------------------------------------------------------------ */
+/* Read `path`, verify its SHA-256 and structure, upload to CUDA device
+ * `device`.  device == -1 gives a host-only handle (no CUDA call is made):
+ * query, labels, weights and records work, every traversal returns
+ * INVALID_ARG.  flags: reserved, pass 0.  Errors: IO, FORMAT (bad header or
+ * inconsistent arrays), CHECKSUM (payload digest mismatch), CUDA,
+ * OUT_OF_MEMORY. */
+cut_status cut_graph_load(const char *path, int device, unsigned flags, cut_graph **out);
+cut_status cut_graph_free(cut_graph *g);
+
+typedef struct {
+    int algebra, nmodes, max_rank, n_codes;
+    int64_t n, n_g, R_g, R_L;
+    uint8_t sha256[32];      /* digest of the bundle payload */
+    int64_t device_bytes;    /* graph bytes resident on the device */
+    int64_t record_bytes;    /* bytes of one stored record (both stages) */
+} cut_graph_desc;
+
+cut_status cut_graph_query(const cut_graph *g, cut_graph_desc *out);
+/* host out: labels[n], gen_labels[n_g], diag[n] (1 = block-diagonal
+ * coordinate, the mask D of Sec. 2.2); any pointer may be NULL. */
+cut_status cut_graph_labels(const cut_graph *g, uint64_t *labels, uint64_t *gen_labels, uint8_t *diag);
+/* host out: exact factor table, value of code c = num[c] / den[c]. */
+cut_status cut_graph_weights(const cut_graph *g, int32_t *num, int32_t *den);
+/* host out: the stored records of one stage (0 = generator, rows are
+ * generator coordinates a, inputs (i, j); 1 = commutator, rows are outputs
+ * k, inputs (a, j)).  row_ptr[rows+1], in1[R], in2[R], code[R]. */
+cut_status cut_graph_records(const cut_graph *g, int stage, int64_t *row_ptr, int32_t *in1,
+                             int32_t *in2, uint8_t *code);
+
+/* ------------------------------------------------------------------ */
+/* One right-hand side (Eq. graph-actions)                              */
+/* ------------------------------------------------------------------ */
+/* dh = P[eta(h), H], dx_o = P[eta(h), X_o] for o < n_obs.
+ * device in : h[n], x[n_obs][n] (NULL if n_obs == 0)
+ * device out: dh[n], dx[n_obs][n], xi_out[n_g] (optional, NULL = not kept)
+ * Runs asynchronously on `stream`.  Errors: INVALID_ARG, CUDA. */
+cut_status cut_rhs(const cut_graph *g, const double *h, int n_obs, const double *x, double *dh,
+                   double *dx, double *xi_out, cut_stream_t stream);
+
+/* Reverse traversal (Sec. 2.4): vector-Jacobian product of cut_rhs.
+ * With L = <w_h, dh> + sum_o <w_x[o], dx_o>:
+ *   h_bar = dL/dh (through eta and through X_0 = H),  x_bar[o] = dL/dx_o.
+ * device in : h[n], x[n_obs][n], w_h[n], w_x[n_obs][n]
+ * device out: h_bar[n], x_bar[n_obs][n]
+ * The transposed record orders are built on the host at the first call
+ * (synchronous), then kept with the graph.  Errors: INVALID_ARG, CUDA,
+ * OUT_OF_MEMORY. */
+cut_status cut_rhs_adjoint(const cut_graph *g, const double *h, int n_obs, const double *x,
+                           const double *w_h, const double *w_x, double *h_bar, double *x_bar,
+                           cut_stream_t stream);
+
+/* ------------------------------------------------------------------ */
+/* Flows                                                                */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int method;              /* CUT_RK4 (fixed ds) or CUT_DP45 (adaptive) */
+    double s0, s1;           /* flow interval */
+    double ds;               /* RK4 step; DP45 first trial step */
+    double rtol, atol;       /* DP45 tolerances */
+    int64_t max_steps;       /* DP45: limit on attempted steps (0 = 10^6) */
+    const double *replay_steps; /* host, DP45 only: if non-NULL, take exactly
+                                   these n_replay steps, all accepted */
+    int64_t n_replay;
+    double *record_steps;    /* host, optional: accepted step sizes out */
+    int64_t record_cap;      /* capacity of record_steps */
+} cut_flow_opts;
+
+typedef struct {
+    int64_t steps, rejects, rhs_calls;
+    double s_final;
+} cut_flow_stats;
+
+/* Integrate the stacked state [h; x_1..x_nobs] from s0 to s1.
+ * device in/out: h[n], x[n_obs][n].  host out: stats (may be NULL).
+ * RK4: nsteps = round((s1-s0)/ds) steps of exactly ds (the last one lands
+ * on s1).  DP45: Dormand-Prince 5(4), error ratio
+ * max_k |e_k| / (atol + rtol max(|y_k|, |y5_k|)), accept when <= 1,
+ * ds *= clamp(0.9 r^-1/5, 0.2, 5) (growth capped at 1 after a rejection).
+ * Synchronises `stream` before returning.
+ * Errors: INVALID_ARG, CUDA, NONFINITE (a non-finite state was produced),
+ * STEP_UNDERFLOW (ds fell below 1e-14 |s|), MAX_STEPS. */
+cut_status cut_flow(const cut_graph *g, double *h, int n_obs, double *x, const cut_flow_opts *opts,
+                    cut_flow_stats *stats, cut_stream_t stream);
+
+/* Gradient through a flow: the discrete adjoint of the RK steps that
+ * cut_flow took (pass its accepted steps in opts->replay_steps for DP45;
+ * RK4 recomputes its uniform steps).  Given y_bar = dJ/dy(s1) for the
+ * stacked final state, returns dJ/dy(s0).  The forward states are stored
+ * every `checkpoint_every` steps and recomputed segment by segment.
+ * device in : h0[n], x0[n_obs][n] (initial state, unchanged),
+ *             yb_h[n], yb_x[n_obs][n]
+ * device out: gh[n], gx[n_obs][n]
+ * Errors: INVALID_ARG, CUDA, OUT_OF_MEMORY. */
+cut_status cut_flow_vjp(const cut_graph *g, const double *h0, int n_obs, const double *x0,
+                        const cut_flow_opts *opts, int checkpoint_every, const double *yb_h,
+                        const double *yb_x, double *gh, double *gx, cut_stream_t stream);
+
+/* Many coefficient sets through one graph read per record (batched flows).
+ * device in/out: h[batch][n], x[batch][n_obs][n] (instance-major, as a user
+ * holds them; the library transposes internally).
+ * precision: CUT_FP64 or CUT_FP32REC_FP64STATE (records, products and sums
+ * in FP32; RK state and step control in FP64).
+ * Each instance has its own adaptive step sequence (DP45) and stops at s1.
+ * device out: steps_out[batch] accepted steps, status_out[batch] cut_status.
+ * host in: opts (replay/record fields ignored).  `tile` chooses the instance
+ * tile width (0 = autotuned).  Synchronises `stream` before returning.
+ * Errors: INVALID_ARG, CUDA, OUT_OF_MEMORY. */
+cut_status cut_flow_batched(const cut_graph *g, int batch, double *h, int n_obs, double *x,
+                            int precision, const cut_flow_opts *opts, int tile, int *steps_out,
+                            int *status_out, cut_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CUT_H */

@@ -1,0 +1,293 @@
+"""B300-native engine for compile-once CUT operation graphs (Python binding).
+
+This module only marshals arguments: every step of the graph build, the
+right-hand side, the adjoint and the flows runs inside libcut.so (C++ and
+sm_103a CUDA kernels behind the C ABI of include/cut.h).  PyTorch provides
+device memory and streams.  If libcut.so is missing the import of the
+library fails loudly; there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcut.so")
+
+ALG_PAULI, ALG_FERMION = 0, 1
+RK4, DP45 = 0, 1
+FP64, FP32REC_FP64STATE = 0, 1
+
+STATUS_NAMES = ["OK", "INVALID_ARG", "IO", "FORMAT", "CHECKSUM", "OUT_OF_MEMORY", "CUDA",
+                "NONFINITE", "STEP_UNDERFLOW", "MAX_STEPS", "TIMEOUT", "UNSUPPORTED"]
+
+
+class CutError(RuntimeError):
+    def __init__(self, status, msg):
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"CUT_ERR_{name}: {msg}")
+        self.status = status
+        self.name = name
+
+
+class BuildOpts(ctypes.Structure):
+    _fields_ = [("algebra", ctypes.c_int), ("nmodes", ctypes.c_int), ("max_rank", ctypes.c_int),
+                ("threads", ctypes.c_int)]
+
+
+class BuildStats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("n_g", ctypes.c_int64), ("R_g", ctypes.c_int64),
+                ("R_L", ctypes.c_int64), ("n_codes", ctypes.c_int),
+                ("seconds_count", ctypes.c_double), ("seconds_write", ctypes.c_double),
+                ("seconds_total", ctypes.c_double), ("bytes_stored", ctypes.c_int64),
+                ("peak_rss_bytes", ctypes.c_int64)]
+
+
+class GraphDesc(ctypes.Structure):
+    _fields_ = [("algebra", ctypes.c_int), ("nmodes", ctypes.c_int), ("max_rank", ctypes.c_int),
+                ("n_codes", ctypes.c_int), ("n", ctypes.c_int64), ("n_g", ctypes.c_int64),
+                ("R_g", ctypes.c_int64), ("R_L", ctypes.c_int64), ("sha256", ctypes.c_uint8 * 32),
+                ("device_bytes", ctypes.c_int64), ("record_bytes", ctypes.c_int64)]
+
+
+class FlowOpts(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int), ("s0", ctypes.c_double), ("s1", ctypes.c_double),
+                ("ds", ctypes.c_double), ("rtol", ctypes.c_double), ("atol", ctypes.c_double),
+                ("max_steps", ctypes.c_int64), ("replay_steps", ctypes.POINTER(ctypes.c_double)),
+                ("n_replay", ctypes.c_int64), ("record_steps", ctypes.POINTER(ctypes.c_double)),
+                ("record_cap", ctypes.c_int64)]
+
+
+class FlowStats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("rejects", ctypes.c_int64), ("rhs_calls", ctypes.c_int64),
+                ("s_final", ctypes.c_double)]
+
+
+_lib = None
+VP = ctypes.c_void_p
+
+
+def lib():
+    """Load libcut.so (built in-tree by build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libcut.so is not built ({LIB_PATH}); run paper_2609_14831_b300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    i, i64, st = ctypes.c_int, ctypes.c_int64, ctypes.c_int
+    sig = {
+        "cut_last_error": (ctypes.c_char_p, []),
+        "cut_version": (ctypes.c_char_p, []),
+        "cut_build": (st, [ctypes.POINTER(BuildOpts), i64, VP, ctypes.c_char_p, ctypes.POINTER(BuildStats)]),
+        "cut_graph_load": (st, [ctypes.c_char_p, i, ctypes.c_uint, ctypes.POINTER(VP)]),
+        "cut_graph_free": (st, [VP]),
+        "cut_graph_query": (st, [VP, ctypes.POINTER(GraphDesc)]),
+        "cut_graph_labels": (st, [VP, VP, VP, VP]),
+        "cut_graph_weights": (st, [VP, VP, VP]),
+        "cut_graph_records": (st, [VP, i, VP, VP, VP, VP]),
+        "cut_rhs": (st, [VP, VP, i, VP, VP, VP, VP, VP]),
+        "cut_rhs_adjoint": (st, [VP, VP, i, VP, VP, VP, VP, VP, VP]),
+        "cut_flow": (st, [VP, VP, i, VP, ctypes.POINTER(FlowOpts), ctypes.POINTER(FlowStats), VP]),
+        "cut_flow_vjp": (st, [VP, VP, i, VP, ctypes.POINTER(FlowOpts), i, VP, VP, VP, VP, VP]),
+        "cut_flow_batched": (st, [VP, i, VP, i, VP, i, ctypes.POINTER(FlowOpts), i, VP, VP, VP]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def check(status):
+    if status != 0:
+        raise CutError(status, lib().cut_last_error().decode())
+
+
+def build_graph(algebra, nmodes, labels, path, max_rank=0, threads=0):
+    """Compile the operation graph of a registry into a bundle file."""
+    labels = np.ascontiguousarray(labels, dtype=np.uint64)
+    opts = BuildOpts(int(algebra), int(nmodes), int(max_rank), int(threads))
+    st = BuildStats()
+    check(lib().cut_build(ctypes.byref(opts), len(labels), labels.ctypes.data, os.fsencode(path),
+                          ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in BuildStats._fields_}
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_f64(t, n, name, device):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor):
+        t = torch.as_tensor(np.asarray(t, dtype=np.float64))
+    t = t.to(device=device, dtype=torch.float64).contiguous()
+    if t.shape[-1] != n:
+        raise ValueError(f"{name}: last dimension {t.shape[-1]} != registry size {n}")
+    return t
+
+
+class Graph:
+    """A loaded operation graph resident on one CUDA device."""
+
+    def __init__(self, path, device=0):
+        self._h = VP()
+        check(lib().cut_graph_load(os.fsencode(path), int(device), 0, ctypes.byref(self._h)))
+        self.device_index = int(device)
+        d = GraphDesc()
+        check(lib().cut_graph_query(self._h, ctypes.byref(d)))
+        self.desc = {f: (bytes(getattr(d, f)).hex() if f == "sha256" else getattr(d, f))
+                     for f, _ in GraphDesc._fields_}
+        self.n, self.n_g = d.n, d.n_g
+        self.R_g, self.R_L = d.R_g, d.R_L
+
+    def close(self):
+        if self._h:
+            lib().cut_graph_free(self._h)
+            self._h = VP()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def device(self):
+        return _torch().device("cuda", self.device_index)
+
+    # ---- host-side views of the bundle
+    def labels(self):
+        lab = np.empty(self.n, dtype=np.uint64)
+        gl = np.empty(max(1, self.n_g), dtype=np.uint64)
+        dg = np.empty(self.n, dtype=np.uint8)
+        check(lib().cut_graph_labels(self._h, lab.ctypes.data, gl.ctypes.data, dg.ctypes.data))
+        return lab, gl[:self.n_g], dg.astype(bool)
+
+    def weights(self):
+        nc = self.desc["n_codes"]
+        num = np.empty(nc, dtype=np.int32)
+        den = np.empty(nc, dtype=np.int32)
+        check(lib().cut_graph_weights(self._h, num.ctypes.data, den.ctypes.data))
+        return num, den
+
+    def records(self, stage):
+        rows = self.n_g if stage == 0 else self.n
+        R = self.R_g if stage == 0 else self.R_L
+        rp = np.empty(rows + 1, dtype=np.int64)
+        a = np.empty(max(R, 1), dtype=np.int32)
+        b = np.empty(max(R, 1), dtype=np.int32)
+        c = np.empty(max(R, 1), dtype=np.uint8)
+        check(lib().cut_graph_records(self._h, int(stage), rp.ctypes.data, a.ctypes.data,
+                                      b.ctypes.data, c.ctypes.data))
+        return rp, a[:R], b[:R], c[:R]
+
+    # ---- device traversals
+    def rhs(self, h, xs=None, want_xi=False, stream=None):
+        """(dh, dxs[, xi]) = P[eta(h), H], P[eta(h), X_o]; tensors on this device."""
+        torch = _torch()
+        h = _dev_f64(h, self.n, "h", self.device)
+        n_obs = 0 if xs is None else len(xs)
+        x = _dev_f64(torch.stack([_dev_f64(v, self.n, "x", self.device) for v in xs]), self.n, "x",
+                     self.device) if n_obs else None
+        dh = torch.empty_like(h)
+        dx = torch.empty_like(x) if n_obs else None
+        xi = torch.empty(max(1, self.n_g), dtype=torch.float64, device=self.device) if want_xi else None
+        check(lib().cut_rhs(self._h, _ptr(h), n_obs, _ptr(x), _ptr(dh), _ptr(dx), _ptr(xi),
+                            _stream(stream)))
+        out = (dh, list(dx) if n_obs else [])
+        return out + (xi[:self.n_g],) if want_xi else out
+
+    def rhs_adjoint(self, h, xs, w_h, w_xs, stream=None):
+        """Vector-Jacobian product of rhs(): (h_bar, [x_bar_o])."""
+        torch = _torch()
+        h = _dev_f64(h, self.n, "h", self.device)
+        w_h = _dev_f64(w_h, self.n, "w_h", self.device)
+        n_obs = len(xs)
+        x = torch.stack([_dev_f64(v, self.n, "x", self.device) for v in xs]) if n_obs else None
+        wx = torch.stack([_dev_f64(v, self.n, "w_x", self.device) for v in w_xs]) if n_obs else None
+        hb = torch.empty_like(h)
+        xb = torch.empty_like(x) if n_obs else None
+        check(lib().cut_rhs_adjoint(self._h, _ptr(h), n_obs, _ptr(x), _ptr(w_h), _ptr(wx), _ptr(hb),
+                                    _ptr(xb), _stream(stream)))
+        return hb, (list(xb) if n_obs else [])
+
+    def _opts(self, method, s0, s1, ds, rtol, atol, max_steps, replay, record_cap):
+        o = FlowOpts()
+        o.method = RK4 if method == "rk4" else DP45
+        o.s0, o.s1, o.ds, o.rtol, o.atol = float(s0), float(s1), float(ds), float(rtol), float(atol)
+        o.max_steps = int(max_steps)
+        keep = []
+        if replay is not None:
+            r = np.ascontiguousarray(replay, dtype=np.float64)
+            keep.append(r)
+            o.replay_steps = r.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            o.n_replay = len(r)
+        rec = None
+        if record_cap:
+            rec = np.zeros(record_cap, dtype=np.float64)
+            o.record_steps = rec.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            o.record_cap = record_cap
+        return o, keep, rec
+
+    def flow(self, h, xs=(), method="rk4", s0=0.0, s1=10.0, ds=1e-3, rtol=1e-10, atol=0.0,
+             max_steps=0, replay=None, record_cap=1 << 20, stream=None):
+        """Integrate [h; x_1..] from s0 to s1.  Returns (h, xs, stats, accepted_steps)."""
+        torch = _torch()
+        h = _dev_f64(h, self.n, "h", self.device).clone()
+        n_obs = len(xs)
+        x = torch.stack([_dev_f64(v, self.n, "x", self.device) for v in xs]).clone() if n_obs else None
+        o, keep, rec = self._opts(method, s0, s1, ds, rtol, atol, max_steps, replay,
+                                  record_cap if method == "dp45" else 0)
+        st = FlowStats()
+        check(lib().cut_flow(self._h, _ptr(h), n_obs, _ptr(x), ctypes.byref(o), ctypes.byref(st),
+                             _stream(stream)))
+        stats = {f: getattr(st, f) for f, _ in FlowStats._fields_}
+        steps = rec[:min(st.steps, len(rec))].copy() if rec is not None else None
+        return h, (list(x) if n_obs else []), stats, steps
+
+    def flow_vjp(self, h0, xs0, yb_h, yb_xs, method="rk4", s0=0.0, s1=10.0, ds=1e-3, steps=None,
+                 checkpoint_every=64, stream=None):
+        """Discrete adjoint of a flow: dJ/d[h0; x0] given dJ/d[h; x] at s1."""
+        torch = _torch()
+        h0 = _dev_f64(h0, self.n, "h0", self.device)
+        yb_h = _dev_f64(yb_h, self.n, "yb_h", self.device)
+        n_obs = len(xs0)
+        x0 = torch.stack([_dev_f64(v, self.n, "x0", self.device) for v in xs0]) if n_obs else None
+        ybx = torch.stack([_dev_f64(v, self.n, "yb_x", self.device) for v in yb_xs]) if n_obs else None
+        gh = torch.empty_like(h0)
+        gx = torch.empty_like(x0) if n_obs else None
+        o, keep, _ = self._opts(method, s0, s1, ds, 1e-10, 0.0, 0, steps, 0)
+        check(lib().cut_flow_vjp(self._h, _ptr(h0), n_obs, _ptr(x0), ctypes.byref(o),
+                                 int(checkpoint_every), _ptr(yb_h), _ptr(ybx), _ptr(gh), _ptr(gx),
+                                 _stream(stream)))
+        return gh, (list(gx) if n_obs else [])
+
+    def flow_batched(self, H, Xs=None, precision="fp64", method="dp45", s0=0.0, s1=10.0, ds=1e-2,
+                     rtol=1e-10, atol=0.0, max_steps=0, tile=0, stream=None):
+        """Flows of many coefficient sets through one graph: H [B, n], Xs [B, n_obs, n]."""
+        torch = _torch()
+        H = _dev_f64(H, self.n, "H", self.device).clone()
+        B = H.shape[0]
+        n_obs = 0 if Xs is None else int(Xs.shape[1])
+        X = _dev_f64(Xs, self.n, "X", self.device).clone() if n_obs else None
+        steps = torch.zeros(B, dtype=torch.int32, device=self.device)
+        status = torch.zeros(B, dtype=torch.int32, device=self.device)
+        o, keep, _ = self._opts(method, s0, s1, ds, rtol, atol, max_steps, None, 0)
+        prec = FP64 if precision == "fp64" else FP32REC_FP64STATE
+        check(lib().cut_flow_batched(self._h, B, _ptr(H), n_obs, _ptr(X), prec, ctypes.byref(o),
+                                     int(tile), _ptr(steps), _ptr(status), _stream(stream)))
+        return H, X, steps, status

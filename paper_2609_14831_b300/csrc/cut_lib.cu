@@ -1,0 +1,806 @@
+// cut_lib.cu -- C ABI of the graph engine: load/upload, right-hand side,
+// adjoint, flows (paper Sec. 2.2-2.4).  See include/cut.h for the contract.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "bundle.h"
+#include "cut.h"
+#include "flow_kernels.cuh"
+#include "kernels.cuh"
+#include "status.h"
+
+namespace cut {
+
+static thread_local std::string g_err;
+cut_status set_error(cut_status s, const std::string &msg) {
+    g_err = msg;
+    return s;
+}
+cut_status set_ok() { return CUT_OK; }
+
+#define CUDA_TRY(expr)                                                                          \
+    do {                                                                                        \
+        cudaError_t _e = (expr);                                                                \
+        if (_e != cudaSuccess)                                                                  \
+            return set_error(_e == cudaErrorMemoryAllocation ? CUT_ERR_OUT_OF_MEMORY : CUT_ERR_CUDA, \
+                             std::string(#expr) + ": " + cudaGetErrorString(_e));               \
+    } while (0)
+
+struct DevCSR {
+    uint64_t *rp = nullptr;
+    uint2 *rec = nullptr;
+    int64_t rows = 0, R = 0;
+};
+
+}  // namespace cut
+
+struct cut_graph {
+    int device = 0;
+    cut::HostGraph host;
+    cut::DevCSR st[2];             // forward stages
+    cut::DevCSR tx, txi, th;       // transposed orders (adjoint), built lazily
+    bool have_T = false;
+    double *wtab = nullptr;        // exact factors as doubles
+    float *wtab32 = nullptr;
+    int64_t device_bytes = 0;
+    std::mutex mu;
+    ~cut_graph() {
+        if (device < 0) return;
+        int cur = 0;
+        cudaGetDevice(&cur);
+        cudaSetDevice(device);
+        for (auto *c : {&st[0], &st[1], &tx, &txi, &th}) {
+            cudaFree(c->rp);
+            cudaFree(c->rec);
+        }
+        cudaFree(wtab);
+        cudaFree(wtab32);
+        cudaSetDevice(cur);
+    }
+};
+
+namespace cut {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int d) {
+        cudaGetDevice(&prev);
+        if (prev != d) cudaSetDevice(d);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+static int grid_for_rows(int64_t rows) {
+    int64_t b = (rows + k::kWarpsPerBlock - 1) / k::kWarpsPerBlock;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, 148 * 16));
+}
+static int grid_for_len(int64_t len) {
+    int64_t b = (len + 255) / 256;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, 148 * 8));
+}
+
+static cut_status upload_csr(DevCSR &d, const std::vector<uint64_t> &rp, const std::vector<uint32_t> &rec,
+                             int64_t &bytes) {
+    d.rows = (int64_t)rp.size() - 1;
+    d.R = (int64_t)rec.size() / 2;
+    CUDA_TRY(cudaMalloc(&d.rp, rp.size() * 8));
+    CUDA_TRY(cudaMemcpy(d.rp, rp.data(), rp.size() * 8, cudaMemcpyHostToDevice));
+    size_t rb = std::max<size_t>(8, rec.size() * 4);
+    CUDA_TRY(cudaMalloc(&d.rec, rb));
+    if (!rec.empty()) CUDA_TRY(cudaMemcpy(d.rec, rec.data(), rec.size() * 4, cudaMemcpyHostToDevice));
+    bytes += (int64_t)(rp.size() * 8 + rec.size() * 4);
+    return CUT_OK;
+}
+
+// ----------------------------------------------------------------- RHS core
+// dx_o (o < nops) for operands x_o, given xi; operands processed 4 at a time.
+static void launch_comm(const cut_graph *g, const double *xi, int nops, const double *const *xs,
+                        double *const *dxs, cudaStream_t s, const int *done) {
+    const DevCSR &c = g->st[1];
+    int grid = grid_for_rows(c.rows);
+    int nc = (int)g->host.num.size();
+    for (int o0 = 0; o0 < nops; o0 += 4) {
+        int m = std::min(4, nops - o0);
+        switch (m) {
+#define CASE(M)                                                                                   \
+    case M: {                                                                                     \
+        k::Ops<M> ops;                                                                            \
+        for (int t = 0; t < M; t++) { ops.x[t] = xs[o0 + t]; ops.dx[t] = dxs[o0 + t]; }             \
+        k::comm_stage<M><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, g->wtab, nc, xi, ops, c.rows, done); \
+    } break;
+            CASE(1) CASE(2) CASE(3) CASE(4)
+#undef CASE
+        }
+    }
+}
+
+static void launch_gen(const cut_graph *g, const double *h, double *xi, cudaStream_t s, const int *done) {
+    const DevCSR &c = g->st[0];
+    k::gen_stage<<<grid_for_rows(c.rows), k::kBlock, 0, s>>>(c.rp, c.rec, g->wtab, (int)g->host.num.size(),
+                                                              h, xi, c.rows, done);
+}
+
+// f(Y) for the stacked state Y[nops][n] into DY[nops][n].
+static void stacked_rhs(const cut_graph *g, const double *Y, double *DY, int nops, double *xi,
+                        cudaStream_t s, const int *done) {
+    const int64_t n = g->host.n();
+    launch_gen(g, Y, xi, s, done);
+    const double *xs[64];
+    double *dxs[64];
+    for (int o = 0; o < nops; o++) { xs[o] = Y + o * n; dxs[o] = DY + o * n; }
+    launch_comm(g, xi, nops, xs, dxs, s, done);
+}
+
+}  // namespace cut
+
+using namespace cut;
+
+extern "C" {
+
+const char *cut_last_error(void) { return g_err.c_str(); }
+const char *cut_version(void) { return "cutgraph-b300 0.1 (sm_103a)"; }
+
+cut_status cut_graph_load(const char *path, int device, unsigned flags, cut_graph **out) {
+    if (!path || !out) return set_error(CUT_ERR_INVALID_ARG, "cut_graph_load: null argument");
+    if (flags != 0) return set_error(CUT_ERR_INVALID_ARG, "cut_graph_load: flags must be 0");
+    *out = nullptr;
+    if (device < -1) return set_error(CUT_ERR_INVALID_ARG, "cut_graph_load: bad device");
+    if (device >= 0) {
+        int ndev = 0;
+        CUDA_TRY(cudaGetDeviceCount(&ndev));
+        if (device >= ndev) return set_error(CUT_ERR_INVALID_ARG, "cut_graph_load: bad device");
+    }
+    std::unique_ptr<cut_graph> g(new cut_graph());
+    g->device = device;
+    std::string err;
+    int rc = read_bundle(path, g->host, &err);
+    if (rc != 0) return set_error((cut_status)rc, "cut_graph_load: " + err);
+    if (device == -1) {  // host-only handle: query, labels, weights, records
+        g->st[0].rows = g->host.n_g(); g->st[0].R = g->host.R(0);
+        g->st[1].rows = g->host.n(); g->st[1].R = g->host.R(1);
+        *out = g.release();
+        return set_ok();
+    }
+    DeviceGuard dg(device);
+    int64_t bytes = 0;
+    for (int s = 0; s < 2; s++) {
+        cut_status st = upload_csr(g->st[s], g->host.rp[s], g->host.rec[s], bytes);
+        if (st != CUT_OK) return st;
+    }
+    std::vector<double> w(g->host.num.size());
+    std::vector<float> w32(w.size());
+    for (size_t c = 0; c < w.size(); c++) {
+        w[c] = (double)g->host.num[c] / (double)g->host.den[c];
+        w32[c] = (float)w[c];
+    }
+    CUDA_TRY(cudaMalloc(&g->wtab, w.size() * 8));
+    CUDA_TRY(cudaMemcpy(g->wtab, w.data(), w.size() * 8, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMalloc(&g->wtab32, w.size() * 4));
+    CUDA_TRY(cudaMemcpy(g->wtab32, w32.data(), w.size() * 4, cudaMemcpyHostToDevice));
+    g->device_bytes = bytes + (int64_t)w.size() * 12;
+    *out = g.release();
+    return set_ok();
+}
+
+cut_status cut_graph_free(cut_graph *g) {
+    delete g;
+    return set_ok();
+}
+
+cut_status cut_graph_query(const cut_graph *g, cut_graph_desc *out) {
+    if (!g || !out) return set_error(CUT_ERR_INVALID_ARG, "cut_graph_query: null argument");
+    memset(out, 0, sizeof(*out));
+    out->algebra = g->host.algebra;
+    out->nmodes = g->host.nmodes;
+    out->max_rank = g->host.max_rank;
+    out->n_codes = (int)g->host.num.size();
+    out->n = g->host.n();
+    out->n_g = g->host.n_g();
+    out->R_g = g->st[0].R;
+    out->R_L = g->st[1].R;
+    memcpy(out->sha256, g->host.sha, 32);
+    out->device_bytes = g->device_bytes;
+    out->record_bytes = 8;
+    return set_ok();
+}
+
+cut_status cut_graph_labels(const cut_graph *g, uint64_t *labels, uint64_t *gen_labels, uint8_t *diag) {
+    if (!g) return set_error(CUT_ERR_INVALID_ARG, "cut_graph_labels: null graph");
+    if (labels) memcpy(labels, g->host.labels.data(), g->host.labels.size() * 8);
+    if (gen_labels) memcpy(gen_labels, g->host.gen_labels.data(), g->host.gen_labels.size() * 8);
+    if (diag) memcpy(diag, g->host.diag.data(), g->host.diag.size());
+    return set_ok();
+}
+
+cut_status cut_graph_weights(const cut_graph *g, int32_t *num, int32_t *den) {
+    if (!g) return set_error(CUT_ERR_INVALID_ARG, "cut_graph_weights: null graph");
+    if (num) memcpy(num, g->host.num.data(), g->host.num.size() * 4);
+    if (den) memcpy(den, g->host.den.data(), g->host.den.size() * 4);
+    return set_ok();
+}
+
+cut_status cut_graph_records(const cut_graph *g, int stage, int64_t *row_ptr, int32_t *in1, int32_t *in2,
+                             uint8_t *code) {
+    if (!g || stage < 0 || stage > 1) return set_error(CUT_ERR_INVALID_ARG, "cut_graph_records: bad argument");
+    const auto &rp = g->host.rp[stage];
+    const auto &rc = g->host.rec[stage];
+    if (rc.size() / 2 != (size_t)g->st[stage].R)
+        return set_error(CUT_ERR_UNSUPPORTED, "cut_graph_records: host copy of the records was released");
+    if (row_ptr) for (size_t r = 0; r < rp.size(); r++) row_ptr[r] = (int64_t)rp[r];
+    for (size_t e = 0; e < rc.size() / 2; e++) {
+        if (in1) in1[e] = (int32_t)(rc[2 * e] & kIndexMask);
+        if (in2) in2[e] = (int32_t)rc[2 * e + 1];
+        if (code) code[e] = (uint8_t)(rc[2 * e] >> kIndexBits);
+    }
+    return set_ok();
+}
+
+cut_status cut_rhs(const cut_graph *g, const double *h, int n_obs, const double *x, double *dh, double *dx,
+                   double *xi_out, cut_stream_t stream) {
+    if (!g || g->device < 0 || !h || !dh || n_obs < 0 || n_obs > 63 || (n_obs > 0 && (!x || !dx)))
+        return set_error(CUT_ERR_INVALID_ARG, "cut_rhs: bad argument");
+    DeviceGuard dg(g->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = g->host.n();
+    double *xi = xi_out;
+    if (!xi) CUDA_TRY(cudaMallocAsync(&xi, std::max<int64_t>(1, g->host.n_g()) * 8, s));
+    launch_gen(g, h, xi, s, nullptr);
+    const double *xs[64];
+    double *dxs[64];
+    xs[0] = h;
+    dxs[0] = dh;
+    for (int o = 0; o < n_obs; o++) { xs[o + 1] = x + o * n; dxs[o + 1] = dx + o * n; }
+    launch_comm(g, xi, n_obs + 1, xs, dxs, s, nullptr);
+    CUDA_TRY(cudaGetLastError());
+    if (!xi_out) CUDA_TRY(cudaFreeAsync(xi, s));
+    return set_ok();
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------------------- adjoint
+namespace cut {
+
+// Counting sort of records into a new CSR keyed by `row_of(e)`, payload
+// (code | first(e), second(e)).
+template <class RowF, class AF, class BF>
+static void transpose(const std::vector<uint64_t> &rp, const std::vector<uint32_t> &rec, int64_t rows_out,
+                      RowF row_of, AF first, BF second, std::vector<uint64_t> &orp,
+                      std::vector<uint32_t> &orec) {
+    const int64_t rows_in = (int64_t)rp.size() - 1;
+    orp.assign(rows_out + 1, 0);
+    for (int64_t r = 0; r < rows_in; r++)
+        for (uint64_t e = rp[r]; e < rp[r + 1]; e++) orp[row_of(r, rec[2 * e], rec[2 * e + 1]) + 1]++;
+    for (int64_t r = 0; r < rows_out; r++) orp[r + 1] += orp[r];
+    std::vector<uint64_t> cur(orp.begin(), orp.end() - 1);
+    orec.assign(rec.size(), 0);
+    for (int64_t r = 0; r < rows_in; r++)
+        for (uint64_t e = rp[r]; e < rp[r + 1]; e++) {
+            uint32_t w0 = rec[2 * e], w1 = rec[2 * e + 1];
+            uint64_t p = cur[row_of(r, w0, w1)]++;
+            orec[2 * p] = ((w0 >> kIndexBits) << kIndexBits) | first(r, w0, w1);
+            orec[2 * p + 1] = second(r, w0, w1);
+        }
+}
+
+static cut_status ensure_transposes(cut_graph *g) {
+    std::lock_guard<std::mutex> lk(g->mu);
+    if (g->have_T) return CUT_OK;
+    const auto &H = g->host;
+    const int64_t n = H.n(), ng = H.n_g();
+    std::vector<uint64_t> rp;
+    std::vector<uint32_t> rc;
+    int64_t bytes = 0;
+    // rows j, entries (code|a, k)
+    transpose(H.rp[1], H.rec[1], n, [](int64_t, uint32_t, uint32_t w1) { return (int64_t)w1; },
+              [](int64_t, uint32_t w0, uint32_t) { return w0 & kIndexMask; },
+              [](int64_t k, uint32_t, uint32_t) { return (uint32_t)k; }, rp, rc);
+    cut_status st = upload_csr(g->tx, rp, rc, bytes);
+    if (st != CUT_OK) return st;
+    // rows a, entries (code|k, j)
+    transpose(H.rp[1], H.rec[1], ng, [](int64_t, uint32_t w0, uint32_t) { return (int64_t)(w0 & kIndexMask); },
+              [](int64_t k, uint32_t, uint32_t) { return (uint32_t)k; },
+              [](int64_t, uint32_t, uint32_t w1) { return w1; }, rp, rc);
+    st = upload_csr(g->txi, rp, rc, bytes);
+    if (st != CUT_OK) return st;
+    // rows r (both inputs of a generator record), entries (code|a, partner)
+    {
+        std::vector<uint64_t> orp(n + 1, 0);
+        const auto &grp = H.rp[0];
+        const auto &grc = H.rec[0];
+        for (int64_t a = 0; a < ng; a++)
+            for (uint64_t e = grp[a]; e < grp[a + 1]; e++) {
+                orp[(grc[2 * e] & kIndexMask) + 1]++;
+                orp[grc[2 * e + 1] + 1]++;
+            }
+        for (int64_t r = 0; r < n; r++) orp[r + 1] += orp[r];
+        std::vector<uint64_t> cur(orp.begin(), orp.end() - 1);
+        std::vector<uint32_t> orc(2 * orp[n]);
+        for (int64_t a = 0; a < ng; a++)
+            for (uint64_t e = grp[a]; e < grp[a + 1]; e++) {
+                uint32_t w0 = grc[2 * e], w1 = grc[2 * e + 1];
+                uint32_t code = w0 >> kIndexBits, i = w0 & kIndexMask, j = w1;
+                uint64_t p = cur[i]++;
+                orc[2 * p] = (code << kIndexBits) | (uint32_t)a;
+                orc[2 * p + 1] = j;
+                p = cur[j]++;
+                orc[2 * p] = (code << kIndexBits) | (uint32_t)a;
+                orc[2 * p + 1] = i;
+            }
+        st = upload_csr(g->th, orp, orc, bytes);
+        if (st != CUT_OK) return st;
+    }
+    g->device_bytes += bytes;
+    g->have_T = true;
+    return CUT_OK;
+}
+
+// VJP of the stacked RHS at Y with cotangent W: YB = J(Y)^T W.  xi, xib:
+// scratch [n_g]; xbar0: scratch [n].
+static void stacked_vjp(const cut_graph *g, const double *Y, const double *W, double *YB, int nops, double *xi,
+                        double *xib, double *xbar0, cudaStream_t s) {
+    const int64_t n = g->host.n(), ng = g->host.n_g();
+    const int nc = (int)g->host.num.size();
+    launch_gen(g, Y, xi, s, nullptr);
+    // x_bar_o = L(h)^T w_o ; operand 0's goes to scratch, then into h_bar
+    for (int o0 = 0; o0 < nops; o0 += 4) {
+        int m = std::min(4, nops - o0);
+        switch (m) {
+#define CASE(M)                                                                              \
+    case M: {                                                                                \
+        k::Ops<M> ops;                                                                       \
+        for (int t = 0; t < M; t++) {                                                        \
+            ops.x[t] = W + (o0 + t) * n;                                                     \
+            ops.dx[t] = (o0 + t == 0) ? xbar0 : YB + (o0 + t) * n;                           \
+        }                                                                                    \
+        k::commT_x<M><<<grid_for_rows(n), k::kBlock, 0, s>>>(g->tx.rp, g->tx.rec, g->wtab, nc, xi, ops, n); \
+    } break;
+            CASE(1) CASE(2) CASE(3) CASE(4)
+#undef CASE
+        }
+    }
+    for (int o0 = 0; o0 < nops; o0 += 4) {
+        int m = std::min(4, nops - o0);
+        switch (m) {
+#define CASE(M)                                                                              \
+    case M: {                                                                                \
+        k::Pairs<M> pr;                                                                      \
+        for (int t = 0; t < M; t++) { pr.x[t] = Y + (o0 + t) * n; pr.w[t] = W + (o0 + t) * n; } \
+        k::commT_xi<M><<<grid_for_rows(ng), k::kBlock, 0, s>>>(g->txi.rp, g->txi.rec, g->wtab, nc, pr, xib, ng, o0 > 0); \
+    } break;
+            CASE(1) CASE(2) CASE(3) CASE(4)
+#undef CASE
+        }
+    }
+    k::genT<<<grid_for_rows(n), k::kBlock, 0, s>>>(g->th.rp, g->th.rec, g->wtab, nc, xib, Y, xbar0, YB, n);
+}
+
+}  // namespace cut
+
+extern "C" cut_status cut_rhs_adjoint(const cut_graph *g, const double *h, int n_obs, const double *x,
+                                      const double *w_h, const double *w_x, double *h_bar, double *x_bar,
+                                      cut_stream_t stream) {
+    if (!g || g->device < 0 || !h || !w_h || !h_bar || n_obs < 0 || n_obs > 63 || (n_obs > 0 && (!x || !w_x || !x_bar)))
+        return set_error(CUT_ERR_INVALID_ARG, "cut_rhs_adjoint: bad argument");
+    DeviceGuard dg(g->device);
+    cut_status st = ensure_transposes(const_cast<cut_graph *>(g));
+    if (st != CUT_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = g->host.n(), ng = std::max<int64_t>(1, g->host.n_g());
+    const int nops = n_obs + 1;
+    // stacked copies so that one code path serves single calls and flows
+    double *buf = nullptr;
+    const size_t L = (size_t)nops * n;
+    CUDA_TRY(cudaMallocAsync(&buf, (3 * L + 2 * ng + n) * 8, s));
+    double *Y = buf, *W = buf + L, *YB = buf + 2 * L, *xi = buf + 3 * L, *xib = xi + ng, *xb0 = xib + ng;
+    CUDA_TRY(cudaMemcpyAsync(Y, h, n * 8, cudaMemcpyDeviceToDevice, s));
+    if (n_obs) CUDA_TRY(cudaMemcpyAsync(Y + n, x, (size_t)n_obs * n * 8, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(W, w_h, n * 8, cudaMemcpyDeviceToDevice, s));
+    if (n_obs) CUDA_TRY(cudaMemcpyAsync(W + n, w_x, (size_t)n_obs * n * 8, cudaMemcpyDeviceToDevice, s));
+    stacked_vjp(g, Y, W, YB, nops, xi, xib, xb0, s);
+    CUDA_TRY(cudaMemcpyAsync(h_bar, YB, n * 8, cudaMemcpyDeviceToDevice, s));
+    if (n_obs) CUDA_TRY(cudaMemcpyAsync(x_bar, YB + n, (size_t)n_obs * n * 8, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaFreeAsync(buf, s));
+    return set_ok();
+}
+
+// ----------------------------------------------------------------- flows
+namespace cut {
+
+static const double RK4_A[4][4] = {{0, 0, 0, 0}, {0.5, 0, 0, 0}, {0, 0.5, 0, 0}, {0, 0, 1.0, 0}};
+static const double RK4_B[4] = {1.0 / 6, 1.0 / 3, 1.0 / 3, 1.0 / 6};
+// Dormand & Prince (1980) 5(4) tableau
+static const double DP_A[7][6] = {
+    {0, 0, 0, 0, 0, 0},
+    {1.0 / 5, 0, 0, 0, 0, 0},
+    {3.0 / 40, 9.0 / 40, 0, 0, 0, 0},
+    {44.0 / 45, -56.0 / 15, 32.0 / 9, 0, 0, 0},
+    {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729, 0, 0},
+    {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656, 0},
+    {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84}};
+static const double DP_B[7] = {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84, 0};
+static const double DP_BS[7] = {5179.0 / 57600, 0, 7571.0 / 16695, 393.0 / 640, -92097.0 / 339200, 187.0 / 2100,
+                                1.0 / 40};
+
+struct FlowWork {
+    double *Y, *U, *Y5, *K[7], *xi;
+    k::Control *ctl;
+    double *replay, *record;
+    int *flag;
+    void *base = nullptr;
+};
+
+static cut_status alloc_work(FlowWork &w, int64_t L, int64_t ng, int64_t nrec, cudaStream_t s) {
+    size_t doubles = (size_t)(3 + 7) * L + ng + 2 * nrec + 64;
+    size_t bytes = doubles * 8 + sizeof(k::Control) + 64;
+    CUDA_TRY(cudaMallocAsync(&w.base, bytes, s));
+    double *p = (double *)w.base;
+    w.Y = p; p += L;
+    w.U = p; p += L;
+    w.Y5 = p; p += L;
+    for (int i = 0; i < 7; i++) { w.K[i] = p; p += L; }
+    w.xi = p; p += std::max<int64_t>(1, ng);
+    w.replay = p; p += nrec;
+    w.record = p; p += nrec;
+    w.flag = (int *)p; p += 8;
+    w.ctl = (k::Control *)p;
+    return CUT_OK;
+}
+
+// U = Y + ds sum_j A[i][j] K_j
+static void stage_input(const FlowWork &w, const double *A, int i, int64_t L, const double *dsp, double dsc,
+                        cudaStream_t s, const int *done, double *out) {
+    k::Combine cb;
+    cb.base = w.Y;
+    cb.nk = 0;
+    for (int j = 0; j < i; j++)
+        if (A[j] != 0.0) { cb.K[cb.nk] = w.K[j]; cb.c[cb.nk] = A[j]; cb.nk++; }
+    k::rk_combine<<<grid_for_len(L), 256, 0, s>>>(cb, out, L, dsp, dsc, done);
+}
+
+// One RK4 step on w.Y (fixed ds), K/U scratch.
+static void rk4_step(const cut_graph *g, FlowWork &w, int nops, double ds, cudaStream_t s) {
+    const int64_t L = (int64_t)nops * g->host.n();
+    for (int i = 0; i < 4; i++) {
+        const double *in = w.Y;
+        if (i > 0) {
+            stage_input(w, RK4_A[i], i, L, nullptr, ds, s, nullptr, w.U);
+            in = w.U;
+        }
+        stacked_rhs(g, in, w.K[i], nops, w.xi, s, nullptr);
+    }
+    k::Combine cb;
+    cb.base = w.Y;
+    cb.nk = 4;
+    for (int j = 0; j < 4; j++) { cb.K[j] = w.K[j]; cb.c[j] = RK4_B[j]; }
+    k::rk_combine<<<grid_for_len(L), 256, 0, s>>>(cb, w.Y, L, nullptr, ds, nullptr);
+}
+
+// One Dormand-Prince attempt under device control (w.K[0] holds f(Y)).
+static void dp_attempt(const cut_graph *g, FlowWork &w, int nops, cudaStream_t s, bool replay,
+                       int64_t record_cap) {
+    const int64_t L = (int64_t)nops * g->host.n();
+    const int *done = &w.ctl->done;
+    const double *dsp = &w.ctl->ds;
+    for (int i = 1; i < 6; i++) {
+        stage_input(w, DP_A[i], i, L, dsp, 0.0, s, done, w.U);
+        stacked_rhs(g, w.U, w.K[i], nops, w.xi, s, done);
+    }
+    stage_input(w, DP_A[6], 6, L, dsp, 0.0, s, done, w.Y5);
+    stacked_rhs(g, w.Y5, w.K[6], nops, w.xi, s, done);
+    if (!replay) {
+        k::ErrTerms et;
+        for (int i = 0; i < 7; i++) { et.K[i] = w.K[i]; et.e[i] = DP_B[i] - DP_BS[i]; }
+        k::dp_error<<<grid_for_len(L), 256, 0, s>>>(et, w.Y, w.Y5, L, w.ctl);
+    }
+    k::dp_control<<<1, 1, 0, s>>>(w.ctl, replay ? w.replay : nullptr, w.record, record_cap);
+    k::dp_accept<<<grid_for_len(L), 256, 0, s>>>(w.ctl, w.Y, w.Y5, w.K[0], w.K[6], L);
+}
+
+struct StreamPair {
+    cudaStream_t user, work;
+    cudaEvent_t ev;
+};
+
+static cut_status begin_work(StreamPair &sp) {
+    CUDA_TRY(cudaStreamCreateWithFlags(&sp.work, cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreateWithFlags(&sp.ev, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventRecord(sp.ev, sp.user));
+    CUDA_TRY(cudaStreamWaitEvent(sp.work, sp.ev, 0));
+    return CUT_OK;
+}
+static void end_work(StreamPair &sp) {
+    cudaEventRecord(sp.ev, sp.work);
+    cudaStreamWaitEvent(sp.user, sp.ev, 0);
+    cudaStreamDestroy(sp.work);
+    cudaEventDestroy(sp.ev);
+}
+
+// Capture `body` into a graph once and replay it `times` times.
+template <class F>
+static cut_status replay_graph(cudaStream_t s, int64_t times, F body) {
+    if (times <= 0) return CUT_OK;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    body();
+    CUDA_TRY(cudaStreamEndCapture(s, &graph));
+    cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CUDA_TRY(e);
+    for (int64_t t = 0; t < times; t++) {
+        e = cudaGraphLaunch(exec, s);
+        if (e != cudaSuccess) break;
+    }
+    cudaGraphExecDestroy(exec);
+    CUDA_TRY(e);
+    return CUT_OK;
+}
+
+static cut_status check_opts(const cut_flow_opts *o) {
+    if (!o) return set_error(CUT_ERR_INVALID_ARG, "flow: null options");
+    if (o->method != CUT_RK4 && o->method != CUT_DP45) return set_error(CUT_ERR_INVALID_ARG, "flow: unknown method");
+    if (!(o->s1 >= o->s0) || !std::isfinite(o->s0) || !std::isfinite(o->s1))
+        return set_error(CUT_ERR_INVALID_ARG, "flow: need finite s1 >= s0");
+    if (o->method == CUT_RK4 && !(o->ds > 0)) return set_error(CUT_ERR_INVALID_ARG, "flow: RK4 needs ds > 0");
+    if (o->method == CUT_DP45 && !o->replay_steps && (!(o->ds > 0) || !(o->rtol > 0) || o->atol < 0))
+        return set_error(CUT_ERR_INVALID_ARG, "flow: DP45 needs ds > 0, rtol > 0, atol >= 0");
+    if (o->replay_steps && o->n_replay <= 0) return set_error(CUT_ERR_INVALID_ARG, "flow: empty replay list");
+    return CUT_OK;
+}
+
+static int64_t rk4_nsteps(const cut_flow_opts *o, double *ds_eff) {
+    int64_t N = (int64_t)std::llround((o->s1 - o->s0) / o->ds);
+    if (N < 1) N = (o->s1 > o->s0) ? 1 : 0;
+    *ds_eff = N > 0 ? (o->s1 - o->s0) / (double)N : 0.0;
+    return N;
+}
+
+}  // namespace cut
+
+extern "C" cut_status cut_flow(const cut_graph *g, double *h, int n_obs, double *x, const cut_flow_opts *o,
+                               cut_flow_stats *stats, cut_stream_t stream) {
+    if (!g || g->device < 0 || !h || n_obs < 0 || n_obs > 63 || (n_obs > 0 && !x)) return set_error(CUT_ERR_INVALID_ARG, "cut_flow: bad argument");
+    cut_status st = check_opts(o);
+    if (st != CUT_OK) return st;
+    DeviceGuard dg(g->device);
+    const int64_t n = g->host.n(), ng = g->host.n_g();
+    const int nops = n_obs + 1;
+    const int64_t L = (int64_t)nops * n;
+    StreamPair sp{(cudaStream_t)stream, nullptr, nullptr};
+    st = begin_work(sp);
+    if (st != CUT_OK) return st;
+    cudaStream_t s = sp.work;
+    const bool dp = o->method == CUT_DP45;
+    const bool replay = dp && o->replay_steps;
+    const int64_t max_steps = o->max_steps > 0 ? o->max_steps : 1000000;
+    const int64_t nrec = dp ? (replay ? o->n_replay : std::min<int64_t>(max_steps, 1 << 22)) : 1;
+    FlowWork w;
+    st = alloc_work(w, L, ng, nrec, s);
+    if (st != CUT_OK) { end_work(sp); return st; }
+    auto fail = [&](cut_status e) { cudaFreeAsync(w.base, s); end_work(sp); return e; };
+    cudaMemcpyAsync(w.Y, h, n * 8, cudaMemcpyDeviceToDevice, s);
+    if (n_obs) cudaMemcpyAsync(w.Y + n, x, (size_t)n_obs * n * 8, cudaMemcpyDeviceToDevice, s);
+    cudaMemsetAsync(w.flag, 0, 8, s);
+    cut_flow_stats out;
+    memset(&out, 0, sizeof(out));
+    int status = CUT_OK;
+    if (!dp) {
+        double ds;
+        int64_t N = rk4_nsteps(o, &ds);
+        const int64_t chunk = 32;
+        st = replay_graph(s, N / chunk, [&]() { for (int t = 0; t < chunk; t++) rk4_step(g, w, nops, ds, s); });
+        if (st != CUT_OK) return fail(st);
+        for (int64_t t = 0; t < N % chunk; t++) rk4_step(g, w, nops, ds, s);
+        k::scan_nonfinite<<<grid_for_len(L), 256, 0, s>>>(w.Y, L, w.flag);
+        int flag = 0;
+        cudaMemcpyAsync(&flag, w.flag, 4, cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return fail(set_error(CUT_ERR_CUDA, std::string("cut_flow: ") + cudaGetErrorString(e)));
+        if (flag) status = CUT_ERR_NONFINITE;
+        out.steps = N;
+        out.rhs_calls = 4 * N;
+        out.s_final = o->s0 + ds * (double)N;
+    } else {
+        k::Control c;
+        memset(&c, 0, sizeof(c));
+        c.s = o->s0;
+        c.s1 = o->s1;
+        c.rtol = o->rtol;
+        c.atol = o->atol;
+        c.max_steps = max_steps;
+        c.n_replay = replay ? o->n_replay : 0;
+        c.ds = replay ? o->replay_steps[0] : std::min(o->ds, o->s1 - o->s0);
+        c.done = (replay || o->s1 > o->s0) ? 0 : 1;
+        cudaMemcpyAsync(w.ctl, &c, sizeof(c), cudaMemcpyHostToDevice, s);
+        if (replay) cudaMemcpyAsync(w.replay, o->replay_steps, o->n_replay * 8, cudaMemcpyHostToDevice, s);
+        stacked_rhs(g, w.Y, w.K[0], nops, w.xi, s, nullptr);
+        const int64_t chunk = 16;
+        cudaGraph_t graph;
+        cudaGraphExec_t exec;
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return fail(set_error(CUT_ERR_CUDA, "cut_flow: capture failed"));
+        for (int t = 0; t < chunk; t++) dp_attempt(g, w, nops, s, replay, nrec);
+        e = cudaStreamEndCapture(s, &graph);
+        if (e != cudaSuccess) return fail(set_error(CUT_ERR_CUDA, "cut_flow: capture failed"));
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return fail(set_error(CUT_ERR_CUDA, "cut_flow: graph instantiate failed"));
+        k::Control hc;
+        int64_t attempts_cap = replay ? o->n_replay : max_steps;
+        for (int64_t launched = 0;; launched += chunk) {
+            cudaGraphLaunch(exec, s);
+            cudaMemcpyAsync(&hc, w.ctl, sizeof(hc), cudaMemcpyDeviceToHost, s);
+            e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess || hc.done || launched > attempts_cap + chunk) break;
+        }
+        cudaGraphExecDestroy(exec);
+        if (e != cudaSuccess) return fail(set_error(CUT_ERR_CUDA, std::string("cut_flow: ") + cudaGetErrorString(e)));
+        status = hc.status;
+        if (!hc.done && status == CUT_OK) status = CUT_ERR_MAX_STEPS;
+        out.steps = hc.steps;
+        out.rejects = hc.rejects;
+        out.rhs_calls = 1 + 6 * hc.attempts;
+        out.s_final = hc.s;
+        if (o->record_steps && o->record_cap > 0) {
+            int64_t m = std::min<int64_t>(std::min<int64_t>(hc.steps, o->record_cap), nrec);
+            cudaMemcpyAsync(o->record_steps, w.record, m * 8, cudaMemcpyDeviceToHost, s);
+        }
+    }
+    cudaMemcpyAsync(h, w.Y, n * 8, cudaMemcpyDeviceToDevice, s);
+    if (n_obs) cudaMemcpyAsync(x, w.Y + n, (size_t)n_obs * n * 8, cudaMemcpyDeviceToDevice, s);
+    cudaFreeAsync(w.base, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    end_work(sp);
+    if (e != cudaSuccess) return set_error(CUT_ERR_CUDA, std::string("cut_flow: ") + cudaGetErrorString(e));
+    if (stats) *stats = out;
+    if (status != CUT_OK) {
+        static const char *names[] = {"", "", "", "", "", "", "", "non-finite state", "step size underflow",
+                                      "step limit reached"};
+        return set_error((cut_status)status, std::string("cut_flow: ") + (status < 10 ? names[status] : "error"));
+    }
+    return set_ok();
+}
+
+// ----------------------------------------------------------------- flow VJP
+extern "C" cut_status cut_flow_vjp(const cut_graph *g, const double *h0, int n_obs, const double *x0,
+                                   const cut_flow_opts *o, int checkpoint_every, const double *yb_h,
+                                   const double *yb_x, double *gh, double *gx, cut_stream_t stream) {
+    if (!g || g->device < 0 || !h0 || !yb_h || !gh || n_obs < 0 || n_obs > 63 || (n_obs > 0 && (!x0 || !yb_x || !gx)) ||
+        checkpoint_every < 1)
+        return set_error(CUT_ERR_INVALID_ARG, "cut_flow_vjp: bad argument");
+    cut_status st = check_opts(o);
+    if (st != CUT_OK) return st;
+    if (o->method == CUT_DP45 && !o->replay_steps)
+        return set_error(CUT_ERR_INVALID_ARG, "cut_flow_vjp: DP45 needs the accepted steps in replay_steps");
+    DeviceGuard dg(g->device);
+    st = ensure_transposes(const_cast<cut_graph *>(g));
+    if (st != CUT_OK) return st;
+    const int64_t n = g->host.n(), ng = std::max<int64_t>(1, g->host.n_g());
+    const int nops = n_obs + 1;
+    const int64_t L = (int64_t)nops * n;
+    // step list
+    std::vector<double> steps;
+    const double(*A)[6] = nullptr;
+    const double *B = nullptr;
+    int S = 0;
+    double rkA[4][6] = {{0}};
+    if (o->method == CUT_RK4) {
+        double ds;
+        int64_t N = rk4_nsteps(o, &ds);
+        steps.assign(N, ds);
+        for (int i = 0; i < 4; i++)
+            for (int j = 0; j < 4; j++) rkA[i][j] = RK4_A[i][j];
+        A = rkA;
+        B = RK4_B;
+        S = 4;
+    } else {
+        steps.assign(o->replay_steps, o->replay_steps + o->n_replay);
+        A = DP_A;
+        B = DP_B;
+        S = 6;
+    }
+    const int64_t N = (int64_t)steps.size();
+    const int64_t C = checkpoint_every;
+    const int64_t ncp = (N + C - 1) / C + 1;
+    StreamPair sp{(cudaStream_t)stream, nullptr, nullptr};
+    st = begin_work(sp);
+    if (st != CUT_OK) return st;
+    cudaStream_t s = sp.work;
+    // memory: checkpoints [ncp][L], segment states [C+1][L], stages U[S][L],
+    // K[S][L], yb, ub, kb[S][L], xi, xib, xb0
+    double *buf = nullptr;
+    size_t tot = (size_t)(ncp + (C + 1) + 3 * S + 3) * L + 2 * ng + n;
+    cudaError_t e = cudaMallocAsync(&buf, tot * 8, s);
+    if (e != cudaSuccess) { end_work(sp); return set_error(CUT_ERR_OUT_OF_MEMORY, "cut_flow_vjp: workspace"); }
+    double *cp = buf, *seg = cp + ncp * L, *U = seg + (C + 1) * L, *K = U + S * L, *KB = K + S * L;
+    double *yb = KB + S * L, *ub = yb + L, *ybn = ub + L, *xi = ybn + L, *xib = xi + ng, *xb0 = xib + ng;
+    cudaMemcpyAsync(cp, h0, n * 8, cudaMemcpyDeviceToDevice, s);
+    if (n_obs) cudaMemcpyAsync(cp + n, x0, (size_t)n_obs * n * 8, cudaMemcpyDeviceToDevice, s);
+    // generic explicit RK step with stage storage: y (in) -> out, stages in U/K
+    auto step = [&](const double *y, double *out, double ds) {
+        for (int i = 0; i < S; i++) {
+            k::Combine cb;
+            cb.base = y;
+            cb.nk = 0;
+            for (int j = 0; j < i; j++)
+                if (A[i][j] != 0.0) { cb.K[cb.nk] = K + j * L; cb.c[cb.nk] = A[i][j]; cb.nk++; }
+            k::rk_combine<<<grid_for_len(L), 256, 0, s>>>(cb, U + i * L, L, nullptr, ds, nullptr);
+            stacked_rhs(g, U + i * L, K + i * L, nops, xi, s, nullptr);
+        }
+        k::Combine cb;
+        cb.base = y;
+        cb.nk = 0;
+        for (int j = 0; j < S; j++)
+            if (B[j] != 0.0) { cb.K[cb.nk] = K + j * L; cb.c[cb.nk] = B[j]; cb.nk++; }
+        k::rk_combine<<<grid_for_len(L), 256, 0, s>>>(cb, out, L, nullptr, ds, nullptr);
+    };
+    // forward: the state at step c*C is kept as checkpoint c
+    {
+        double *cur = seg, *nxt = seg + L;
+        cudaMemcpyAsync(cur, cp, L * 8, cudaMemcpyDeviceToDevice, s);
+        for (int64_t t = 0; t < N; t++) {
+            step(cur, nxt, steps[t]);
+            std::swap(cur, nxt);
+            if ((t + 1) % C == 0 && t + 1 < N) cudaMemcpyAsync(cp + ((t + 1) / C) * L, cur, L * 8, cudaMemcpyDeviceToDevice, s);
+        }
+    }
+    // backward, segment by segment: recompute the segment's step-start
+    // states from its checkpoint, then walk its steps in reverse
+    cudaMemcpyAsync(yb, yb_h, n * 8, cudaMemcpyDeviceToDevice, s);
+    if (n_obs) cudaMemcpyAsync(yb + n, yb_x, (size_t)n_obs * n * 8, cudaMemcpyDeviceToDevice, s);
+    auto axpy = [&](double *out, const double *base, const double *v, double c, double ds) {
+        k::Combine cb;
+        cb.base = base;
+        cb.nk = 1;
+        cb.K[0] = v;
+        cb.c[0] = c;
+        k::rk_combine<<<grid_for_len(L), 256, 0, s>>>(cb, out, L, nullptr, ds, nullptr);
+    };
+    for (int64_t c0 = N > 0 ? ((N - 1) / C) * C : -1; c0 >= 0; c0 -= C) {
+        const int64_t c1 = std::min(N, c0 + C);
+        cudaMemcpyAsync(seg, cp + (c0 / C) * L, L * 8, cudaMemcpyDeviceToDevice, s);
+        for (int64_t t = c0; t < c1 - 1; t++) step(seg + (t - c0) * L, seg + (t - c0 + 1) * L, steps[t]);
+        for (int64_t t = c1 - 1; t >= c0; t--) {
+            const double ds = steps[t];
+            step(seg + (t - c0) * L, ybn, ds);  // stage inputs U_i of step t
+            // k_bar_i = ds b_i y_bar, y_bar_new = y_bar
+            for (int i = 0; i < S; i++) {
+                cudaMemsetAsync(KB + i * L, 0, L * 8, s);
+                if (B[i] != 0.0) axpy(KB + i * L, KB + i * L, yb, B[i], ds);
+            }
+            cudaMemcpyAsync(ybn, yb, L * 8, cudaMemcpyDeviceToDevice, s);
+            for (int i = S - 1; i >= 0; i--) {
+                stacked_vjp(g, U + i * L, KB + i * L, ub, nops, xi, xib, xb0, s);  // u_bar_i
+                axpy(ybn, ybn, ub, 1.0, 1.0);
+                for (int j = 0; j < i; j++)
+                    if (A[i][j] != 0.0) axpy(KB + j * L, KB + j * L, ub, A[i][j], ds);
+            }
+            cudaMemcpyAsync(yb, ybn, L * 8, cudaMemcpyDeviceToDevice, s);
+        }
+    }
+    cudaMemcpyAsync(gh, yb, n * 8, cudaMemcpyDeviceToDevice, s);
+    if (n_obs) cudaMemcpyAsync(gx, yb + n, (size_t)n_obs * n * 8, cudaMemcpyDeviceToDevice, s);
+    cudaFreeAsync(buf, s);
+    e = cudaStreamSynchronize(s);
+    end_work(sp);
+    if (e != cudaSuccess) return set_error(CUT_ERR_CUDA, std::string("cut_flow_vjp: ") + cudaGetErrorString(e));
+    return set_ok();
+}
+
+extern "C" cut_status cut_flow_batched(const cut_graph *, int, double *, int, double *, int, const cut_flow_opts *,
+                                       int, int *, int *, cut_stream_t) {
+    return set_error(CUT_ERR_UNSUPPORTED, "cut_flow_batched: not built yet");
+}

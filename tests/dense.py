@@ -97,3 +97,56 @@ def rk4_dense(f, B, ds, nsteps):
         k4 = f(B + ds * k3)
         B = B + ds * (k1 + 2 * k2 + 2 * k3 + k4) / 6
     return B
+
+
+def _apply_monomial(label, state):
+    """Jordan-Wigner action of a+_{c1}..a+_{cm} a_{am}..a_{a1} on an occupation
+    bit mask: returns (sign, new_state) or (0, None)."""
+    label = int(label)
+    c, a = label & 0xFFFFFFFF, label >> 32
+    sign = 1
+    s = state
+    for p in range(32):                 # a_{a1} acts first (smallest index)
+        if a >> p & 1:
+            if not (s >> p) & 1:
+                return 0, None
+            sign *= (-1) ** bin(s & ((1 << p) - 1)).count("1")
+            s ^= 1 << p
+    for p in reversed(range(32)):       # then a+_{cm} ... a+_{c1}
+        if c >> p & 1:
+            if (s >> p) & 1:
+                return 0, None
+            sign *= (-1) ** bin(s & ((1 << p) - 1)).count("1")
+            s |= 1 << p
+    return sign, s
+
+
+def sector_matrix(labels, coefs, norb, N):
+    """Matrix of sum_k coefs[k] O_k on the N-particle occupation states."""
+    basis = sector_basis(norb, N)
+    pos = {s: i for i, s in enumerate(basis)}
+    M = np.zeros((len(basis), len(basis)))
+    for l, c in zip(labels, coefs):
+        if c == 0:
+            continue
+        for col, s in enumerate(basis):
+            sg, t = _apply_monomial(l, s)
+            if sg:
+                M[pos[t], col] += sg * c
+    return M
+
+
+def rk_dense(f, y, ds, A, B):
+    """One explicit RK step with tableau (A, B) for any array state."""
+    ks = []
+    for i in range(len(B)):
+        u = y
+        for j, a in enumerate(A[i]):
+            if a != 0.0:
+                u = u + ds * a * ks[j]
+        ks.append(f(u))
+    out = y
+    for b, k in zip(B, ks):
+        if b != 0.0:
+            out = out + ds * b * k
+    return out

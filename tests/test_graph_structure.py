@@ -1,0 +1,205 @@
+"""The compiled graph against the oracle, record by record (CPU only).
+
+Every stored record is an exact integer factor: bit-exact equality is
+required.  The expected records come from oracle unit-vector probes:
+  generator stage: alpha(g; i, j) = coefficient of G_g in [O_i, O_j]
+                   (divided by i for Pauli strings, eta = i sum xi G);
+  commutator stage: beta(k; a, j) = coefficient of O_k in P[G_a, O_j]
+                   (times i for Pauli strings).
+Also: deterministic rebuilds, thread-count independence, validated reload.
+"""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2609_14831_b300 as cg
+from cut_inputs import (ALG_FERMION, ALG_PAULI, fermion_registry, pauli_registry, workload,
+                        cfg2_registry)
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2609_14831_b300 import build
+    build.build()
+
+
+def _graph(tmp_path, alg, nmodes, labels, name, **kw):
+    path = str(tmp_path / f"{name}.cutg")
+    stats = cg.build_graph(alg, nmodes, labels, path, **kw)
+    return path, stats, cg.Graph(path, device=-1)
+
+
+def _graph_records(G, stage):
+    rp, a, b, c = G.records(stage)
+    num, den = G.weights()
+    assert np.all(den == 1)
+    rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+    return {(int(r), int(x), int(y)): int(num[z]) for r, x, y, z in zip(rows, a, b, c)}
+
+
+def _expected_gen(alg, nmodes, labels, gen_labels):
+    gidx = {int(l): a for a, l in enumerate(gen_labels)}
+    diag = [oracle.is_diagonal(alg, l) for l in labels]
+    out, dropped = {}, set()
+    for i, li in enumerate(labels):
+        if not diag[i]:
+            continue
+        for j, lj in enumerate(labels):
+            if diag[j]:
+                continue
+            for g, v in oracle.commutator(alg, nmodes, {int(li): 1.0}, {int(lj): 1.0}).items():
+                if v == 0:
+                    continue
+                val = v / 1j if alg == ALG_PAULI else v
+                assert val.imag == 0 and val.real == round(val.real)
+                if g in gidx:
+                    out[(gidx[g], i, j)] = int(val.real)
+                else:
+                    dropped.add(g)
+    return out, dropped
+
+
+def _expected_comm(alg, nmodes, labels, gen_labels, a_subset=None):
+    kidx = {int(l): k for k, l in enumerate(labels)}
+    out = {}
+    for a, ga in enumerate(gen_labels):
+        if a_subset is not None and a not in a_subset:
+            continue
+        for j, lj in enumerate(labels):
+            for k, v in oracle.commutator(alg, nmodes, {int(ga): 1.0}, {int(lj): 1.0}).items():
+                if v == 0 or k not in kidx:
+                    continue
+                val = v * 1j if alg == ALG_PAULI else v
+                assert val.imag == 0 and val.real == round(val.real)
+                out[(kidx[k], a, j)] = int(val.real)
+    return out
+
+
+def _check_dropped_generators_are_inert(alg, nmodes, labels, dropped, max_rank):
+    """Generator terms the graph leaves out must not reach the registry."""
+    reg = {int(l) for l in labels}
+    for g in list(dropped)[:60]:
+        for lj in labels:
+            F = oracle.commutator(alg, nmodes, {g: 1.0}, {int(lj): 1.0})
+            assert all(v == 0 or k not in reg for k, v in F.items()), (hex(g), hex(int(lj)))
+
+
+@pytest.mark.parametrize("case", ["pauli3", "pauli4", "fermion5", "fermion5_3body"])
+def test_records_match_oracle_probes_exactly(tmp_path, case):
+    if case.startswith("pauli"):
+        nq = int(case[-1])
+        alg, nmodes, labels = ALG_PAULI, nq, pauli_registry(nq)
+    elif case == "fermion5":
+        alg, nmodes, labels = ALG_FERMION, 5, fermion_registry(5)
+    else:
+        alg, nmodes = ALG_FERMION, 5
+        labels = cfg2_registry(5, keep_shared1=0.3, seed=3)
+    path, stats, G = _graph(tmp_path, alg, nmodes, labels, case)
+    lab, gen_labels, diag = G.labels()
+    np.testing.assert_array_equal(lab, labels)
+    assert list(diag) == [oracle.is_diagonal(alg, l) for l in labels]
+    want_gen, dropped = _expected_gen(alg, nmodes, labels, gen_labels)
+    assert _graph_records(G, 0) == want_gen
+    assert _graph_records(G, 1) == _expected_comm(alg, nmodes, labels, gen_labels)
+    max_rank = max(bin(int(l) & 0xFFFFFFFF).count("1") for l in labels)
+    _check_dropped_generators_are_inert(alg, nmodes, labels, dropped, max_rank)
+    if case == "pauli4":
+        assert (stats["R_g"], stats["R_L"]) == (15 * 128, 240 * 128)   # closed-form counts
+
+
+def test_molecular_8so_records_sampled(tmp_path):
+    w = workload("molecular_8so")
+    path, stats, G = _graph(tmp_path, w.alg, w.nmodes, w.labels, "mol8")
+    _, gen_labels, _ = G.labels()
+    assert stats["n"] == 848
+    rng = np.random.default_rng(0)
+    subset = set(int(a) for a in rng.choice(len(gen_labels), 24, replace=False))
+    want = _expected_comm(w.alg, w.nmodes, w.labels, gen_labels, subset)
+    got = {key: v for key, v in _graph_records(G, 1).items() if key[1] in subset}
+    assert got == want
+    want_gen, _ = _expected_gen(w.alg, w.nmodes, w.labels, gen_labels)
+    assert _graph_records(G, 0) == want_gen
+
+
+def test_rebuild_is_bitwise_identical_for_any_thread_count(tmp_path):
+    labels = cfg2_registry(6, keep_shared1=0.2, seed=4)
+    paths = []
+    for t, threads in enumerate((1, 3, 0)):
+        p = str(tmp_path / f"g{t}.cutg")
+        cg.build_graph(ALG_FERMION, 6, labels, p, threads=threads)
+        paths.append(p)
+    blobs = [open(p, "rb").read() for p in paths]
+    assert blobs[0] == blobs[1] == blobs[2]
+    G = cg.Graph(paths[0], device=-1)
+    assert len(G.desc["sha256"]) == 64
+
+
+def test_validated_reload_rejects_damaged_bundles(tmp_path):
+    labels = fermion_registry(4)
+    p = str(tmp_path / "g.cutg")
+    cg.build_graph(ALG_FERMION, 4, labels, p)
+    blob = bytearray(open(p, "rb").read())
+    # flipped payload byte -> checksum error
+    bad = bytearray(blob)
+    bad[len(bad) // 2] ^= 0x40
+    q = str(tmp_path / "flip.cutg")
+    open(q, "wb").write(bad)
+    with pytest.raises(cg.CutError) as e:
+        cg.Graph(q, device=-1)
+    assert e.value.name == "CHECKSUM"
+    # truncated -> format error
+    q = str(tmp_path / "trunc.cutg")
+    open(q, "wb").write(blob[: len(blob) - 100])
+    with pytest.raises(cg.CutError) as e:
+        cg.Graph(q, device=-1)
+    assert e.value.name == "FORMAT"
+    # wrong magic -> format error
+    bad = bytearray(blob)
+    bad[0:8] = b"NOTAGRPH"
+    q = str(tmp_path / "magic.cutg")
+    open(q, "wb").write(bad)
+    with pytest.raises(cg.CutError) as e:
+        cg.Graph(q, device=-1)
+    assert e.value.name == "FORMAT"
+    # missing -> IO
+    with pytest.raises(cg.CutError) as e:
+        cg.Graph(str(tmp_path / "absent.cutg"), device=-1)
+    assert e.value.name == "IO"
+
+
+def test_builder_rejects_bad_registries(tmp_path):
+    p = str(tmp_path / "x.cutg")
+    labels = fermion_registry(3)
+    with pytest.raises(cg.CutError) as e:
+        cg.build_graph(ALG_FERMION, 3, np.concatenate([labels, labels[:1]]), p)
+    assert e.value.name == "INVALID_ARG"
+    with pytest.raises(cg.CutError):
+        cg.build_graph(ALG_FERMION, 2, labels, p)         # label beyond nmodes
+    with pytest.raises(cg.CutError):
+        cg.build_graph(ALG_FERMION, 3, np.array([1 | (3 << 32)], dtype=np.uint64), p)  # not number conserving
+
+
+def test_library_exports_every_declared_symbol():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(cut_[a-z0-9_]+)\s*\(", text))
+    assert "cut_rhs" in names and "cut_flow_batched" in names
+    L = cg.lib()
+    for n in sorted(names):
+        assert hasattr(L, n), n
+
+
+def test_traversals_refuse_host_only_handles(tmp_path):
+    p = str(tmp_path / "h.cutg")
+    cg.build_graph(ALG_PAULI, 2, pauli_registry(2), p)
+    G = cg.Graph(p, device=-1)
+    rc = cg.lib().cut_rhs(G._h, None, 0, None, None, None, None, None)
+    assert rc == 1

@@ -299,3 +299,15 @@ def test_integrator_tableaux_and_closed_form_odes():
     # replay of the accepted steps reproduces the result exactly
     y2, _, _ = oracle.dp45_flow(lambda y: A @ y, np.array([1.0, 0.0]), 0.0, 3.0, 0.1, 1e-10, 1e-14, replay=steps)
     np.testing.assert_array_equal(y, y2)
+
+
+def test_occupation_sector_matrices_match_jordan_wigner_blocks():
+    """The occupation-basis sector helper used by the full-size GPU flow
+    checks agrees with the Jordan-Wigner matrices."""
+    norb = 5
+    labels = fermion_registry(norb, ranks=(1, 2, 3))
+    h = molecular_hamiltonian(labels, norb, seed=16, scale=0.3)
+    M = dense.vec_matrix(labels, h, ALG_FERMION, norb)
+    for N in (1, 2, 3):
+        np.testing.assert_allclose(dense.sector_matrix(labels, h, norb, N), dense.sector_block(M, norb, N).real,
+                                   atol=1e-13)
