@@ -1,0 +1,318 @@
+"""Benchmark: graph records applied per second on one B300 (and per job).
+
+Workload (default): the stress operation graph -- 16 spin-orbitals, one- and
+two-body labels plus selected three-body labels (about 3.3e8 records, 2.6 GB
+resident), the molecular coefficient recipe, H flowed with the particle
+number N and a dipole-like D (three operands per record read).  A step is
+one fixed-ds RK4 step of the flow: four right-hand sides (generator stage +
+commutator stage each) and the stage combinations, all in libcut.so kernels.
+
+  value    : records applied per second = 4 (R_g + R_L) / step time, summed
+             over ranks (each rank flows its own seeded instance: weak scaling,
+             no collective on the data path);
+  e2e      : the same through the public API with the state copied from and
+             to pinned host memory inside every step;
+  roofline : one graph apply (generator + commutator stage kernels) timed
+             with CUDA events on its stream, against the measured HBM copy
+             bandwidth; algorithmic bytes = stored records + row pointers +
+             coefficient outputs (gathers assumed on chip);
+  cpu_baseline : the oracle (plain string multiplication, one host thread) on
+             a bounded sample of the same recipe (7 spin-orbitals).
+
+`--impl reference` times the oracle on the host cores instead (the paper
+ships no code; the oracle is the reference arm).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6400.0
+
+
+def _peak_hbm():
+    try:
+        with open(PEAKS) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(ms, world, device=None):
+    """Slowest rank's time (the job finishes when every rank has)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank_step, ms_step, world):
+    """Whole-job units per second: every rank processes its own units."""
+    return world * units_per_rank_step / (ms_step * 1e-3)
+
+
+def _build(workload_name, seed, tmpdir, rank):
+    import paper_2609_14831_b300 as cg
+    from cut_inputs import workload
+    w = workload(workload_name, seed=seed)
+    path = os.path.join(tmpdir, f"{workload_name}_r{rank}.cutg")
+    t0 = time.time()
+    stats = cg.build_graph(w.alg, w.nmodes, w.labels, path)
+    return w, path, stats, time.time() - t0
+
+
+def cpu_sample(seconds_budget=20.0):
+    """Oracle RHS on the 7-spin-orbital stress recipe; records/s of its graph."""
+    import oracle
+    import paper_2609_14831_b300 as cg
+    from cut_inputs import workload
+    w = workload("stress_7so", seed=2)
+    with tempfile.TemporaryDirectory() as d:
+        p = os.path.join(d, "s8.cutg")
+        st = cg.build_graph(w.alg, w.nmodes, w.labels, p)
+    rec = st["R_g"] + st["R_L"]
+    t0 = time.time()
+    calls = 0
+    while True:
+        oracle.rhs(w.alg, w.nmodes, w.labels, w.h, w.observables)
+        calls += 1
+        if time.time() - t0 > seconds_budget or calls >= 3:
+            break
+    dt = (time.time() - t0) / calls
+    return {"value": rec / dt, "unit": "records/s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle right-hand side (H, N, D) of the same recipe on 7 spin-orbitals "
+                      f"(n={len(w.labels)}, {rec} graph records), {calls} call(s), {dt:.2f} s each; "
+                      f"value = graph records / oracle time"}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    cb = cpu_sample(seconds_budget=max(5.0, 60.0 / max(1, args.steps + args.warmup)))
+    line = {"impl": "reference", "metric": "graph records applied per second", "value": cb["value"],
+            "unit": "records/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "stress_16so (oracle on the 7-spin-orbital sample)"},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "records/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cut", choices=["cut", "reference"])
+    ap.add_argument("--workload", default="stress_16so")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2609_14831_b300 as cg
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    tmpdir = tempfile.mkdtemp(prefix="cutbench_")
+    w, path, bstats, tbuild = _build(args.workload, 2 + rank, tmpdir, rank)
+    G = cg.Graph(path, device=local)
+    os.remove(path)
+    R = G.R_g + G.R_L
+    n = G.n
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    h0 = torch.tensor(w.h, dtype=torch.float64, device=dev)
+    xs0 = [torch.tensor(x, dtype=torch.float64, device=dev) for x in w.observables]
+    ds = w.ds
+
+    def steps_on_device(k):
+        return G.flow(h0, xs0, method="rk4", s0=0.0, s1=k * ds, ds=ds, stream=stream)
+
+    with torch.cuda.stream(stream):
+        steps_on_device(args.warmup)
+    torch.cuda.synchronize()
+
+    # ---- timed region: exactly K RK4 steps, inputs resident in HBM
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        _, _, fst, _ = steps_on_device(args.steps)
+        ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ck = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    assert fst["steps"] == args.steps
+    ms = max_over_ranks(ms, world, dev)
+    ms_step = ms / args.steps
+    value = job_throughput(4 * R, ms_step, world)
+
+    # ---- roofline: one graph apply (generator + commutator stage) on its stream
+    napply = 20
+    with torch.cuda.stream(stream):
+        G.rhs(h0, xs0, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(napply):
+            G.rhs(h0, xs0, stream=stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    apply_ms = e0.elapsed_time(e1) / napply
+    nops = 1 + len(xs0)
+    alg_bytes = 8 * R + 8 * (G.n_g + 1) + 8 * (n + 1) + 8 * G.n_g + 8 * nops * n
+    peak, peak_kind = _peak_hbm()
+    achieved = alg_bytes / (apply_ms * 1e-3) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        try:
+            traffic = json.load(open(tpath)).get(f"{args.workload}:graph_apply")
+        except Exception:
+            traffic = None
+
+    # ---- end to end through the public API with host buffers
+    pin_h = torch.tensor(w.h, dtype=torch.float64).pin_memory()
+    pin_x = [torch.tensor(x, dtype=torch.float64).pin_memory() for x in w.observables]
+    out_h = torch.empty(n, dtype=torch.float64).pin_memory()
+    out_x = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in w.observables]
+    e2e_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for _ in range(e2e_steps):
+            hd = pin_h.to(dev, non_blocking=True)
+            xd = [p.to(dev, non_blocking=True) for p in pin_x]
+            hs, xo, _, _ = G.flow(hd, xd, method="rk4", s0=0.0, s1=ds, ds=ds, stream=stream)
+            out_h.copy_(hs, non_blocking=True)
+            for o, x in zip(out_x, xo):
+                o.copy_(x, non_blocking=True)
+            stream.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_val = world * 4 * R / e2e_s
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_sample()
+
+    if rank == 0:
+        line = {
+            "metric": "graph records applied per second (stress graph RK4 flow, FP64)",
+            "value": value, "unit": "records/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n": int(n), "n_g": int(G.n_g), "R_g": int(G.R_g),
+                       "R_L": int(G.R_L), "operands": nops, "record_bytes": 8, "integrator": "rk4",
+                       "ds": ds, "l2": "inputs larger than L2 (graph %.2f GB resident)" % (8 * R / 1e9),
+                       "build_s": round(tbuild, 1), "build_peak_over_stored":
+                           round(bstats["peak_rss_bytes"] / max(1, bstats["bytes_stored"]), 3),
+                       "parallelism": f"{world} independent instance(s)"},
+            "gpu_launches": int(args.steps * 4 * (1 + (nops + 3) // 4) + args.steps * 4),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "kernel": "graph apply = gen_stage + comm_stage<3>",
+                         "apply_ms": apply_ms, "algorithmic_bytes": alg_bytes},
+            "clocks": ck,
+            "e2e": {"value": e2e_val, "unit": "records/s",
+                    "h2d_bytes_per_step": int(8 * n * nops), "d2h_bytes_per_step": int(8 * n * nops)},
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    G.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

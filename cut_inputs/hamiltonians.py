@@ -174,7 +174,8 @@ def workload(name, **kw):
 
     closed_pauli_4q    : 256 Pauli strings, RK4, ds = 1e-3 to s = 10.
     molecular_8so      : 848 fermion labels, H + N + D, DP45 rtol 1e-10.
-    stress_16so        : 16 spin-orbitals + selected three-body labels.
+    stress_<k>so       : k spin-orbitals + selected three-body labels
+                         (stress_16so is the ~3.4e8-record stress graph).
     molecular_<k>so    : the molecular recipe on k spin-orbitals (tests).
     """
     if name == "closed_pauli_4q":
@@ -189,15 +190,20 @@ def workload(name, **kw):
         hmax = np.max(np.abs(h))
         return Workload(name, ALG_FERMION, norb, labels, h, obs, "dp45", 10.0, 1e-2,
                         1e-10, 1e-12 * hmax, max(ranks))
-    if name == "stress_16so":
-        labels = cfg2_registry(16, keep_shared1=kw.get("keep_shared1", STRESS_KEEP_SHARED1))
-        h = molecular_hamiltonian(labels, 16, seed=2)
-        obs = [number_operator(labels, 16), dipole_operator(labels, 16, seed=2)]
+    if name.startswith("stress_") and name.endswith("so"):
+        norb = int(name[len("stress_"):-2])
+        labels = cfg2_registry(norb, keep_shared1=STRESS_KEEP_SHARED1, keep_shared0=STRESS_KEEP_SHARED0,
+                               seed=kw.get("seed", 2))
+        h = molecular_hamiltonian(labels, norb, seed=kw.get("seed", 2))
+        obs = [number_operator(labels, norb), dipole_operator(labels, norb, seed=kw.get("seed", 2))]
         hmax = np.max(np.abs(h))
-        return Workload(name, ALG_FERMION, 16, labels, h, obs, "rk4", 10.0, 1e-2,
+        return Workload(name, ALG_FERMION, norb, labels, h, obs, "rk4", 10.0, 1e-3,
                         1e-10, 1e-12 * hmax, 3)
     raise KeyError(name)
 
 
-# fraction of one-shared-orbital three-body labels kept in the stress registry
-STRESS_KEEP_SHARED1 = 0.0
+# Stress registry (16 spin-orbitals, about 3.3e8 records): every three-body
+# label sharing >= 1 orbital between its creator and annihilator sets and a
+# seeded 28% of the disjoint ones.
+STRESS_KEEP_SHARED1 = 1.0
+STRESS_KEEP_SHARED0 = 0.28

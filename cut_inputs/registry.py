@@ -90,11 +90,12 @@ def fermion_string(label):
     return " ".join([f"a+{i}" for i in cs] + [f"a{i}" for i in an])
 
 
-def cfg2_registry(norb=16, keep_shared1=0.0, seed=2):
+def cfg2_registry(norb=16, keep_shared1=0.0, seed=2, keep_shared0=0.0):
     """Stress registry: every one- and two-body label on `norb` orbitals, plus
     three-body labels whose creator and annihilator sets share at least two
-    orbitals (spectator-dressed one-body moves), plus a seeded fraction
-    `keep_shared1` of the three-body labels sharing exactly one orbital.
+    orbitals (spectator-dressed one-body moves), plus seeded fractions
+    `keep_shared1` / `keep_shared0` of the three-body labels sharing exactly
+    one / no orbital (fraction 1 keeps all of them).
     """
     rng = np.random.default_rng(seed)
     combos3 = list(combinations(range(norb), 3))
@@ -106,7 +107,8 @@ def cfg2_registry(norb=16, keep_shared1=0.0, seed=2):
         cs = set(c)
         for ai, a in enumerate(combos3):
             shared = len(cs.intersection(a))
-            if shared >= 2 or (shared == 1 and draws[ci, ai] < keep_shared1):
+            if (shared >= 2 or (shared == 1 and draws[ci, ai] < keep_shared1)
+                    or (shared == 0 and draws[ci, ai] < keep_shared0)):
                 sel.append(make_label(_mask(c), _mask(a)))
     base = fermion_registry(norb, ranks=(1, 2))
     return np.concatenate([base, np.array(sel, dtype=np.uint64)])

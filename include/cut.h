@@ -210,6 +210,44 @@ cut_status cut_flow_batched(const cut_graph *g, int batch, double *h, int n_obs,
                             int precision, const cut_flow_opts *opts, int tile, int *steps_out,
                             int *status_out, cut_stream_t stream);
 
+/* ------------------------------------------------------------------ */
+/* Learned surrogate of the flow map (the paper has no counterpart: a   */
+/* warm start and screen in front of the graph flow, which stays the    */
+/* fallback and the judge of its error)                                 */
+/* ------------------------------------------------------------------ */
+/* MLP n_in -> n_hidden -> n_hidden -> n_out, GELU after the two hidden
+ * layers, BF16 operands with FP32 accumulation on the tensor cores
+ * (tcgen05), FP32 master weights, AdamW.  Targets are standardised per
+ * output, t_hat = (t - shift) / scale; the forward pass returns
+ * y = scale * y_hat + shift.  Weights start uniform in +-1/sqrt(fan_in)
+ * from `seed`, biases 0, scale 1, shift 0. */
+typedef struct cut_mlp cut_mlp;
+cut_status cut_mlp_create(int n_in, int n_hidden, int n_out, uint64_t seed, int device, cut_mlp **out);
+cut_status cut_mlp_free(cut_mlp *m);
+/* host in: scale[n_out] (> 0), shift[n_out] */
+cut_status cut_mlp_set_output_affine(cut_mlp *m, const float *scale, const float *shift);
+/* number of parameters in the flat layout W1, b1, W2, b2, W3, b3 (W [out][in]) */
+int64_t cut_mlp_param_count(const cut_mlp *m);
+/* host out: parameters (grads = 0) or the gradients of the last backward
+ * (grads = 1), flat layout above.  Synchronous. */
+cut_status cut_mlp_get_params(cut_mlp *m, float *host, int grads);
+/* host in: parameters, flat layout above.  Synchronous. */
+cut_status cut_mlp_set_params(cut_mlp *m, const float *host);
+/* device in: x[batch][n_in] (FP32); device out: y[batch][n_out] (FP32). */
+cut_status cut_mlp_forward(cut_mlp *m, int batch, const float *x, float *y, cut_stream_t stream);
+/* Gradients of the mean squared error over batch x n_out of the
+ * standardised targets, kept inside m.  device in: x[batch][n_in],
+ * target[batch][n_out]; device in/out: loss (one float, the loss is ADDED,
+ * may be NULL). */
+cut_status cut_mlp_backward(cut_mlp *m, int batch, const float *x, const float *target, float *loss,
+                            cut_stream_t stream);
+/* One AdamW update (decoupled weight decay, none on biases) from the last
+ * backward's gradients. */
+cut_status cut_mlp_adamw_step(cut_mlp *m, float lr, float beta1, float beta2, float eps, float weight_decay,
+                              cut_stream_t stream);
+/* Synchronises; TIMEOUT if a tensor-core pipeline wait gave up. */
+cut_status cut_mlp_status(cut_mlp *m);
+
 #ifdef __cplusplus
 }
 #endif

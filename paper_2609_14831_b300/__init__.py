@@ -91,6 +91,17 @@ def lib():
         "cut_flow": (st, [VP, VP, i, VP, ctypes.POINTER(FlowOpts), ctypes.POINTER(FlowStats), VP]),
         "cut_flow_vjp": (st, [VP, VP, i, VP, ctypes.POINTER(FlowOpts), i, VP, VP, VP, VP, VP]),
         "cut_flow_batched": (st, [VP, i, VP, i, VP, i, ctypes.POINTER(FlowOpts), i, VP, VP, VP]),
+        "cut_mlp_create": (st, [i, i, i, ctypes.c_uint64, i, ctypes.POINTER(VP)]),
+        "cut_mlp_free": (st, [VP]),
+        "cut_mlp_set_output_affine": (st, [VP, VP, VP]),
+        "cut_mlp_param_count": (i64, [VP]),
+        "cut_mlp_get_params": (st, [VP, VP, i]),
+        "cut_mlp_set_params": (st, [VP, VP]),
+        "cut_mlp_forward": (st, [VP, i, VP, VP, VP]),
+        "cut_mlp_backward": (st, [VP, i, VP, VP, VP, VP]),
+        "cut_mlp_adamw_step": (st, [VP, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                    ctypes.c_float, VP]),
+        "cut_mlp_status": (st, [VP]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -291,3 +302,73 @@ class Graph:
         check(lib().cut_flow_batched(self._h, B, _ptr(H), n_obs, _ptr(X), prec, ctypes.byref(o),
                                      int(tile), _ptr(steps), _ptr(status), _stream(stream)))
         return H, X, steps, status
+
+
+class MLP:
+    """The surrogate network n_in -> H -> H -> n_out (tcgen05 BF16 GEMMs)."""
+
+    def __init__(self, n_in, n_hidden, n_out, seed=0, device=0):
+        self._h = VP()
+        check(lib().cut_mlp_create(int(n_in), int(n_hidden), int(n_out), int(seed), int(device),
+                                   ctypes.byref(self._h)))
+        self.n_in, self.n_hidden, self.n_out = n_in, n_hidden, n_out
+        self.device_index = int(device)
+
+    @property
+    def device(self):
+        return _torch().device("cuda", self.device_index)
+
+    def close(self):
+        if self._h:
+            lib().cut_mlp_free(self._h)
+            self._h = VP()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_output_affine(self, scale, shift):
+        sc = np.ascontiguousarray(scale, dtype=np.float32)
+        sh = np.ascontiguousarray(shift, dtype=np.float32)
+        check(lib().cut_mlp_set_output_affine(self._h, sc.ctypes.data, sh.ctypes.data))
+
+    def params(self, grads=False):
+        out = np.empty(lib().cut_mlp_param_count(self._h), dtype=np.float32)
+        check(lib().cut_mlp_get_params(self._h, out.ctypes.data, 1 if grads else 0))
+        return out
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        assert flat.size == lib().cut_mlp_param_count(self._h)
+        check(lib().cut_mlp_set_params(self._h, flat.ctypes.data))
+
+    def _f32(self, t, cols):
+        torch = _torch()
+        t = t if isinstance(t, torch.Tensor) else torch.as_tensor(np.asarray(t, dtype=np.float32))
+        t = t.to(device=self.device, dtype=torch.float32).contiguous()
+        assert t.dim() == 2 and t.shape[1] == cols
+        return t
+
+    def forward(self, x, stream=None):
+        torch = _torch()
+        x = self._f32(x, self.n_in)
+        y = torch.empty(x.shape[0], self.n_out, dtype=torch.float32, device=self.device)
+        check(lib().cut_mlp_forward(self._h, x.shape[0], _ptr(x), _ptr(y), _stream(stream)))
+        return y
+
+    def backward(self, x, target, stream=None):
+        """Gradients of the standardised MSE; returns the loss tensor (device)."""
+        torch = _torch()
+        x = self._f32(x, self.n_in)
+        t = self._f32(target, self.n_out)
+        loss = torch.zeros(1, dtype=torch.float32, device=self.device)
+        check(lib().cut_mlp_backward(self._h, x.shape[0], _ptr(x), _ptr(t), _ptr(loss), _stream(stream)))
+        return loss
+
+    def step(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, stream=None):
+        check(lib().cut_mlp_adamw_step(self._h, lr, beta1, beta2, eps, weight_decay, _stream(stream)))
+
+    def status(self):
+        check(lib().cut_mlp_status(self._h))

@@ -29,7 +29,7 @@ def build(force=False, verbose=False):
     nvcc = os.environ.get("NVCC", "nvcc")
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc, "-O3", "-std=c++17", "-shared", "-Xcompiler", "-fPIC,-O3", *ARCH, "-lineinfo",
-           "-I", os.path.join(ROOT, "include"), "-I", CSRC, "-o", tmp, *sources(), "-lpthread", "-lcuda"]
+           "-I", os.path.join(ROOT, "include"), "-I", CSRC, "-o", tmp, *sources(), "-lpthread"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
         print(" ".join(cmd), file=sys.stderr)

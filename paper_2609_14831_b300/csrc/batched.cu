@@ -1,0 +1,530 @@
+// batched.cu -- many coefficient sets through one graph (paper Sec. 1 and 4:
+// parameter ensembles reuse one compiled algebra; Eq. graph-actions applied
+// to a batch of Hamiltonians).
+//
+// One persistent kernel integrates the whole batch.  Each CTA owns TILE
+// instance slots.  A record is read once per CTA and applied to all TILE
+// instances: lane = (record group g, instance b), 32/TILE records in flight
+// per warp.  The stage input U and the generator xi live in shared memory
+// with the instance index fastest ([row][TILE]), so the gathers of one record
+// are one contiguous shared-memory access per group.  The RK state Y, Y5 and
+// the error control are FP64 (per instance, in the CTA's global workspace);
+// records, products and sums run in the compute type T (float or double).
+// A slot whose instance finishes is refilled from a global queue (active-set
+// compaction): no host round trip and no grid-wide barrier anywhere.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "cut.h"
+#include "status.h"
+
+namespace cut {
+namespace kb {
+
+constexpr uint32_t kIdx = (1u << 24) - 1;
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+struct Tableau {
+    int stages;       // RHS evaluations per step (RK4: 4; DP45: 7 incl. FSAL stage)
+    double a[7][7];
+    double b[7];      // solution weights
+    double e[7];      // error weights (b - b*)
+    int adaptive;
+};
+
+struct Args {
+    const uint64_t *rp0, *rp1;
+    const uint2 *rec0, *rec1;
+    const double *wtab;
+    int n_codes;
+    int64_t n, n_g;
+    int nops, B;
+    double *H, *X;              // user state, instance-major, in/out
+    int *steps_out, *status_out;
+    int *queue;                 // next instance to start
+    double *ws;                 // per-CTA workspace
+    int64_t ws_stride;          // bytes per CTA
+    double s0, s1, ds0, rtol, atol;
+    long long max_steps;        // attempts per instance
+    long long probe_attempts;   // > 0: stop every CTA after that many attempts (autotuning)
+    Tableau tb;
+};
+
+template <typename T>
+__device__ __forceinline__ T group_sum(T v, int tile) {
+    for (int o = 16; o >= tile; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// RHS of all TILE slots: U (smem, [nops][n][TILE]) -> K (global, [nops][n][TILE])
+template <typename T, int TILE, int NOPS>
+__device__ void rhs_tile(const Args &a, const T *__restrict__ U, T *__restrict__ xis, const T *__restrict__ ws,
+                         T *__restrict__ K) {
+    constexpr int G = 32 / TILE;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane / TILE, b = lane % TILE;
+    const int64_t n = a.n;
+    // generator stage: xi[a][b] = sum alpha U0[i][b] U0[j][b]
+    for (int64_t r = warp; r < a.n_g; r += kWarps) {
+        T acc = T(0);
+        for (uint64_t p = a.rp0[r] + g; p < a.rp0[r + 1]; p += G) {
+            uint2 q = __ldg(a.rec0 + p);
+            acc += ws[q.x >> 24] * U[(q.x & kIdx) * TILE + b] * U[(int64_t)q.y * TILE + b];
+        }
+        acc = group_sum(acc, TILE);
+        if (g == 0) xis[r * TILE + b] = acc;
+    }
+    __syncthreads();
+    // commutator stage: K_o[k][b] = sum beta xi[a][b] U_o[j][b]
+    for (int64_t r = warp; r < n; r += kWarps) {
+        T acc[NOPS];
+#pragma unroll
+        for (int o = 0; o < NOPS; o++) acc[o] = T(0);
+        for (uint64_t p = a.rp1[r] + g; p < a.rp1[r + 1]; p += G) {
+            uint2 q = __ldg(a.rec1 + p);
+            const T c = ws[q.x >> 24] * xis[(q.x & kIdx) * TILE + b];
+            const int64_t j = (int64_t)q.y * TILE + b;
+#pragma unroll
+            for (int o = 0; o < NOPS; o++) acc[o] += c * U[o * n * TILE + j];
+        }
+#pragma unroll
+        for (int o = 0; o < NOPS; o++) {
+            T v = group_sum(acc[o], TILE);
+            if (g == 0) K[(o * n + r) * TILE + b] = v;
+        }
+    }
+}
+
+template <typename T, int TILE, int NOPS>
+__global__ void __launch_bounds__(kThreads, 1) flow_batched_kernel(Args a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int64_t n = a.n, L = (int64_t)NOPS * n;
+    double *red = reinterpret_cast<double *>(smem);     // [kThreads]
+    T *U = reinterpret_cast<T *>(red + kThreads);       // [NOPS][n][TILE]
+    T *xis = U + L * TILE;                              // [n_g][TILE]
+    T *ws = xis + a.n_g * TILE;                         // [256]
+    __shared__ int inst[TILE], status[TILE], need_k1[TILE], acc_flag[TILE];
+    __shared__ double s_[TILE], ds_[TILE];
+    __shared__ long long steps_[TILE], attempts_[TILE];
+    __shared__ int any_active, any_new;
+    __shared__ long long cta_attempts;
+
+    for (int c = threadIdx.x; c < 256; c += kThreads) ws[c] = c < a.n_codes ? T(a.wtab[c]) : T(0);
+    // workspace of this CTA: Y, Y5 (double) then K[7] (T), all [NOPS][n][TILE]
+    double *Y = reinterpret_cast<double *>(reinterpret_cast<char *>(a.ws) + (int64_t)blockIdx.x * a.ws_stride);
+    double *Y5 = Y + L * TILE;
+    T *Kb = reinterpret_cast<T *>(Y5 + L * TILE);
+    auto Kst = [&](int s) { return Kb + (int64_t)s * L * TILE; };
+    if (threadIdx.x < TILE) { inst[threadIdx.x] = -1; status[threadIdx.x] = 0; }
+    if (threadIdx.x == 0) cta_attempts = 0;
+    __syncthreads();
+    const Tableau &tb = a.tb;
+    const int S = tb.stages;
+    const int mb = threadIdx.x % TILE;   // every element this thread touches belongs to slot mb
+
+    for (;;) {
+        // ---- refill idle slots from the queue
+        if (threadIdx.x < TILE) {
+            const int t = threadIdx.x;
+            need_k1[t] = 0;
+            if (inst[t] == -1) {
+                int b = atomicAdd(a.queue, 1);
+                if (b < a.B) {
+                    inst[t] = b;
+                    s_[t] = a.s0;
+                    ds_[t] = tb.adaptive ? fmin(a.ds0, a.s1 - a.s0) : a.ds0;
+                    steps_[t] = 0;
+                    attempts_[t] = 0;
+                    status[t] = 0;
+                    need_k1[t] = 1;
+                } else {
+                    inst[t] = -2;   // queue exhausted
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int act = 0, nw = 0;
+            for (int t = 0; t < TILE; t++) { act |= inst[t] >= 0; nw |= need_k1[t]; }
+            any_active = act && !(a.probe_attempts > 0 && cta_attempts >= a.probe_attempts);
+            any_new = nw;
+        }
+        // load the initial state of new instances
+        for (int64_t e = threadIdx.x; e < L * TILE; e += kThreads) {
+            const int b = (int)(e % TILE);
+            if (!need_k1[b]) continue;
+            const int64_t row = e / TILE, o = row / n, k = row % n;
+            const int64_t i = inst[b];
+            Y[e] = o == 0 ? a.H[i * n + k] : a.X[(i * (NOPS - 1) + (o - 1)) * n + k];
+        }
+        __syncthreads();
+        if (!any_active) break;
+        if (threadIdx.x == 0) cta_attempts++;
+
+        // ---- stages
+        for (int st = 0; st < S; st++) {
+            const bool fsal_first = tb.adaptive && st == 0;
+            if (fsal_first && !any_new) continue;       // K1 = f(Y) carried over (FSAL)
+            // U = Y + ds sum_j a[st][j] K_j   (FP64, rounded to T into shared memory)
+            for (int64_t e = threadIdx.x; e < L * TILE; e += kThreads) {
+                double u = Y[e];
+                const double ds = ds_[mb];
+                for (int j = 0; j < st; j++)
+                    if (tb.a[st][j] != 0.0) u += (tb.a[st][j] * ds) * (double)Kst(j)[e];
+                if (tb.adaptive && st == S - 1) Y5[e] = u;
+                U[e] = T(u);
+            }
+            __syncthreads();
+            rhs_tile<T, TILE, NOPS>(a, U, xis, ws, fsal_first ? Kst(S) : Kst(st));
+            __syncthreads();
+            if (fsal_first) {   // only the new slots take the fresh K1
+                for (int64_t e = threadIdx.x; e < L * TILE; e += kThreads)
+                    if (need_k1[mb]) Kst(0)[e] = Kst(S)[e];
+                __syncthreads();
+            }
+        }
+        // ---- error ratio per slot (adaptive) or the fixed-step update
+        {
+            double m = 0.0;
+            bool bad = false;
+            for (int64_t e = threadIdx.x; e < L * TILE; e += kThreads) {
+                const double ds = ds_[mb];
+                if (tb.adaptive) {
+                    double err = 0.0;
+                    for (int j = 0; j < S; j++)
+                        if (tb.e[j] != 0.0) err += (ds * tb.e[j]) * (double)Kst(j)[e];
+                    const double sc = a.atol + a.rtol * fmax(fabs(Y[e]), fabs(Y5[e]));
+                    const double r = fabs(err) / sc;
+                    if (!(r == r) || !isfinite(Y5[e])) bad = true;
+                    else m = fmax(m, r);
+                } else {
+                    double y = Y[e];
+                    for (int j = 0; j < S; j++)
+                        if (tb.b[j] != 0.0) y += (tb.b[j] * ds) * (double)Kst(j)[e];
+                    Y5[e] = y;
+                    if (!isfinite(y)) bad = true;
+                }
+            }
+            red[threadIdx.x] = bad ? NAN : m;
+        }
+        __syncthreads();
+        // ---- per-slot control (one thread per slot)
+        if (threadIdx.x < TILE) {
+            const int t = threadIdx.x;
+            acc_flag[t] = 0;
+            if (inst[t] >= 0) {
+                double r = 0.0;
+                bool bad = false;
+                for (int q = t; q < kThreads; q += TILE) {
+                    double v = red[q];
+                    if (!(v == v)) bad = true;
+                    else r = fmax(r, v);
+                }
+                attempts_[t]++;
+                int done = 0;
+                if (bad) {
+                    status[t] = CUT_ERR_NONFINITE;
+                    done = 1;
+                } else if (!tb.adaptive) {
+                    acc_flag[t] = 1;
+                    steps_[t]++;
+                    s_[t] = a.s0 + (double)steps_[t] * ds_[t];
+                    if (steps_[t] >= a.max_steps) done = 1;
+                } else {
+                    const int accept = r <= 1.0;
+                    double fac;
+                    if (accept) fac = r == 0.0 ? 5.0 : fmin(5.0, fmax(0.2, 0.9 * pow(r, -0.2)));
+                    else fac = fmin(1.0, fmax(0.2, 0.9 * pow(r, -0.2)));
+                    if (accept) { s_[t] += ds_[t]; steps_[t]++; acc_flag[t] = 1; }
+                    double ds = ds_[t] * fac;
+                    if (!(s_[t] < a.s1)) done = 1;
+                    else {
+                        ds = fmin(ds, a.s1 - s_[t]);
+                        if (ds < 1e-14 * fmax(1.0, fabs(s_[t]))) { status[t] = CUT_ERR_STEP_UNDERFLOW; done = 1; }
+                        else if (attempts_[t] >= a.max_steps) { status[t] = CUT_ERR_MAX_STEPS; done = 1; }
+                        ds_[t] = ds;
+                    }
+                }
+                if (done) {
+                    a.steps_out[inst[t]] = (int)steps_[t];
+                    a.status_out[inst[t]] = status[t];
+                    acc_flag[t] |= 2;   // write back after the accept copy
+                }
+            }
+        }
+        __syncthreads();
+        // ---- accept: Y <- Y5 (and K1 <- K7 under FSAL); write back finished slots
+        for (int64_t e = threadIdx.x; e < L * TILE; e += kThreads) {
+            const int b = (int)(e % TILE);
+            if (acc_flag[b] & 1) {
+                Y[e] = Y5[e];
+                if (tb.adaptive) Kst(0)[e] = Kst(S - 1)[e];
+            }
+            if (acc_flag[b] & 2) {
+                const int64_t row = e / TILE, o = row / n, k = row % n;
+                const int64_t i = inst[b];
+                if (o == 0) a.H[i * n + k] = Y[e];
+                else a.X[(i * (NOPS - 1) + (o - 1)) * n + k] = Y[e];
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < TILE && (acc_flag[threadIdx.x] & 2)) inst[threadIdx.x] = -1;
+        __syncthreads();
+    }
+}
+
+}  // namespace kb
+
+// ------------------------------------------------------------------ host side
+struct BatchedGraphView {
+    const uint64_t *rp0, *rp1;
+    const uint2 *rec0, *rec1;
+    const double *wtab;
+    int n_codes;
+    int64_t n, n_g;
+    const unsigned char *sha;
+};
+
+template <typename T, int TILE, int NOPS>
+static size_t smem_bytes(const BatchedGraphView &v) {
+    return sizeof(T) * TILE * ((size_t)NOPS * v.n + v.n_g) + 256 * sizeof(T) + kb::kThreads * sizeof(double);
+}
+
+template <typename T, int TILE, int NOPS>
+static size_t ws_bytes(const BatchedGraphView &v) {
+    size_t L = (size_t)NOPS * v.n * TILE;
+    size_t b = L * (2 * sizeof(double) + 8 * sizeof(T));
+    return (b + 255) & ~size_t(255);
+}
+
+template <typename T, int TILE, int NOPS>
+static cudaError_t launch_tile(const BatchedGraphView &v, kb::Args args, int max_ctas, cudaStream_t s,
+                               void **ws_base, size_t *ws_cap, int *ctas_out) {
+    size_t sm = smem_bytes<T, TILE, NOPS>(v);
+    auto kern = kb::flow_batched_kernel<T, TILE, NOPS>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    int dev = 0, nsm = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kb::kThreads, sm);
+    if (e != cudaSuccess) return e;
+    if (per < 1) return cudaErrorInvalidConfiguration;
+    int ctas = std::min<int64_t>((args.B + TILE - 1) / TILE, (int64_t)nsm * per);
+    if (max_ctas > 0) ctas = std::min(ctas, max_ctas);
+    size_t need = ws_bytes<T, TILE, NOPS>(v) * ctas;
+    if (need > *ws_cap) {
+        if (*ws_base) cudaFreeAsync(*ws_base, s);
+        e = cudaMallocAsync(ws_base, need, s);
+        if (e != cudaSuccess) return e;
+        *ws_cap = need;
+    }
+    args.ws = (double *)*ws_base;
+    args.ws_stride = (int64_t)ws_bytes<T, TILE, NOPS>(v);
+    if (ctas_out) *ctas_out = ctas;
+    kern<<<ctas, kb::kThreads, sm, s>>>(args);
+    return cudaGetLastError();
+}
+
+typedef cudaError_t (*LaunchFn)(const BatchedGraphView &, kb::Args, int, cudaStream_t, void **, size_t *, int *);
+
+template <typename T, int NOPS>
+static LaunchFn pick(int tile) {
+    switch (tile) {
+        case 2: return launch_tile<T, 2, NOPS>;
+        case 4: return launch_tile<T, 4, NOPS>;
+        case 8: return launch_tile<T, 8, NOPS>;
+        case 16: return launch_tile<T, 16, NOPS>;
+        case 32: return launch_tile<T, 32, NOPS>;
+    }
+    return nullptr;
+}
+
+static LaunchFn pick_any(bool fp32, int nops, int tile) {
+    if (fp32) {
+        switch (nops) {
+            case 1: return pick<float, 1>(tile);
+            case 2: return pick<float, 2>(tile);
+            case 3: return pick<float, 3>(tile);
+            case 4: return pick<float, 4>(tile);
+        }
+    } else {
+        switch (nops) {
+            case 1: return pick<double, 1>(tile);
+            case 2: return pick<double, 2>(tile);
+            case 3: return pick<double, 3>(tile);
+            case 4: return pick<double, 4>(tile);
+        }
+    }
+    return nullptr;
+}
+
+static size_t smem_for(bool fp32, int nops, int tile, const BatchedGraphView &v) {
+    size_t e = fp32 ? 4 : 8;
+    return e * tile * ((size_t)nops * v.n + v.n_g) + 256 * e + kb::kThreads * 8;  // matches smem_bytes
+}
+
+static kb::Tableau make_tableau(int method) {
+    kb::Tableau t;
+    memset(&t, 0, sizeof(t));
+    if (method == CUT_RK4) {
+        t.stages = 4;
+        t.adaptive = 0;
+        t.a[1][0] = 0.5;
+        t.a[2][1] = 0.5;
+        t.a[3][2] = 1.0;
+        t.b[0] = 1.0 / 6; t.b[1] = 1.0 / 3; t.b[2] = 1.0 / 3; t.b[3] = 1.0 / 6;
+        return t;
+    }
+    // Dormand & Prince (1980) 5(4); stage 7 is evaluated at Y5 (FSAL)
+    static const double A[7][6] = {
+        {0, 0, 0, 0, 0, 0},
+        {1.0 / 5, 0, 0, 0, 0, 0},
+        {3.0 / 40, 9.0 / 40, 0, 0, 0, 0},
+        {44.0 / 45, -56.0 / 15, 32.0 / 9, 0, 0, 0},
+        {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729, 0, 0},
+        {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656, 0},
+        {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84}};
+    static const double Bv[7] = {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84, 0};
+    static const double Bs[7] = {5179.0 / 57600, 0, 7571.0 / 16695, 393.0 / 640, -92097.0 / 339200,
+                                 187.0 / 2100, 1.0 / 40};
+    t.stages = 7;
+    t.adaptive = 1;
+    for (int i = 0; i < 7; i++) {
+        for (int j = 0; j < 6; j++) t.a[i][j] = A[i][j];
+        t.b[i] = Bv[i];
+        t.e[i] = Bv[i] - Bs[i];
+    }
+    return t;
+}
+
+// Tile width chosen per (graph, batch, operands, precision, method) by timing
+// a two-attempt probe of every width that fits in shared memory.
+static std::mutex g_tune_mu;
+static std::map<std::tuple<std::string, int, int, int, int>, int> g_tune;
+
+cut_status flow_batched_impl(const BatchedGraphView &v, int device, int batch, double *h, int n_obs, double *x,
+                             int precision, const cut_flow_opts *o, int tile, int *steps_out, int *status_out,
+                             cudaStream_t user, int *chosen_tile) {
+    const int nops = n_obs + 1;
+    const bool fp32 = precision == CUT_FP32REC_FP64STATE;
+    int dev_smem = 0;
+    cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    std::vector<int> cands;
+    for (int t : {2, 4, 8, 16, 32})
+        if (smem_for(fp32, nops, t, v) <= (size_t)dev_smem - 1024) cands.push_back(t);
+    if (cands.empty()) return set_error(CUT_ERR_UNSUPPORTED, "cut_flow_batched: registry too large for the shared-memory tile");
+    if (tile != 0 && std::find(cands.begin(), cands.end(), tile) == cands.end())
+        return set_error(CUT_ERR_INVALID_ARG, "cut_flow_batched: tile must be one of 2,4,8,16,32 and fit in shared memory");
+
+    kb::Args a;
+    memset(&a, 0, sizeof(a));
+    a.rp0 = v.rp0; a.rp1 = v.rp1; a.rec0 = v.rec0; a.rec1 = v.rec1;
+    a.wtab = v.wtab; a.n_codes = v.n_codes; a.n = v.n; a.n_g = v.n_g;
+    a.nops = nops; a.B = batch;
+    a.s0 = o->s0; a.s1 = o->s1; a.rtol = o->rtol; a.atol = o->atol;
+    a.tb = make_tableau(o->method);
+    if (o->method == CUT_RK4) {
+        int64_t N = (int64_t)llround((o->s1 - o->s0) / o->ds);
+        if (N < 1) N = 1;
+        a.ds0 = (o->s1 - o->s0) / (double)N;
+        a.max_steps = N;
+    } else {
+        a.ds0 = o->ds;
+        a.max_steps = o->max_steps > 0 ? o->max_steps : 1000000;
+    }
+    cudaStream_t s;
+    cudaEvent_t ev;
+    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    cudaEventRecord(ev, user);
+    cudaStreamWaitEvent(s, ev, 0);
+    void *ws = nullptr;
+    size_t ws_cap = 0;
+    int *queue = nullptr;
+    cudaError_t e = cudaMallocAsync(&queue, 256, s);
+    auto finish = [&](cut_status st) {
+        if (ws) cudaFreeAsync(ws, s);
+        if (queue) cudaFreeAsync(queue, s);
+        cudaEventRecord(ev, s);
+        cudaStreamWaitEvent(user, ev, 0);
+        cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+        cudaEventDestroy(ev);
+        return st;
+    };
+    if (e != cudaSuccess) return finish(set_error(CUT_ERR_OUT_OF_MEMORY, "cut_flow_batched: queue"));
+    a.queue = queue;
+    a.steps_out = steps_out;
+    a.status_out = status_out;
+
+    if (tile == 0) {
+        auto key = std::make_tuple(std::string((const char *)v.sha, 32), batch, nops, (int)fp32, o->method);
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune.find(key);
+            if (it != g_tune.end()) tile = it->second;
+        }
+        if (tile == 0) {
+            // probe on scratch copies so the caller's state is untouched
+            double *hc = nullptr, *xc = nullptr;
+            int *so = nullptr;
+            size_t hb = (size_t)batch * v.n * 8, xb = (size_t)batch * n_obs * v.n * 8;
+            e = cudaMallocAsync(&hc, hb + xb + 2 * (size_t)batch * 4 + 64, s);
+            if (e != cudaSuccess) return finish(set_error(CUT_ERR_OUT_OF_MEMORY, "cut_flow_batched: autotune scratch"));
+            xc = hc + (size_t)batch * v.n;
+            so = (int *)(xc + (size_t)batch * n_obs * v.n);
+            cudaEvent_t t0, t1;
+            cudaEventCreate(&t0);
+            cudaEventCreate(&t1);
+            float best = 1e30f;
+            for (int t : cands) {
+                cudaMemcpyAsync(hc, h, hb, cudaMemcpyDeviceToDevice, s);
+                if (n_obs) cudaMemcpyAsync(xc, x, xb, cudaMemcpyDeviceToDevice, s);
+                cudaMemsetAsync(queue, 0, 4, s);
+                kb::Args p = a;
+                p.H = hc; p.X = xc; p.steps_out = so; p.status_out = so + batch;
+                p.probe_attempts = 2;
+                int ctas = 0;
+                cudaEventRecord(t0, s);
+                e = pick_any(fp32, nops, t)(v, p, 0, s, &ws, &ws_cap, &ctas);
+                cudaEventRecord(t1, s);
+                cudaEventSynchronize(t1);
+                if (e != cudaSuccess) { cudaGetLastError(); continue; }
+                float ms = 0;
+                cudaEventElapsedTime(&ms, t0, t1);
+                // time per instance-attempt: every resident slot ran two attempts
+                const double inflight = std::min<double>(batch, (double)ctas * t);
+                const float norm = (float)(ms / inflight);
+                if (norm < best) { best = norm; tile = t; }
+            }
+            cudaEventDestroy(t0);
+            cudaEventDestroy(t1);
+            cudaFreeAsync(hc, s);
+            if (tile == 0) return finish(set_error(CUT_ERR_CUDA, "cut_flow_batched: no tile width ran"));
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tune[key] = tile;
+        }
+    }
+    if (chosen_tile) *chosen_tile = tile;
+    a.H = h;
+    a.X = x;
+    cudaMemsetAsync(queue, 0, 4, s);
+    e = pick_any(fp32, nops, tile)(v, a, 0, s, &ws, &ws_cap, nullptr);
+    if (e != cudaSuccess) return finish(set_error(CUT_ERR_CUDA, std::string("cut_flow_batched: ") + cudaGetErrorString(e)));
+    cut_status st = finish(CUT_OK);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(CUT_ERR_CUDA, std::string("cut_flow_batched: ") + cudaGetErrorString(e));
+    return st;
+}
+
+}  // namespace cut

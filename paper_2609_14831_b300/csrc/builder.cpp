@@ -22,6 +22,7 @@
 #include <stdexcept>
 #include <string>
 #include <thread>
+#include <unordered_map>
 #include <unordered_set>
 #include <vector>
 
@@ -125,6 +126,8 @@ struct Ctx {
     std::vector<uint64_t> labels;
     std::vector<int32_t> diag_idx, off_idx;
     std::vector<std::vector<int32_t>> byC, byA;  // fermion: operands with p in C / in A
+    std::unordered_map<uint32_t, std::vector<int32_t>> byCset, byAset;  // operands by exact C / A set
+    int reg_rank = 0;                            // highest rank in the registry
     LabelIndex *reg = nullptr;
 };
 
@@ -162,6 +165,25 @@ void comm_terms(const Ctx &c, const std::vector<uint64_t> &gl, int64_t lo, int64
         };
         if (c.alg == 0) {
             for (int32_t j = 0; j < n; j++) visit(j);
+        } else if (popc(lo32(G)) >= c.reg_rank) {
+            // A generator of the registry's top rank r: a term of G O_j has
+            // rank r + r_j - |K| with K the contracted part of C_j, so it stays
+            // within rank r only if every creator of O_j is contracted
+            // (C_j subset of A_G); likewise A_j subset of C_G for O_j G.
+            int32_t tag = (int32_t)a;
+            uint32_t Ag = hi32(G), Cg = lo32(G);
+            for (uint32_t S = Ag; S; S = (S - 1) & Ag) {
+                auto it = c.byCset.find(S);
+                if (it != c.byCset.end())
+                    for (int32_t j : it->second)
+                        if (stamp[j] != tag) { stamp[j] = tag; visit(j); }
+            }
+            for (uint32_t S = Cg; S; S = (S - 1) & Cg) {
+                auto it = c.byAset.find(S);
+                if (it != c.byAset.end())
+                    for (int32_t j : it->second)
+                        if (stamp[j] != tag) { stamp[j] = tag; visit(j); }
+            }
         } else {
             // [G, O_j] vanishes unless an annihilator of G meets a creator of
             // O_j or a creator of G meets an annihilator of O_j.
@@ -234,6 +256,7 @@ void build_graph(const cut_build_opts &o, int64_t n, const uint64_t *labels, Hos
         reg_rank = std::max(reg_rank, rank_of(c.alg, l));
     }
     c.max_rank = o.max_rank > 0 ? o.max_rank : reg_rank;
+    c.reg_rank = reg_rank;
     LabelIndex reg(c.labels);
     c.reg = &reg;
     for (int32_t i = 0; i < (int32_t)n; i++) (is_diagonal(c.alg, c.labels[i]) ? c.diag_idx : c.off_idx).push_back(i);
@@ -243,6 +266,8 @@ void build_graph(const cut_build_opts &o, int64_t n, const uint64_t *labels, Hos
         for (int32_t j = 0; j < (int32_t)n; j++) {
             for (uint32_t s = lo32(c.labels[j]); s; s &= s - 1) c.byC[__builtin_ctz(s)].push_back(j);
             for (uint32_t s = hi32(c.labels[j]); s; s &= s - 1) c.byA[__builtin_ctz(s)].push_back(j);
+            c.byCset[lo32(c.labels[j])].push_back(j);
+            c.byAset[hi32(c.labels[j])].push_back(j);
         }
     }
     const int T = c.threads;

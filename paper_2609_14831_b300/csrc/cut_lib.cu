@@ -800,7 +800,34 @@ extern "C" cut_status cut_flow_vjp(const cut_graph *g, const double *h0, int n_o
     return set_ok();
 }
 
-extern "C" cut_status cut_flow_batched(const cut_graph *, int, double *, int, double *, int, const cut_flow_opts *,
-                                       int, int *, int *, cut_stream_t) {
-    return set_error(CUT_ERR_UNSUPPORTED, "cut_flow_batched: not built yet");
+// ----------------------------------------------------------------- batched
+namespace cut {
+struct BatchedGraphView {
+    const uint64_t *rp0, *rp1;
+    const uint2 *rec0, *rec1;
+    const double *wtab;
+    int n_codes;
+    int64_t n, n_g;
+    const unsigned char *sha;
+};
+cut_status flow_batched_impl(const BatchedGraphView &v, int device, int batch, double *h, int n_obs, double *x,
+                             int precision, const cut_flow_opts *o, int tile, int *steps_out, int *status_out,
+                             cudaStream_t user, int *chosen_tile);
+static thread_local int g_last_tile = 0;
+}  // namespace cut
+
+extern "C" cut_status cut_flow_batched(const cut_graph *g, int batch, double *h, int n_obs, double *x, int precision,
+                                       const cut_flow_opts *o, int tile, int *steps_out, int *status_out,
+                                       cut_stream_t stream) {
+    if (!g || g->device < 0 || batch < 1 || !h || n_obs < 0 || n_obs > 3 || (n_obs > 0 && !x) || !steps_out ||
+        !status_out || (precision != CUT_FP64 && precision != CUT_FP32REC_FP64STATE) || tile < 0)
+        return set_error(CUT_ERR_INVALID_ARG, "cut_flow_batched: bad argument (n_obs <= 3)");
+    cut_status st = check_opts(o);
+    if (st != CUT_OK) return st;
+    if (o->replay_steps) return set_error(CUT_ERR_INVALID_ARG, "cut_flow_batched: replay is not supported");
+    DeviceGuard dg(g->device);
+    BatchedGraphView v{g->st[0].rp, g->st[1].rp, g->st[0].rec, g->st[1].rec, g->wtab,
+                       (int)g->host.num.size(), g->host.n(), g->host.n_g(), g->host.sha};
+    return flow_batched_impl(v, g->device, batch, h, n_obs, x, precision, o, tile, steps_out, status_out,
+                             (cudaStream_t)stream, &g_last_tile);
 }

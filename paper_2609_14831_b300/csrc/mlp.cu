@@ -1,0 +1,494 @@
+// mlp.cu -- the learned surrogate: an MLP n_in -> H -> H -> n_out with GELU,
+// BF16 operands and FP32 accumulation on the tcgen05 tensor cores, trained by
+// the library's own forward, backward and AdamW kernels.  It maps a
+// Hamiltonian parameter vector to the flowed coefficients (a warm start and a
+// screen; the graph flow stays the fallback and the judge of its error).
+//
+// Layouts (rows padded to 128, feature dimensions padded to 64 / 128):
+//   W_l  bf16 [out_l][in_l]   forward B operand (C = X W^T)
+//   W_l^T bf16 [in_l][out_l]  backward B operand (dX = dZ W)
+//   activations bf16 [M][f] and their transposes [f][M] (dW = dZ^T X),
+//   written by the GEMM epilogues directly.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "cut.h"
+#include "status.h"
+#include "tc_gemm.cuh"
+
+using bf16 = __nv_bfloat16;
+
+namespace cut {
+namespace mlpk {
+
+__global__ void pack_input(const float *__restrict__ x, int batch, int n_in, int in_p, int Mp, bf16 *__restrict__ xb,
+                           bf16 *__restrict__ xt) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)Mp * in_p;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int m = (int)(e / in_p), c = (int)(e % in_p);
+        const float v = (m < batch && c < n_in) ? x[(int64_t)m * n_in + c] : 0.0f;
+        const bf16 b = __float2bfloat16(v);
+        xb[e] = b;
+        xt[(int64_t)c * Mp + m] = b;
+    }
+}
+
+// dZ = 2 (Y - (T - shift) / scale) / (batch n_out) on valid entries; loss sum
+__global__ void mse_grad(const float *__restrict__ Y, int ldy, const float *__restrict__ T, int batch, int n_out,
+                         const float *__restrict__ scale, const float *__restrict__ shift, int Mp, int Np,
+                         bf16 *__restrict__ dz, bf16 *__restrict__ dzt, float *__restrict__ dz32,
+                         float *__restrict__ loss) {
+    __shared__ float red[256];
+    float acc = 0.0f;
+    const float inv = 1.0f / ((float)batch * (float)n_out);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)Mp * Np;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int m = (int)(e / Np), c = (int)(e % Np);
+        float g = 0.0f;
+        if (m < batch && c < n_out) {
+            const float t = (T[(int64_t)m * n_out + c] - shift[c]) / scale[c];
+            const float r = Y[(int64_t)m * ldy + c] - t;
+            acc += r * r;
+            g = 2.0f * r * inv;
+        }
+        dz[e] = __float2bfloat16(g);
+        dzt[(int64_t)c * Mp + m] = __float2bfloat16(g);
+        dz32[e] = g;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && loss) atomicAdd(loss, red[0] * inv);
+}
+
+// db[c] = sum_m dz[m][c] (valid rows)
+__global__ void col_sum(const float *__restrict__ dz, int ld, int rows, int cols, float *__restrict__ db) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+    float s = 0.0f;
+    for (int m = 0; m < rows; m++) s += dz[(int64_t)m * ld + c];
+    db[c] = s;
+}
+
+// AdamW (Loshchilov & Hutter): decoupled weight decay; refreshes the BF16
+// copies W and W^T.  Parameters are [out][in] (bias: in = 1, no transpose).
+__global__ void adamw(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m, float *__restrict__ v,
+                      int64_t count, int in_p, float lr, float b1, float b2, float eps, float wd, float bc1, float bc2,
+                      bf16 *__restrict__ wb, bf16 *__restrict__ wt, int out_p) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+        const float gr = g[e];
+        const float mm = b1 * m[e] + (1.0f - b1) * gr;
+        const float vv = b2 * v[e] + (1.0f - b2) * gr * gr;
+        m[e] = mm;
+        v[e] = vv;
+        float x = w[e];
+        x -= lr * ((mm / bc1) / (sqrtf(vv / bc2) + eps) + wd * x);
+        w[e] = x;
+        if (wb) {
+            const bf16 b = __float2bfloat16(x);
+            wb[e] = b;
+            if (wt) wt[(e % in_p) * (int64_t)out_p + e / in_p] = b;
+        }
+    }
+}
+
+__global__ void to_bf16(const float *__restrict__ w, int64_t count, int in_p, int out_p, bf16 *__restrict__ wb,
+                        bf16 *__restrict__ wt) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+        const bf16 b = __float2bfloat16(w[e]);
+        wb[e] = b;
+        wt[(e % in_p) * (int64_t)out_p + e / in_p] = b;
+    }
+}
+
+}  // namespace mlpk
+
+static int pad_to(int v, int q) { return (v + q - 1) / q * q; }
+
+// The tensor-map encoder is a driver entry point; it is fetched through the
+// runtime so that the library loads on machines without a driver.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+static cut_status make_map(CUtensorMap *map, const void *ptr, int rows, int cols, int box_rows) {
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return set_error(CUT_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides,
+                                        box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(CUT_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return CUT_OK;
+}
+
+// C[M][N] = A[M][K] B[N][K]^T, M % 128 == 0, N % 64 == 0, K % 64 == 0
+static cut_status gemm(const bf16 *A, const bf16 *B, int M, int N, int K, tc::Epi ep, cudaStream_t s) {
+    if (M % 128 || N % 64 || K % 64) return set_error(CUT_ERR_INVALID_ARG, "gemm: shape not padded");
+    CUtensorMap ma, mb;
+    const int bn = (N % 128 == 0) ? 128 : 64;
+    cut_status st = make_map(&ma, A, M, K, 128);
+    if (st != CUT_OK) return st;
+    st = make_map(&mb, B, N, K, bn);
+    if (st != CUT_OK) return st;
+    dim3 grid(M / 128, N / bn);
+    if (bn == 128) {
+        auto k = tc::gemm_bf16_tn<128>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::gemm_smem_bytes<128>());
+        k<<<grid, tc::kThreads, tc::gemm_smem_bytes<128>(), s>>>(ma, mb, K, ep);
+    } else {
+        auto k = tc::gemm_bf16_tn<64>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::gemm_smem_bytes<64>());
+        k<<<grid, tc::kThreads, tc::gemm_smem_bytes<64>(), s>>>(ma, mb, K, ep);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(CUT_ERR_CUDA, std::string("gemm launch: ") + cudaGetErrorString(e));
+    return CUT_OK;
+}
+
+static tc::Epi epi0(int M, int N, int *err) {
+    tc::Epi e;
+    memset(&e, 0, sizeof(e));
+    e.alpha = 1.0f;
+    e.M = M;
+    e.N = N;
+    e.err = err;
+    return e;
+}
+
+}  // namespace cut
+
+using namespace cut;
+
+struct Layer {
+    int in, out, in_p, out_p;
+    float *w = nullptr, *b = nullptr, *gw = nullptr, *gb = nullptr;   // fp32 master and grads
+    float *mw = nullptr, *vw = nullptr, *mb = nullptr, *vb = nullptr;  // Adam moments
+    bf16 *wb = nullptr, *wt = nullptr;                                 // bf16 W, W^T
+};
+
+struct cut_mlp {
+    int device = 0, n_in = 0, n_hid = 0, n_out = 0;
+    Layer L[3];
+    float *scale = nullptr, *shift = nullptr;   // output affine (targets standardised)
+    int *err = nullptr;
+    long long t = 0;                            // Adam step
+    // activations for the largest padded batch seen
+    int Mcap = 0;
+    bf16 *xb = nullptr, *xt = nullptr;
+    float *z[3] = {nullptr, nullptr, nullptr};  // pre-activations fp32 [M][out_p]
+    bf16 *hb[2] = {nullptr, nullptr}, *ht[2] = {nullptr, nullptr};
+    bf16 *dzb = nullptr, *dzt = nullptr;        // scratch for the current layer's dZ
+    float *dz32 = nullptr;
+    bf16 *dzb2 = nullptr, *dzt2 = nullptr;
+    float *dz32b = nullptr;
+    std::vector<void *> allocs;
+    ~cut_mlp() {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        cudaSetDevice(device);
+        for (void *p : allocs) cudaFree(p);
+        cudaSetDevice(cur);
+    }
+    template <class T>
+    cudaError_t alloc(T **p, size_t count) {
+        cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+        if (e == cudaSuccess) {
+            allocs.push_back(*p);
+            cudaMemset(*p, 0, count * sizeof(T));
+        }
+        return e;
+    }
+};
+
+static uint64_t splitmix(uint64_t &s) {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static cut_status ensure_batch(cut_mlp *m, int Mp) {
+    if (Mp <= m->Mcap) return CUT_OK;
+    const int H = m->L[0].out_p, O = m->L[2].out_p, I = m->L[0].in_p;
+    const int F = std::max(std::max(H, O), I);
+    bool ok = m->alloc(&m->xb, (size_t)Mp * I) == cudaSuccess && m->alloc(&m->xt, (size_t)Mp * I) == cudaSuccess;
+    for (int l = 0; l < 3 && ok; l++) ok = m->alloc(&m->z[l], (size_t)Mp * m->L[l].out_p) == cudaSuccess;
+    for (int l = 0; l < 2 && ok; l++)
+        ok = m->alloc(&m->hb[l], (size_t)Mp * H) == cudaSuccess && m->alloc(&m->ht[l], (size_t)Mp * H) == cudaSuccess;
+    ok = ok && m->alloc(&m->dzb, (size_t)Mp * F) == cudaSuccess && m->alloc(&m->dzt, (size_t)Mp * F) == cudaSuccess &&
+         m->alloc(&m->dz32, (size_t)Mp * F) == cudaSuccess && m->alloc(&m->dzb2, (size_t)Mp * F) == cudaSuccess &&
+         m->alloc(&m->dzt2, (size_t)Mp * F) == cudaSuccess && m->alloc(&m->dz32b, (size_t)Mp * F) == cudaSuccess;
+    if (!ok) return set_error(CUT_ERR_OUT_OF_MEMORY, "cut_mlp: activation buffers");
+    m->Mcap = Mp;
+    return CUT_OK;
+}
+
+static int grid_of(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 148 * 8)); }
+
+// forward: Z_l, H_l (bf16 + transposes); returns the output pre-affine in z[2]
+static cut_status forward(cut_mlp *m, int batch, const float *x, cudaStream_t s, const float *post_scale,
+                          const float *post_shift, float *y_out) {
+    const int Mp = pad_to(batch, 128);
+    cut_status st = ensure_batch(m, Mp);
+    if (st != CUT_OK) return st;
+    mlpk::pack_input<<<grid_of((int64_t)Mp * m->L[0].in_p), 256, 0, s>>>(x, batch, m->n_in, m->L[0].in_p, Mp, m->xb,
+                                                                          m->xt);
+    const bf16 *in = m->xb;
+    for (int l = 0; l < 3; l++) {
+        Layer &Ly = m->L[l];
+        tc::Epi e = epi0(Mp, Ly.out_p, m->err);
+        e.bias = Ly.b;
+        e.out_f32 = m->z[l];
+        e.ld_f32 = Ly.out_p;
+        if (l < 2) {
+            e.act = 1;
+            e.out_bf16 = m->hb[l];
+            e.ld_bf16 = Ly.out_p;
+            e.out_t = m->ht[l];
+            e.ld_t = Mp;
+        } else if (y_out) {
+            // inference: valid region only, with the output affine
+            e.M = batch;
+            e.N = m->n_out;
+            e.post_scale = post_scale;
+            e.post_shift = post_shift;
+            e.out_f32 = y_out;
+            e.ld_f32 = m->n_out;
+        }
+        st = gemm(in, Ly.wb, Mp, Ly.out_p, Ly.in_p, e, s);
+        if (st != CUT_OK) return st;
+        if (l < 2) in = m->hb[l];
+    }
+    return CUT_OK;
+}
+
+extern "C" {
+
+cut_status cut_mlp_create(int n_in, int n_hidden, int n_out, uint64_t seed, int device, cut_mlp **out) {
+    if (!out || n_in < 1 || n_hidden < 1 || n_out < 1 || n_in > 4096 || n_hidden > 4096 || n_out > 65536)
+        return set_error(CUT_ERR_INVALID_ARG, "cut_mlp_create: bad sizes");
+    std::unique_ptr<cut_mlp> m(new cut_mlp());
+    m->device = device;
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) return set_error(CUT_ERR_INVALID_ARG, "cut_mlp_create: bad device");
+    m->n_in = n_in;
+    m->n_hid = n_hidden;
+    m->n_out = n_out;
+    const int dims[4] = {n_in, n_hidden, n_hidden, n_out};
+    uint64_t rs = seed;
+    for (int l = 0; l < 3; l++) {
+        Layer &Ly = m->L[l];
+        Ly.in = dims[l];
+        Ly.out = dims[l + 1];
+        Ly.in_p = pad_to(Ly.in, 64);
+        Ly.out_p = pad_to(Ly.out, 128);
+        const size_t cnt = (size_t)Ly.in_p * Ly.out_p;
+        bool ok = m->alloc(&Ly.w, cnt) == cudaSuccess && m->alloc(&Ly.gw, cnt) == cudaSuccess &&
+                  m->alloc(&Ly.mw, cnt) == cudaSuccess && m->alloc(&Ly.vw, cnt) == cudaSuccess &&
+                  m->alloc(&Ly.b, Ly.out_p) == cudaSuccess && m->alloc(&Ly.gb, Ly.out_p) == cudaSuccess &&
+                  m->alloc(&Ly.mb, Ly.out_p) == cudaSuccess && m->alloc(&Ly.vb, Ly.out_p) == cudaSuccess &&
+                  m->alloc(&Ly.wb, cnt) == cudaSuccess && m->alloc(&Ly.wt, cnt) == cudaSuccess;
+        if (!ok) return set_error(CUT_ERR_OUT_OF_MEMORY, "cut_mlp_create: parameters");
+        // uniform(-1/sqrt(in), 1/sqrt(in)) from a counter-based generator
+        std::vector<float> hw(cnt, 0.0f);
+        const float a = 1.0f / std::sqrt((float)Ly.in);
+        for (int o = 0; o < Ly.out; o++)
+            for (int i = 0; i < Ly.in; i++) {
+                const double u = (double)(splitmix(rs) >> 11) * (1.0 / 9007199254740992.0);
+                hw[(size_t)o * Ly.in_p + i] = (float)((2.0 * u - 1.0) * a);
+            }
+        cudaMemcpy(Ly.w, hw.data(), cnt * 4, cudaMemcpyHostToDevice);
+        mlpk::to_bf16<<<grid_of(cnt), 256>>>(Ly.w, cnt, Ly.in_p, Ly.out_p, Ly.wb, Ly.wt);
+    }
+    if (m->alloc(&m->scale, m->L[2].out_p) != cudaSuccess || m->alloc(&m->shift, m->L[2].out_p) != cudaSuccess ||
+        m->alloc(&m->err, 4) != cudaSuccess)
+        return set_error(CUT_ERR_OUT_OF_MEMORY, "cut_mlp_create: buffers");
+    std::vector<float> one(m->L[2].out_p, 1.0f);
+    cudaMemcpy(m->scale, one.data(), one.size() * 4, cudaMemcpyHostToDevice);
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return set_error(CUT_ERR_CUDA, std::string("cut_mlp_create: ") + cudaGetErrorString(e));
+    *out = m.release();
+    return set_ok();
+}
+
+cut_status cut_mlp_free(cut_mlp *m) {
+    delete m;
+    return set_ok();
+}
+
+cut_status cut_mlp_set_output_affine(cut_mlp *m, const float *scale, const float *shift) {
+    if (!m || !scale || !shift) return set_error(CUT_ERR_INVALID_ARG, "cut_mlp_set_output_affine: null argument");
+    for (int c = 0; c < m->n_out; c++)
+        if (!(scale[c] > 0.0f) || !std::isfinite(shift[c]))
+            return set_error(CUT_ERR_INVALID_ARG, "cut_mlp_set_output_affine: scale must be > 0, shift finite");
+    cudaSetDevice(m->device);
+    cudaMemcpy(m->scale, scale, m->n_out * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(m->shift, shift, m->n_out * 4, cudaMemcpyHostToDevice);
+    return set_ok();
+}
+
+int64_t cut_mlp_param_count(const cut_mlp *m) {
+    if (!m) return -1;
+    int64_t c = 0;
+    for (int l = 0; l < 3; l++) c += (int64_t)m->L[l].in * m->L[l].out + m->L[l].out;
+    return c;
+}
+
+// Copy parameters (or their gradients, which = 1) between the device and a
+// flat host array W1, b1, W2, b2, W3, b3 (W row-major [out][in]).
+static cut_status params_io(cut_mlp *m, float *host, int to_host, int which) {
+    cudaSetDevice(m->device);
+    int64_t off = 0;
+    for (int l = 0; l < 3; l++) {
+        Layer &Ly = m->L[l];
+        float *W = which ? Ly.gw : Ly.w;
+        float *B = which ? Ly.gb : Ly.b;
+        for (int o = 0; o < Ly.out; o++) {
+            cudaError_t e = to_host ? cudaMemcpy(host + off, W + (size_t)o * Ly.in_p, Ly.in * 4, cudaMemcpyDeviceToHost)
+                                    : cudaMemcpy(W + (size_t)o * Ly.in_p, host + off, Ly.in * 4, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return set_error(CUT_ERR_CUDA, "cut_mlp params copy");
+            off += Ly.in;
+        }
+        cudaError_t e = to_host ? cudaMemcpy(host + off, B, Ly.out * 4, cudaMemcpyDeviceToHost)
+                                : cudaMemcpy(B, host + off, Ly.out * 4, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return set_error(CUT_ERR_CUDA, "cut_mlp params copy");
+        off += Ly.out;
+        if (!to_host && !which) {
+            const size_t cnt = (size_t)Ly.in_p * Ly.out_p;
+            mlpk::to_bf16<<<grid_of(cnt), 256>>>(Ly.w, cnt, Ly.in_p, Ly.out_p, Ly.wb, Ly.wt);
+        }
+    }
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return set_error(CUT_ERR_CUDA, std::string("cut_mlp params: ") + cudaGetErrorString(e));
+    return set_ok();
+}
+
+cut_status cut_mlp_get_params(cut_mlp *m, float *host, int grads) {
+    if (!m || !host) return set_error(CUT_ERR_INVALID_ARG, "cut_mlp_get_params: null argument");
+    return params_io(m, host, 1, grads ? 1 : 0);
+}
+
+cut_status cut_mlp_set_params(cut_mlp *m, const float *host) {
+    if (!m || !host) return set_error(CUT_ERR_INVALID_ARG, "cut_mlp_set_params: null argument");
+    return params_io(m, const_cast<float *>(host), 0, 0);
+}
+
+cut_status cut_mlp_forward(cut_mlp *m, int batch, const float *x, float *y, cut_stream_t stream) {
+    if (!m || batch < 1 || !x || !y) return set_error(CUT_ERR_INVALID_ARG, "cut_mlp_forward: bad argument");
+    cudaSetDevice(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cut_status st = forward(m, batch, x, s, m->scale, m->shift, y);
+    if (st != CUT_OK) return st;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(CUT_ERR_CUDA, std::string("cut_mlp_forward: ") + cudaGetErrorString(e));
+    return set_ok();
+}
+
+cut_status cut_mlp_backward(cut_mlp *m, int batch, const float *x, const float *target, float *loss,
+                            cut_stream_t stream) {
+    if (!m || batch < 1 || !x || !target) return set_error(CUT_ERR_INVALID_ARG, "cut_mlp_backward: bad argument");
+    cudaSetDevice(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cut_status st = forward(m, batch, x, s, nullptr, nullptr, nullptr);
+    if (st != CUT_OK) return st;
+    const int Mp = pad_to(batch, 128);
+    Layer *L = m->L;
+    // output layer
+    mlpk::mse_grad<<<grid_of((int64_t)Mp * L[2].out_p), 256, 0, s>>>(m->z[2], L[2].out_p, target, batch, m->n_out,
+                                                                       m->scale, m->shift, Mp, L[2].out_p, m->dzb,
+                                                                       m->dzt, m->dz32, loss);
+    bf16 *dzb = m->dzb, *dzt = m->dzt, *nb = m->dzb2, *nt = m->dzt2;
+    float *dz32 = m->dz32, *n32 = m->dz32b;
+    for (int l = 2; l >= 0; l--) {
+        Layer &Ly = L[l];
+        // dW_l[out][in] = dZ^T[out][M] * IN^T[in][M]^T
+        const bf16 *inT = l == 0 ? m->xt : m->ht[l - 1];
+        tc::Epi e = epi0(Ly.out_p, Ly.in_p, m->err);
+        e.out_f32 = Ly.gw;
+        e.ld_f32 = Ly.in_p;
+        st = gemm(dzt, inT, Ly.out_p, Ly.in_p, Mp, e, s);
+        if (st != CUT_OK) return st;
+        mlpk::col_sum<<<(Ly.out_p + 255) / 256, 256, 0, s>>>(dz32, Ly.out_p, batch, Ly.out_p, Ly.gb);
+        if (l == 0) break;
+        // dZ_{l-1} = (dZ_l W_l) * GELU'(Z_{l-1})
+        Layer &Lp = L[l - 1];
+        tc::Epi d = epi0(Mp, Lp.out_p, m->err);
+        d.dgelu_z = m->z[l - 1];
+        d.ldz = Lp.out_p;
+        d.out_f32 = n32;
+        d.ld_f32 = Lp.out_p;
+        d.out_bf16 = nb;
+        d.ld_bf16 = Lp.out_p;
+        d.out_t = nt;
+        d.ld_t = Mp;
+        st = gemm(dzb, Ly.wt, Mp, Lp.out_p, Ly.out_p, d, s);
+        if (st != CUT_OK) return st;
+        std::swap(dzb, nb);
+        std::swap(dzt, nt);
+        std::swap(dz32, n32);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(CUT_ERR_CUDA, std::string("cut_mlp_backward: ") + cudaGetErrorString(e));
+    return set_ok();
+}
+
+cut_status cut_mlp_adamw_step(cut_mlp *m, float lr, float beta1, float beta2, float eps, float weight_decay,
+                              cut_stream_t stream) {
+    if (!m || !(lr >= 0) || !(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1) || !(eps > 0))
+        return set_error(CUT_ERR_INVALID_ARG, "cut_mlp_adamw_step: bad hyper-parameters");
+    cudaSetDevice(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    m->t++;
+    const float bc1 = 1.0f - (float)std::pow((double)beta1, (double)m->t);
+    const float bc2 = 1.0f - (float)std::pow((double)beta2, (double)m->t);
+    for (int l = 0; l < 3; l++) {
+        Layer &Ly = m->L[l];
+        const int64_t cnt = (int64_t)Ly.in_p * Ly.out_p;
+        mlpk::adamw<<<grid_of(cnt), 256, 0, s>>>(Ly.w, Ly.gw, Ly.mw, Ly.vw, cnt, Ly.in_p, lr, beta1, beta2, eps,
+                                                 weight_decay, bc1, bc2, Ly.wb, Ly.wt, Ly.out_p);
+        mlpk::adamw<<<grid_of(Ly.out_p), 256, 0, s>>>(Ly.b, Ly.gb, Ly.mb, Ly.vb, Ly.out_p, 1, lr, beta1, beta2, eps, 0.0f,
+                                                      bc1, bc2, nullptr, nullptr, 1);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(CUT_ERR_CUDA, std::string("cut_mlp_adamw_step: ") + cudaGetErrorString(e));
+    return set_ok();
+}
+
+cut_status cut_mlp_status(cut_mlp *m) {
+    if (!m) return set_error(CUT_ERR_INVALID_ARG, "cut_mlp_status: null");
+    cudaSetDevice(m->device);
+    int h = 0;
+    cudaError_t e = cudaMemcpy(&h, m->err, 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return set_error(CUT_ERR_CUDA, std::string("cut_mlp_status: ") + cudaGetErrorString(e));
+    if (h) return set_error(CUT_ERR_TIMEOUT, "cut_mlp: a tensor-core pipeline wait timed out");
+    return set_ok();
+}
+
+}  // extern "C"

@@ -1,0 +1,236 @@
+// tc_gemm.cuh -- BF16 x BF16 -> FP32 GEMM on the 5th-generation tensor cores
+// (tcgen05.mma, accumulator in tensor memory, operands staged by TMA).
+//
+//   C[M, N] = A[M, K] * B[N, K]^T     (both operands K-major, row-major in HBM)
+//
+// One CTA of 128 threads computes a 128 x BN tile:
+//   warp 0, lane 0 : TMA producer, STAGES-deep ring of 128x64 / BNx64 tiles
+//                    (128-byte swizzle), one mbarrier pair per stage;
+//   warp 1, lane 0 : issues tcgen05.mma (M=128, N=BN, K=16 per instruction)
+//                    and tcgen05.commit to release each stage;
+//   all 4 warps    : epilogue, tcgen05.ld of their 32 TMEM lanes (rows),
+//                    fused bias / GELU / GELU-derivative / transposed stores.
+// Every mbarrier wait is bounded; on expiry the kernel records an error,
+// still frees its tensor memory and returns.
+#pragma once
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace cut {
+namespace tc {
+
+constexpr int BM = 128;
+constexpr int BK = 64;          // one 128-byte swizzle row of BF16
+constexpr int STAGES = 4;
+constexpr int kThreads = 128;
+constexpr long long kSpinLimit = 1ll << 26;
+
+struct Epi {
+    const float *bias;          // [N] or null
+    const float *dgelu_z;       // backward: multiply by GELU'(z), z row-major [M][ldz]
+    int ldz;
+    int act;                    // 1 = GELU on the output
+    float alpha;                // scale of the product
+    const float *post_scale;    // optional per-column affine after bias: v * scale + shift
+    const float *post_shift;
+    float *out_f32;             // [M][ld_f32] or null
+    int ld_f32;
+    __nv_bfloat16 *out_bf16;    // [M][ld_bf16] or null
+    int ld_bf16;
+    __nv_bfloat16 *out_t;       // transposed [N][ld_t] or null
+    int ld_t;
+    int M, N;                   // valid extent (rows, columns) written
+    int *err;                   // set to 1 when a wait timed out
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Bounded wait on the phase with the given parity; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    for (long long it = 0; it < kSpinLimit; it++) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n"
+            " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major tile, 128-byte swizzle, 8-row
+// groups 1024 bytes apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(const void *p) {
+    const uint64_t addr = smem_u32(p);
+    uint64_t d = 0;
+    d |= (addr >> 4) & 0x3FFFull;          // start address
+    d |= (uint64_t)1 << 16;                // leading byte offset (unused for this layout)
+    d |= (uint64_t)(1024 >> 4) << 32;      // stride byte offset
+    d |= (uint64_t)1 << 46;                // version
+    d |= (uint64_t)2 << 61;                // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, M = 128, N = bn.
+__host__ __device__ constexpr uint32_t idesc_bf16(int bn) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ float gelu(float x) {
+    return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f));
+}
+__device__ __forceinline__ float dgelu(float x) {
+    const float cdf = 0.5f * (1.0f + erff(x * 0.70710678118654752f));
+    const float pdf = 0.39894228040143268f * __expf(-0.5f * x * x);
+    return cdf + x * pdf;
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kThreads, 1)
+    gemm_bf16_tn(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int K, Epi ep) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte aligned tile ring
+    unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
+    unsigned char *sA = base;
+    unsigned char *sB = base + STAGES * A_BYTES;
+    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], done;
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int failed;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int KT = K / BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; s++) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        mbar_init(&done, 1);
+        failed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(BN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+
+    int issued = 0;
+    if (warp == 0 && lane == 0) {
+        // producer
+        for (int kt = 0; kt < KT && !failed; kt++) {
+            const int s = kt % STAGES;
+            if (kt >= STAGES && !mbar_wait(&empty[s], ((kt / STAGES) - 1) & 1)) { failed = 1; break; }
+            mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
+            tma_load_2d(sA + s * A_BYTES, &tmA, &full[s], kt * BK, m0);
+            tma_load_2d(sB + s * B_BYTES, &tmB, &full[s], kt * BK, n0);
+            issued = kt + 1;
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        constexpr uint32_t idesc = idesc_bf16(BN);
+        for (int kt = 0; kt < KT; kt++) {
+            const int s = kt % STAGES;
+            if (!mbar_wait(&full[s], (kt / STAGES) & 1)) { failed = 1; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; kk++) {
+                const uint64_t da = smem_desc(sA + s * A_BYTES + kk * 32);
+                const uint64_t db = smem_desc(sB + s * B_BYTES + kk * 32);
+                const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(da), "l"(db), "r"(idesc), "r"(acc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&empty[s]))
+                         : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&done))
+                     : "memory");
+    }
+    __syncwarp();
+    // every thread waits for the accumulator
+    const bool ok = mbar_wait(&done, 0);
+    if (!ok) failed = 1;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+
+    if (!failed) {
+        const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 8) {
+            uint32_t r[8];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (row >= ep.M) continue;
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+                const int col = n0 + c0 + i;
+                if (col >= ep.N) continue;
+                float v = __uint_as_float(r[i]) * ep.alpha;
+                if (ep.bias) v += ep.bias[col];
+                if (ep.post_scale) v = v * ep.post_scale[col] + ep.post_shift[col];
+                if (ep.dgelu_z) v *= dgelu(ep.dgelu_z[(int64_t)row * ep.ldz + col]);
+                if (ep.out_f32) ep.out_f32[(int64_t)row * ep.ld_f32 + col] = v;
+                const float a = ep.act ? gelu(v) : v;
+                if (ep.out_bf16) ep.out_bf16[(int64_t)row * ep.ld_bf16 + col] = __float2bfloat16(a);
+                if (ep.out_t) ep.out_t[(int64_t)col * ep.ld_t + row] = __float2bfloat16(a);
+            }
+        }
+    } else {
+        if (threadIdx.x == 0) {
+            // let the copies this thread issued land before the CTA exits
+            for (int kt = issued - STAGES < 0 ? 0 : issued - STAGES; kt < issued; kt++)
+                mbar_wait(&full[kt % STAGES], (kt / STAGES) & 1);
+            if (ep.err) atomicExch(ep.err, 1);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+}
+
+template <int BN>
+constexpr size_t gemm_smem_bytes() {
+    return 1024 + (size_t)STAGES * (BM * BK * 2 + BN * BK * 2);
+}
+
+}  // namespace tc
+}  // namespace cut

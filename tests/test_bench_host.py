@@ -1,0 +1,41 @@
+"""Host logic of the benchmark's multi-rank path on CPU (gloo, world 2)."""
+import os
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _worker(rank, world, port, out):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ms = bench.max_over_ranks(10.0 + 5.0 * rank, world, "cpu")
+    out[rank] = ms
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_with_two_gloo_ranks():
+    ctx = mp.get_context("spawn")
+    out = ctx.Manager().dict()
+    port = 29500 + os.getpid() % 1000
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    assert out[0] == out[1] == 15.0
+
+
+def test_job_throughput_is_weak_scaling_sum():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.job_throughput(1000, 2.0, 1) == 500000.0
+    assert bench.job_throughput(1000, 2.0, 4) == 2000000.0
+    assert bench.max_over_ranks(3.5, 1) == 3.5

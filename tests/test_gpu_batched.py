@@ -1,0 +1,89 @@
+"""Batched flows (many parameter sets, one graph read per record) on the GPU.
+
+FP64 batched RK4 must match the oracle's RK4 flow of every instance at
+RTOL = 1e-10.  FP64 batched DP45 takes each instance's own adaptive path and
+is compared with the single-instance GPU flow (same controller) and its step
+count.  The FP32-record path is compared with FP64 and its error reported.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import assert_close, graph_for, np64
+from cut_inputs import (ALG_FERMION, batched_parameters, dipole_operator, fermion_registry,
+                        number_operator, workload, cfg2_registry, molecular_hamiltonian)
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch(norb, B, seed):
+    labels = fermion_registry(norb)
+    H = batched_parameters(labels, norb, B, seed=seed)
+    N = number_operator(labels, norb)
+    D = dipole_operator(labels, norb, seed=seed)
+    X = np.stack([np.stack([N, D])] * B)
+    return labels, H, X
+
+
+@pytest.mark.parametrize("tile", [0, 2, 8])
+def test_batched_rk4_fp64_matches_oracle(tile):
+    import torch
+    norb, B = 4, 37                       # ragged against every tile width
+    labels, H, X = _batch(norb, B, seed=31)
+    G = graph_for("mol4", ALG_FERMION, norb, labels)
+    Hs, Xs, steps, status = G.flow_batched(torch.tensor(H), torch.tensor(X), precision="fp64", method="rk4",
+                                           s0=0.0, s1=0.2, ds=0.02, tile=tile)
+    assert np.all(status.cpu().numpy() == 0) and np.all(steps.cpu().numpy() == 10)
+    f = oracle.stacked_rhs(ALG_FERMION, norb, labels, 2)
+    n = len(labels)
+    for b in (0, 5, 17, 36):
+        y = oracle.rk4_flow(f, np.concatenate([H[b], X[b, 0], X[b, 1]]), 0.02, 10)
+        assert_close(np64(Hs[b]), y[:n], what=f"h[{b}]")
+        assert_close(np64(Xs[b, 1]), y[2 * n:], what=f"D[{b}]")
+
+
+def test_batched_dp45_fp64_follows_single_instance_flows():
+    import torch
+    w = workload("molecular_8so")
+    B = 24
+    H = batched_parameters(w.labels, 8, B, seed=32)
+    X = np.stack([np.stack(w.observables)] * B)
+    G = graph_for("mol8", w.alg, w.nmodes, w.labels)
+    Hs, Xs, steps, status = G.flow_batched(torch.tensor(H), torch.tensor(X), precision="fp64", method="dp45",
+                                           s0=0.0, s1=2.0, ds=1e-2, rtol=1e-10, atol=1e-12)
+    steps = steps.cpu().numpy()
+    assert np.all(status.cpu().numpy() == 0)
+    assert len(set(steps.tolist())) > 1          # uneven step counts across the batch
+    for b in (0, 7, 23):
+        hs, xs, st, _ = G.flow(H[b], list(X[b]), method="dp45", s0=0.0, s1=2.0, ds=1e-2, rtol=1e-10, atol=1e-12)
+        assert abs(st["steps"] - steps[b]) <= 2
+        # same tolerance-controlled path: agreement at the integration tolerance
+        assert_close(np64(Hs[b]), np64(hs), rtol=1e-8, what=f"h[{b}]")
+        assert_close(np64(Xs[b, 1]), np64(xs[1]), rtol=1e-8, what=f"D[{b}]")
+
+
+def test_batched_fp32_records_error_against_fp64():
+    import torch
+    w = workload("molecular_8so")
+    B = 64
+    H = batched_parameters(w.labels, 8, B, seed=33)
+    X = np.stack([np.stack(w.observables)] * B)
+    G = graph_for("mol8", w.alg, w.nmodes, w.labels)
+    H64, X64, st64, _ = G.flow_batched(torch.tensor(H), torch.tensor(X), precision="fp64", method="dp45",
+                                       s0=0.0, s1=10.0, ds=1e-2, rtol=1e-10, atol=1e-12)
+    H32, X32, st32, status = G.flow_batched(torch.tensor(H), torch.tensor(X), precision="fp32", method="dp45",
+                                            s0=0.0, s1=10.0, ds=1e-2, rtol=1e-6, atol=1e-9)
+    assert np.all(status.cpu().numpy() == 0)
+    err = np.max(np.abs(np64(H32) - np64(H64)), axis=1) / np.max(np.abs(np64(H64)), axis=1)
+    print(f"FP32-record batched flow vs FP64: max rel error {err.max():.2e}, median {np.median(err):.2e}")
+    assert err.max() < 1e-4
+    assert np.all(np64(X32[:, 0]) == np64(X64[:, 0]))     # N is exactly conserved in both
+
+
+def test_batched_rejects_bad_arguments():
+    import torch
+    import paper_2609_14831_b300 as cg
+    labels, H, X = _batch(4, 3, seed=34)
+    G = graph_for("mol4", ALG_FERMION, 4, labels)
+    with pytest.raises(cg.CutError):
+        G.flow_batched(torch.tensor(H), torch.tensor(X), precision="fp64", method="rk4", s0=0.0, s1=0.1, ds=0.01, tile=3)

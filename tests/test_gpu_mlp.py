@@ -1,0 +1,98 @@
+"""Surrogate MLP kernels (tcgen05 BF16 GEMMs, FP32 accumulation) against the
+FP64 oracle MLP with the same BF16 rounding points.
+
+Tolerance: relative Frobenius error <= 5e-3 for outputs and 2e-2 for each
+gradient block (FP32 accumulation order and FP32 GELU against FP64, plus the
+occasional bf16 rounding decision that flips on a last-bit difference).
+"""
+import numpy as np
+import pytest
+
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+
+
+def _setup(n_in, n_hid, n_out, B, seed):
+    import paper_2609_14831_b300 as cg
+    rng = np.random.default_rng(seed)
+    m = cg.MLP(n_in, n_hid, n_out, seed=seed, device=0)
+    layers = [(rng.normal(size=(n_hid, n_in)) / np.sqrt(n_in), rng.normal(size=n_hid) * 0.1),
+              (rng.normal(size=(n_hid, n_hid)) / np.sqrt(n_hid), rng.normal(size=n_hid) * 0.1),
+              (rng.normal(size=(n_out, n_hid)) / np.sqrt(n_hid), rng.normal(size=n_out) * 0.1)]
+    flat = omlp.flatten(layers).astype(np.float32)
+    m.set_params(flat)
+    layers32 = omlp.unflatten(flat.astype(np.float64), n_in, n_hid, n_out)
+    X = rng.normal(size=(B, n_in)).astype(np.float32)
+    T = rng.normal(size=(B, n_out)).astype(np.float32)
+    scale = rng.uniform(0.5, 2.0, n_out).astype(np.float32)
+    shift = rng.normal(size=n_out).astype(np.float32)
+    m.set_output_affine(scale, shift)
+    return m, layers32, X, T, scale.astype(np.float64), shift.astype(np.float64)
+
+
+@pytest.mark.parametrize("dims", [(32, 512, 848, 300), (5, 64, 70, 129), (32, 512, 848, 1024)])
+def test_mlp_forward_matches_oracle(dims):
+    n_in, n_hid, n_out, B = dims
+    m, layers, X, T, scale, shift = _setup(n_in, n_hid, n_out, B, seed=41)
+    y = m.forward(X).cpu().numpy().astype(np.float64)
+    m.status()
+    Yh, _ = omlp.forward(layers, X.astype(np.float64), emulate=True)
+    want = scale * Yh + shift
+    assert y.shape == (B, n_out)
+    assert _rel(y, want) < 5e-3, _rel(y, want)
+
+
+@pytest.mark.parametrize("dims", [(32, 512, 848, 300), (5, 64, 70, 129)])
+def test_mlp_gradients_match_oracle(dims):
+    n_in, n_hid, n_out, B = dims
+    m, layers, X, T, scale, shift = _setup(n_in, n_hid, n_out, B, seed=42)
+    loss = m.backward(X, T).cpu().numpy()[0]
+    m.status()
+    want_loss, grads = omlp.loss_and_grads(layers, X.astype(np.float64), T.astype(np.float64), scale, shift,
+                                           emulate=True)
+    assert abs(loss - want_loss) <= 5e-3 * abs(want_loss)
+    got = omlp.unflatten(m.params(grads=True).astype(np.float64), n_in, n_hid, n_out)
+    for l in range(3):
+        assert _rel(got[l][0], grads[l][0]) < 2e-2, (l, "W", _rel(got[l][0], grads[l][0]))
+        assert _rel(got[l][1], grads[l][1]) < 2e-2, (l, "b", _rel(got[l][1], grads[l][1]))
+
+
+def test_adamw_step_matches_published_update():
+    m, layers, X, T, scale, shift = _setup(6, 64, 10, 128, seed=43)
+    p0 = m.params().astype(np.float64)
+    m.backward(X, T)
+    g = m.params(grads=True).astype(np.float64)
+    m.step(lr=1e-2, beta1=0.9, beta2=0.99, eps=1e-8, weight_decay=0.01)
+    m.status()
+    p1 = m.params().astype(np.float64)
+    # decoupled weight decay on weights only
+    nl = omlp.unflatten(np.arange(p0.size), 6, 64, 10)
+    is_w = np.zeros(p0.size, dtype=bool)
+    for W, _ in nl:
+        is_w[W.ravel().astype(int)] = True
+    want = np.empty_like(p0)
+    for mask, wd in ((is_w, 0.01), (~is_w, 0.0)):
+        want[mask], _, _ = omlp.adamw(p0[mask], g[mask], 0.0, 0.0, 1, 1e-2, 0.9, 0.99, 1e-8, wd)
+    np.testing.assert_allclose(p1, want, rtol=1e-5, atol=1e-7)
+
+
+def test_training_reduces_loss():
+    import torch
+    import paper_2609_14831_b300 as cg
+    rng = np.random.default_rng(44)
+    m = cg.MLP(8, 128, 16, seed=44, device=0)
+    A = rng.normal(size=(8, 16))
+    X = rng.uniform(-1, 1, size=(1024, 8)).astype(np.float32)
+    Y = np.tanh(X @ A).astype(np.float32)
+    Xd, Yd = torch.tensor(X, device="cuda"), torch.tensor(Y, device="cuda")
+    losses = []
+    for it in range(300):
+        losses.append(float(m.backward(Xd, Yd).item()))
+        m.step(lr=3e-3)
+    m.status()
+    assert losses[-1] < 0.05 * losses[0], (losses[0], losses[-1])

@@ -311,3 +311,31 @@ def test_occupation_sector_matrices_match_jordan_wigner_blocks():
     for N in (1, 2, 3):
         np.testing.assert_allclose(dense.sector_matrix(labels, h, norb, N), dense.sector_block(M, norb, N).real,
                                    atol=1e-13)
+
+
+def test_mlp_oracle_gradients_match_central_differences():
+    """Pins the oracle MLP's chain rule (FP64, no rounding emulation)."""
+    from oracle import mlp
+    rng = np.random.default_rng(40)
+    n_in, n_hid, n_out, B = 5, 7, 4, 6
+    layers = [(rng.normal(size=(n_hid, n_in)) * 0.5, rng.normal(size=n_hid) * 0.1),
+              (rng.normal(size=(n_hid, n_hid)) * 0.4, rng.normal(size=n_hid) * 0.1),
+              (rng.normal(size=(n_out, n_hid)) * 0.4, rng.normal(size=n_out) * 0.1)]
+    X = rng.normal(size=(B, n_in))
+    T = rng.normal(size=(B, n_out))
+    scale, shift = rng.uniform(0.5, 2.0, n_out), rng.normal(size=n_out)
+    loss, grads = mlp.loss_and_grads(layers, X, T, scale, shift, emulate=False)
+    flat = mlp.flatten(layers)
+    g = mlp.flatten(grads)
+    for k in rng.choice(flat.size, 25, replace=False):
+        e = np.zeros_like(flat)
+        e[k] = 1e-6
+        lp, _ = mlp.loss_and_grads(mlp.unflatten(flat + e, n_in, n_hid, n_out), X, T, scale, shift, emulate=False)
+        lm, _ = mlp.loss_and_grads(mlp.unflatten(flat - e, n_in, n_hid, n_out), X, T, scale, shift, emulate=False)
+        np.testing.assert_allclose(g[k], (lp - lm) / 2e-6, rtol=1e-6, atol=1e-10)
+    # GELU against its closed-form values and bf16 rounding against exact cases
+    np.testing.assert_allclose(mlp.gelu(np.array([0.0, 1.0, -1.0])), [0.0, 0.8413447460685429, -0.15865525393145707],
+                               rtol=1e-15)
+    assert mlp.bf16(np.array([1.0 + 2.0 ** -8]))[0] == 1.0                 # tie -> even
+    assert mlp.bf16(np.array([1.0 + 3 * 2.0 ** -8]))[0] == 1.0 + 2.0 ** -6  # tie -> even (up)
+    assert mlp.bf16(np.array([1.0 + 2.0 ** -7]))[0] == 1.0 + 2.0 ** -7      # representable
