@@ -61,12 +61,17 @@ class ClockSampler:
         self.lines = []
 
     def start(self):
+        """Start sampling; returns once the first sample arrived, so that the
+        tool's own start-up is not inside the timed region."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
                  "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 20 and self.proc.poll() is None:
+                time.sleep(0.02)
         except Exception:
             self.proc = None
 
@@ -218,9 +223,9 @@ def main():
 
     # ---- timed region: exactly K RK4 steps, inputs resident in HBM
     clocks = ClockSampler(local)
+    clocks.start()
     barrier()
     torch.cuda.synchronize()
-    clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
         ev0.record(stream)

@@ -49,6 +49,9 @@ struct cut_graph {
     bool have_T = false;
     double *wtab = nullptr;        // exact factors as doubles
     float *wtab32 = nullptr;
+    unsigned long long *wsign = nullptr;  // sign bit per code
+    double wmag = 1.0;             // common magnitude when all factors share it
+    int wuniform = 0;
     int64_t device_bytes = 0;
     std::mutex mu;
     ~cut_graph() {
@@ -62,6 +65,7 @@ struct cut_graph {
         }
         cudaFree(wtab);
         cudaFree(wtab32);
+        cudaFree(wsign);
         cudaSetDevice(cur);
     }
 };
@@ -105,19 +109,32 @@ static cut_status upload_csr(DevCSR &d, const std::vector<uint64_t> &rp, const s
 
 // ----------------------------------------------------------------- RHS core
 // dx_o (o < nops) for operands x_o, given xi; operands processed 4 at a time.
+static k::Weights weights_of(const cut_graph *g) {
+    k::Weights w;
+    w.val = g->wtab;
+    w.sign = g->wsign;
+    w.mag = g->wmag;
+    w.n_codes = (int)g->host.num.size();
+    w.uniform = g->wuniform;
+    return w;
+}
+
 static void launch_comm(const cut_graph *g, const double *xi, int nops, const double *const *xs,
                         double *const *dxs, cudaStream_t s, const int *done) {
     const DevCSR &c = g->st[1];
     int grid = grid_for_rows(c.rows);
-    int nc = (int)g->host.num.size();
+    const k::Weights w = weights_of(g);
     for (int o0 = 0; o0 < nops; o0 += 4) {
         int m = std::min(4, nops - o0);
         switch (m) {
-#define CASE(M)                                                                                   \
-    case M: {                                                                                     \
-        k::Ops<M> ops;                                                                            \
-        for (int t = 0; t < M; t++) { ops.x[t] = xs[o0 + t]; ops.dx[t] = dxs[o0 + t]; }             \
-        k::comm_stage<M><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, g->wtab, nc, xi, ops, c.rows, done); \
+#define CASE(M)                                                                                        \
+    case M: {                                                                                          \
+        k::Ops<M> ops;                                                                                 \
+        for (int t = 0; t < M; t++) { ops.x[t] = xs[o0 + t]; ops.dx[t] = dxs[o0 + t]; }                  \
+        if (w.uniform)                                                                                 \
+            k::comm_stage<M, true><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, xi, ops, c.rows, done);    \
+        else                                                                                           \
+            k::comm_stage<M, false><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, xi, ops, c.rows, done);   \
     } break;
             CASE(1) CASE(2) CASE(3) CASE(4)
 #undef CASE
@@ -127,8 +144,11 @@ static void launch_comm(const cut_graph *g, const double *xi, int nops, const do
 
 static void launch_gen(const cut_graph *g, const double *h, double *xi, cudaStream_t s, const int *done) {
     const DevCSR &c = g->st[0];
-    k::gen_stage<<<grid_for_rows(c.rows), k::kBlock, 0, s>>>(c.rp, c.rec, g->wtab, (int)g->host.num.size(),
-                                                              h, xi, c.rows, done);
+    const k::Weights w = weights_of(g);
+    if (w.uniform)
+        k::gen_stage<true><<<grid_for_rows(c.rows), k::kBlock, 0, s>>>(c.rp, c.rec, w, h, xi, c.rows, done);
+    else
+        k::gen_stage<false><<<grid_for_rows(c.rows), k::kBlock, 0, s>>>(c.rp, c.rec, w, h, xi, c.rows, done);
 }
 
 // f(Y) for the stacked state Y[nops][n] into DY[nops][n].
@@ -180,10 +200,17 @@ cut_status cut_graph_load(const char *path, int device, unsigned flags, cut_grap
     }
     std::vector<double> w(g->host.num.size());
     std::vector<float> w32(w.size());
+    std::vector<unsigned long long> sg(w.size());
+    g->wuniform = 1;
     for (size_t c = 0; c < w.size(); c++) {
         w[c] = (double)g->host.num[c] / (double)g->host.den[c];
         w32[c] = (float)w[c];
+        sg[c] = w[c] < 0 ? 0x8000000000000000ull : 0ull;
+        if (std::fabs(w[c]) != std::fabs(w[0]) || w[c] == 0.0) g->wuniform = 0;
     }
+    g->wmag = std::fabs(w[0]);
+    CUDA_TRY(cudaMalloc(&g->wsign, sg.size() * 8));
+    CUDA_TRY(cudaMemcpy(g->wsign, sg.data(), sg.size() * 8, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMalloc(&g->wtab, w.size() * 8));
     CUDA_TRY(cudaMemcpy(g->wtab, w.data(), w.size() * 8, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMalloc(&g->wtab32, w.size() * 4));
@@ -831,3 +858,4 @@ extern "C" cut_status cut_flow_batched(const cut_graph *g, int batch, double *h,
     return flow_batched_impl(v, g->device, batch, h, n_obs, x, precision, o, tile, steps_out, status_out,
                              (cudaStream_t)stream, &g_last_tile);
 }
+

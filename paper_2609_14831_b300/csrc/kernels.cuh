@@ -31,36 +31,66 @@ __device__ __forceinline__ void load_table(double *ws, const double *wtab, int n
     __syncthreads();
 }
 
+// Exact factors of one graph.  When every factor has the same magnitude
+// (+-1 for fermion monomials, +-2 for Pauli strings) the record's factor is
+// a sign, applied by flipping the sign bit of one operand, and the magnitude
+// multiplies the finished row sum once: one FP64 FMA per record and operand,
+// which is what bounds these kernels on B300 (the FP64 pipe, not HBM).
+struct Weights {
+    const double *val;                 // value of each code
+    const unsigned long long *sign;    // sign bit of each code (uniform case)
+    double mag;                        // common magnitude (uniform case)
+    int n_codes, uniform;
+};
+
+__device__ __forceinline__ void load_weights(double *ws, unsigned long long *sg, const Weights &w) {
+    for (int c = threadIdx.x; c < w.n_codes; c += blockDim.x) {
+        ws[c] = w.val[c];
+        sg[c] = w.sign[c];
+    }
+    __syncthreads();
+}
+
+// +-v by the code's sign bit (an integer XOR, no FP64 instruction)
+__device__ __forceinline__ double signed_by(double v, unsigned long long sbit) {
+    return __longlong_as_double(__double_as_longlong(v) ^ (long long)sbit);
+}
+
 // Generator stage: xi[a] = sum_e alpha_e h[i_e] h[j_e]   (Eq. graph-actions, line 1)
+template <bool UNIFORM>
 __global__ void __launch_bounds__(kBlock) gen_stage(const uint64_t *__restrict__ rp,
-                                                    const uint2 *__restrict__ rec,
-                                                    const double *__restrict__ wtab, int n_codes,
+                                                    const uint2 *__restrict__ rec, Weights wt,
                                                     const double *__restrict__ h,
                                                     double *__restrict__ xi, int64_t rows,
                                                     const int *done) {
     __shared__ double ws[256];
+    __shared__ unsigned long long sg[256];
     if (skip(done)) return;
-    load_table(ws, wtab, n_codes);
+    load_weights(ws, sg, wt);
     const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * kWarpsPerBlock;
     for (int64_t r = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); r < rows; r += nw) {
         const uint64_t b = rp[r], e = rp[r + 1];
         double acc = 0.0;
         uint64_t p = b + lane;
+#define TERM(q)                                                                   \
+    (UNIFORM ? signed_by(h[(q).x & kIdx], sg[(q).x >> 24]) * h[(q).y]             \
+             : ws[(q).x >> 24] * h[(q).x & kIdx] * h[(q).y])
         for (; p + 96 < e; p += 128) {
             uint2 q0 = __ldcs(rec + p), q1 = __ldcs(rec + p + 32), q2 = __ldcs(rec + p + 64),
                   q3 = __ldcs(rec + p + 96);
-            acc += ws[q0.x >> 24] * h[q0.x & kIdx] * h[q0.y];
-            acc += ws[q1.x >> 24] * h[q1.x & kIdx] * h[q1.y];
-            acc += ws[q2.x >> 24] * h[q2.x & kIdx] * h[q2.y];
-            acc += ws[q3.x >> 24] * h[q3.x & kIdx] * h[q3.y];
+            acc += TERM(q0);
+            acc += TERM(q1);
+            acc += TERM(q2);
+            acc += TERM(q3);
         }
         for (; p < e; p += 32) {
             uint2 q = __ldcs(rec + p);
-            acc += ws[q.x >> 24] * h[q.x & kIdx] * h[q.y];
+            acc += TERM(q);
         }
+#undef TERM
         acc = warp_sum(acc);
-        if (lane == 0) xi[r] = acc;
+        if (lane == 0) xi[r] = UNIFORM ? acc * wt.mag : acc;
     }
 }
 
@@ -72,15 +102,15 @@ struct Ops {
 
 // Commutator stage: dx_o[k] = sum_e beta_e xi[a_e] x_o[j_e]  (Eq. graph-actions,
 // line 2) for NOPS operands at once: one record read serves every operand.
-template <int NOPS>
+template <int NOPS, bool UNIFORM>
 __global__ void __launch_bounds__(kBlock) comm_stage(const uint64_t *__restrict__ rp,
-                                                     const uint2 *__restrict__ rec,
-                                                     const double *__restrict__ wtab, int n_codes,
+                                                     const uint2 *__restrict__ rec, Weights wt,
                                                      const double *__restrict__ xi, Ops<NOPS> ops,
                                                      int64_t rows, const int *done) {
     __shared__ double ws[256];
+    __shared__ unsigned long long sg[256];
     if (skip(done)) return;
-    load_table(ws, wtab, n_codes);
+    load_weights(ws, sg, wt);
     const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * kWarpsPerBlock;
     for (int64_t r = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); r < rows; r += nw) {
@@ -89,10 +119,10 @@ __global__ void __launch_bounds__(kBlock) comm_stage(const uint64_t *__restrict_
 #pragma unroll
         for (int o = 0; o < NOPS; o++) acc[o] = 0.0;
         uint64_t p = b + lane;
+#define COEF(q) (UNIFORM ? signed_by(xi[(q).x & kIdx], sg[(q).x >> 24]) : ws[(q).x >> 24] * xi[(q).x & kIdx])
         for (; p + 32 < e; p += 64) {
             uint2 q0 = __ldcs(rec + p), q1 = __ldcs(rec + p + 32);
-            double c0 = ws[q0.x >> 24] * xi[q0.x & kIdx];
-            double c1 = ws[q1.x >> 24] * xi[q1.x & kIdx];
+            const double c0 = COEF(q0), c1 = COEF(q1);
 #pragma unroll
             for (int o = 0; o < NOPS; o++) {
                 acc[o] += c0 * ops.x[o][q0.y];
@@ -101,14 +131,15 @@ __global__ void __launch_bounds__(kBlock) comm_stage(const uint64_t *__restrict_
         }
         for (; p < e; p += 32) {
             uint2 q = __ldcs(rec + p);
-            double c = ws[q.x >> 24] * xi[q.x & kIdx];
+            const double c = COEF(q);
 #pragma unroll
             for (int o = 0; o < NOPS; o++) acc[o] += c * ops.x[o][q.y];
         }
+#undef COEF
 #pragma unroll
         for (int o = 0; o < NOPS; o++) {
             double v = warp_sum(acc[o]);
-            if (lane == 0) ops.dx[o][r] = v;
+            if (lane == 0) ops.dx[o][r] = UNIFORM ? v * wt.mag : v;
         }
     }
 }

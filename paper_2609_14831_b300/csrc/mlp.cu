@@ -307,7 +307,9 @@ cut_status cut_mlp_create(int n_in, int n_hidden, int n_out, uint64_t seed, int 
         Layer &Ly = m->L[l];
         Ly.in = dims[l];
         Ly.out = dims[l + 1];
-        Ly.in_p = pad_to(Ly.in, 64);
+        // a layer's padded input width is the previous layer's padded output
+        // width, so that activation buffers chain without re-striding
+        Ly.in_p = l == 0 ? pad_to(Ly.in, 64) : m->L[l - 1].out_p;
         Ly.out_p = pad_to(Ly.out, 128);
         const size_t cnt = (size_t)Ly.in_p * Ly.out_p;
         bool ok = m->alloc(&Ly.w, cnt) == cudaSuccess && m->alloc(&Ly.gw, cnt) == cudaSuccess &&
