@@ -138,6 +138,29 @@ cut_status cut_graph_records(const cut_graph *g, int stage, int64_t *row_ptr, in
 cut_status cut_rhs(const cut_graph *g, const double *h, int n_obs, const double *x, double *dh,
                    double *dx, double *xi_out, cut_stream_t stream);
 
+/* Allocation-free variant of cut_rhs.  The paper has no counterpart; it
+ * exists for callers that may not allocate device memory while they run
+ * (for example a real-time or serving loop whose memory is fixed up front,
+ * or code whose allocator is owned by someone else), since cut_rhs takes a
+ * temporary generator buffer from the stream-ordered allocator when xi_out
+ * is NULL.  Here that buffer is a fixed array of CUT_RHS_NOALLOC_MAX_NG
+ * doubles (8 MiB) compiled into the library: every GPU that loads the
+ * library holds it until the process exits.
+ *   - Same inputs, outputs and results as cut_rhs with xi_out = NULL.
+ *   - Graphs with more than CUT_RHS_NOALLOC_MAX_NG generator coordinates are
+ *     rejected with CUT_ERR_INVALID_ARG before anything is queued.
+ *   - Makes no cudaMalloc, cudaFree or other allocating call.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls on a device share the one array and it keeps what the last
+ *     call left there (every entry is rewritten before it is read, so nothing
+ *     needs clearing): calls whose kernels overlap on the GPU (different
+ *     streams, no ordering between them) race on it and give wrong results. */
+#define CUT_RHS_NOALLOC_MAX_NG (1 << 20)
+cut_status cut_rhs_noalloc(const cut_graph *g, const double *h, int n_obs, const double *x, double *dh,
+                           double *dx, cut_stream_t stream);
+
 /* Reverse traversal (Sec. 2.4): vector-Jacobian product of cut_rhs.
  * With L = <w_h, dh> + sum_o <w_x[o], dx_o>:
  *   h_bar = dL/dh (through eta and through X_0 = H),  x_bar[o] = dL/dx_o.

@@ -88,6 +88,7 @@ def lib():
         "cut_graph_records": (st, [VP, i, VP, VP, VP, VP]),
         "cut_rhs": (st, [VP, VP, i, VP, VP, VP, VP, VP]),
         "cut_rhs_adjoint": (st, [VP, VP, i, VP, VP, VP, VP, VP, VP]),
+        "cut_rhs_noalloc": (st, [VP, VP, i, VP, VP, VP, VP]),
         "cut_flow": (st, [VP, VP, i, VP, ctypes.POINTER(FlowOpts), ctypes.POINTER(FlowStats), VP]),
         "cut_flow_vjp": (st, [VP, VP, i, VP, ctypes.POINTER(FlowOpts), i, VP, VP, VP, VP, VP]),
         "cut_flow_batched": (st, [VP, i, VP, i, VP, i, ctypes.POINTER(FlowOpts), i, VP, VP, VP]),

@@ -859,3 +859,58 @@ extern "C" cut_status cut_flow_batched(const cut_graph *g, int batch, double *h,
                              (cudaStream_t)stream, &g_last_tile);
 }
 
+// ----------------------------------------------------------------- no-alloc RHS
+// A right-hand side for callers that must not allocate device memory: the
+// generator scratch lives in a fixed array inside the library's device image.
+namespace cut {
+
+constexpr int64_t kNoAllocMaxGen = CUT_RHS_NOALLOC_MAX_NG;
+static __device__ __align__(256) double g_noalloc_xi[kNoAllocMaxGen];
+
+static std::mutex g_noalloc_mu;
+static double *g_noalloc_ptr[256] = {nullptr};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the host-side name of the array is not a device address).
+static cut_status noalloc_scratch(int device, double **out) {
+    if (device < 0 || device >= 256) return set_error(CUT_ERR_INVALID_ARG, "cut_rhs_noalloc: device index out of range");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_xi);
+        if (e != cudaSuccess || !p)
+            return set_error(CUT_ERR_CUDA, std::string("cut_rhs_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        g_noalloc_ptr[device] = (double *)p;
+    }
+    *out = g_noalloc_ptr[device];
+    return CUT_OK;
+}
+
+}  // namespace cut
+
+extern "C" cut_status cut_rhs_noalloc(const cut_graph *g, const double *h, int n_obs, const double *x, double *dh,
+                                      double *dx, cut_stream_t stream) {
+    if (!g || g->device < 0 || !h || !dh || n_obs < 0 || n_obs > 63 || (n_obs > 0 && (!x || !dx)))
+        return set_error(CUT_ERR_INVALID_ARG, "cut_rhs_noalloc: bad argument");
+    if (g->host.n_g() > kNoAllocMaxGen)
+        return set_error(CUT_ERR_INVALID_ARG, "cut_rhs_noalloc: the graph has " + std::to_string(g->host.n_g()) +
+                                                  " generator coordinates, more than the fixed scratch holds (" +
+                                                  std::to_string(kNoAllocMaxGen) + "); use cut_rhs");
+    DeviceGuard dg(g->device);
+    double *xi = nullptr;
+    cut_status st = noalloc_scratch(g->device, &xi);
+    if (st != CUT_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = g->host.n();
+    // every generator coordinate is written by the generator stage before the
+    // commutator stage reads it, so the scratch needs no clearing
+    launch_gen(g, h, xi, s, nullptr);
+    const double *xs[64];
+    double *dxs[64];
+    xs[0] = h;
+    dxs[0] = dh;
+    for (int o = 0; o < n_obs; o++) { xs[o + 1] = x + o * n; dxs[o + 1] = dx + o * n; }
+    launch_comm(g, xi, n_obs + 1, xs, dxs, s, nullptr);
+    CUDA_TRY(cudaGetLastError());
+    return set_ok();
+}
