@@ -38,6 +38,7 @@ sys.path.insert(0, ROOT)
 
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6400.0
+FP64_NOMINAL_TFLOPS = 1.25   # B300 FP64 (non-tensor) rate, nominal
 
 
 def _peak_hbm():
@@ -163,6 +164,109 @@ def cpu_sample(seconds_budget=20.0):
                       f"value = graph records / oracle time"}
 
 
+def batched_vs_plain(cg, torch, dev, local, batch=1024, plain_sample=8):
+    """Batched flows/s against the plain single-instance GPU flow.
+
+    8-spin-orbital model, 1024 seeded parameter sets, H + N + D to s = 10 with
+    uneven adaptive step counts.  FP32-record batches at rtol 1e-6 and FP64
+    batches at rtol 1e-10; the plain flow is the FP64 single-instance DP45
+    at rtol 1e-10, timed on `plain_sample` instances and scaled.
+    """
+    from cut_inputs import batched_parameters, workload
+    w = workload("molecular_8so")
+    path = os.path.join(tempfile.mkdtemp(prefix="cutbatch_"), "m8.cutg")
+    cg.build_graph(w.alg, w.nmodes, w.labels, path)
+    G = cg.Graph(path, device=local)
+    H = torch.tensor(batched_parameters(w.labels, 8, batch, seed=3), device=dev)
+    X = torch.tensor(np.stack([np.stack(w.observables)] * batch), device=dev)
+    out = {"workload": f"molecular_8so x {batch} parameter sets, s in [0, 10]"}
+
+    def run(prec, rtol, atol):
+        G.flow_batched(H[:64], X[:64], precision=prec, method="dp45", s0=0.0, s1=10.0, ds=1e-2, rtol=rtol, atol=atol)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Hs, _, steps, status = G.flow_batched(H, X, precision=prec, method="dp45", s0=0.0, s1=10.0, ds=1e-2,
+                                              rtol=rtol, atol=atol)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        st = steps.cpu().numpy()
+        return Hs, dt, st, int(status.abs().max().item())
+
+    H32, t32, st32, bad32 = run("fp32", 1e-6, 1e-9)
+    H64, t64, st64, bad64 = run("fp64", 1e-10, w.atol)
+    G.flow(H[0], list(X[0]), method="dp45", s0=0.0, s1=10.0, ds=1e-2, rtol=1e-10, atol=w.atol)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain = []
+    for b in range(plain_sample):
+        hs, _, stp, _ = G.flow(H[b], list(X[b]), method="dp45", s0=0.0, s1=10.0, ds=1e-2, rtol=1e-10, atol=w.atol)
+        plain.append(hs)
+    torch.cuda.synchronize()
+    tp = (time.perf_counter() - t0) / plain_sample
+    err32 = float(((H32 - H64).abs().max(dim=1).values / H64.abs().max(dim=1).values).max())
+    dev64 = float(max(((H64[b] - plain[b]).abs().max() / plain[b].abs().max()).item() for b in range(plain_sample)))
+    out.update({
+        "fp32_records_flows_per_s": batch / t32, "fp64_flows_per_s": batch / t64,
+        "plain_fp64_flows_per_s": 1.0 / tp,
+        "speedup_fp32_vs_plain": (batch / t32) * tp, "speedup_fp64_vs_plain": (batch / t64) * tp,
+        "steps_fp32": [int(st32.min()), int(st32.max())], "steps_fp64": [int(st64.min()), int(st64.max())],
+        "fp32_max_rel_err_vs_fp64": err32, "fp64_batched_vs_plain_max_rel_dev": dev64,
+        "status_ok": bad32 == 0 and bad64 == 0})
+    G.close()
+    return out
+
+
+def run_surrogate(args):
+    """Surrogate workload: 50k FP32 batched flows of the 8-orbital model
+    (32 parameters theta ~ U(-0.1, 0.1)) train the MLP with the library's
+    kernels; held-out queries are screened (gate 1e-4 on the 36 diagonal
+    coefficients) with the FP64 flow as fallback.  One JSON line."""
+    import torch
+    import paper_2609_14831_b300 as cg
+    from paper_2609_14831_b300.surrogate import Surrogate
+    from cut_inputs import parameter_directions, workload
+    torch.cuda.set_device(0)
+    w = workload("molecular_8so")
+    path = os.path.join(tempfile.mkdtemp(prefix="cutsur_"), "m8.cutg")
+    cg.build_graph(w.alg, w.nmodes, w.labels, path)
+    G = cg.Graph(path, device=0)
+    P = parameter_directions(w.labels, 8)
+    sur = Surrogate(G, w.h, P, w.observables, n_hidden=512, seed=0)
+    rng = np.random.default_rng(4)
+    n_train, n_test = args.surrogate_train, 1024
+    th_tr = rng.uniform(-0.1, 0.1, size=(n_train, 32))
+    th_te = rng.uniform(-0.1, 0.1, size=(n_test, 32))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Htr, _ = sur.flows(th_tr, "fp32")
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    hist = sur.fit(th_tr, Htr, epochs=args.surrogate_epochs, batch=1024, lr=3e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    diag = np.nonzero([int(l) & 0xFFFFFFFF == int(l) >> 32 for l in w.labels])[0]
+    t0 = time.perf_counter()
+    exact, _ = sur.flows(th_te, "fp64")
+    torch.cuda.synchronize()
+    t_fp64 = time.perf_counter() - t0
+    pred = sur.predict(th_te)
+    err_net = (pred[:, diag] - exact[:, diag]).abs().max(dim=1).values.cpu().numpy()
+    out, ok, tm = sur.screen(th_te, diag, tol=1e-4)
+    torch.cuda.synchronize()
+    t_screen = tm["predict_s"] + tm["loose_s"] + tm["fallback_s"]
+    err = (out[:, diag] - exact[:, diag]).abs().max(dim=1).values.cpu().numpy()
+    line = {"metric": "surrogate-screened flows per second vs FP64 batched flows", "unit": "flows/s",
+            "value": n_test / t_screen, "baseline_fp64_flows_per_s": n_test / t_fp64,
+            "accepted_fraction": float(ok.float().mean().item()),
+            "max_err_diag_served": float(err.max()), "median_net_err_diag": float(np.median(err_net)),
+            "p90_net_err_diag": float(np.percentile(err_net, 90)),
+            "train_flows": n_train, "train_flows_s": t_data, "train_s": t_train,
+            "loss_first_last": [hist[0], hist[-1]], "timings": tm, "dtype": "bf16 mlp / f32+f64 flows",
+            "config": {"workload": "molecular_8so surrogate, 32 parameters", "gate": 1e-4}}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -185,9 +289,16 @@ def main():
     ap.add_argument("--impl", default="cut", choices=["cut", "reference"])
     ap.add_argument("--workload", default="stress_16so")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
+    ap.add_argument("--no-df64", action="store_true", help="skip the double-float measurement")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-flow measurement")
+    ap.add_argument("--surrogate", action="store_true", help="run the surrogate workload instead")
+    ap.add_argument("--surrogate-train", type=int, default=50000)
+    ap.add_argument("--surrogate-epochs", type=int, default=60)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.surrogate:
+        return run_surrogate(args)
 
     import torch
     import paper_2609_14831_b300 as cg
@@ -208,6 +319,7 @@ def main():
     os.remove(path)
     R = G.R_g + G.R_L
     n = G.n
+    nops = 1 + len(w.observables)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     h0 = torch.tensor(w.h, dtype=torch.float64, device=dev)
@@ -240,28 +352,73 @@ def main():
     ms_step = ms / args.steps
     value = job_throughput(4 * R, ms_step, world)
 
-    # ---- roofline: one graph apply (generator + commutator stage) on its stream
-    napply = 20
-    with torch.cuda.stream(stream):
-        G.rhs(h0, xs0, stream=stream)
+    # ---- roofline of the dominant kernel: the commutator stage alone
+    #      (cut_apply_L with the generator coordinates of h0), on its stream
+    nops = 1 + len(xs0)
+    xi = G.rhs(h0, xs0, want_xi=True, stream=stream)[2].contiguous()
+    X = torch.stack([h0] + xs0).contiguous()
+    DX = torch.empty_like(X)
+
+    def time_comm(reps=20):
+        import ctypes
+        args = (G._h, ctypes.c_void_p(xi.data_ptr()), nops, ctypes.c_void_p(X.data_ptr()),
+                ctypes.c_void_p(DX.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
+        cg.check(cg.lib().cut_apply_L(*args))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(napply):
-            G.rhs(h0, xs0, stream=stream)
+        for _ in range(reps):
+            cg.lib().cut_apply_L(*args)
         e1.record(stream)
-    torch.cuda.synchronize()
-    apply_ms = e0.elapsed_time(e1) / napply
-    nops = 1 + len(xs0)
-    alg_bytes = 8 * R + 8 * (G.n_g + 1) + 8 * (n + 1) + 8 * G.n_g + 8 * nops * n
-    peak, peak_kind = _peak_hbm()
-    achieved = alg_bytes / (apply_ms * 1e-3) / 1e9
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    comm_ms = time_comm()
+    comm_bytes = 8 * G.R_L + 8 * (n + 1) + 8 * nops * n
+    fp64_flop = 2 * nops * G.R_L                # one FMA per record and operand
+    hbm_peak, peak_kind = _peak_hbm()
+    fp64_peak = FP64_NOMINAL_TFLOPS
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tpath):
         try:
-            traffic = json.load(open(tpath)).get(f"{args.workload}:graph_apply")
+            traffic = json.load(open(tpath)).get(f"{args.workload}:comm_stage_fp64")
         except Exception:
             traffic = None
+    roofline = {"bound": "alu", "achieved": fp64_flop / (comm_ms * 1e-3) / 1e12, "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": fp64_flop / (comm_ms * 1e-3) / 1e12 / fp64_peak, "traffic": traffic,
+                "peak_kind": "nominal B300 FP64 rate (profiling recipe table); the FP64 pipe is the "
+                             "measured bound (ncu: sm__pipe_fp64_cycles_active > 90%)",
+                "kernel": f"comm_stage<{nops}> (FP64), one launch per operand block",
+                "launch_ms": comm_ms, "algorithmic_flop": fp64_flop,
+                "hbm_view": {"achieved": comm_bytes / (comm_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                             "frac": comm_bytes / (comm_ms * 1e-3) / 1e9 / hbm_peak, "peak_kind": peak_kind,
+                             "algorithmic_bytes": comm_bytes}}
+
+    # ---- the same flow and kernel in double-float arithmetic (FP32 pairs)
+    df = None
+    if not args.no_df64:
+        G.set_arithmetic("df64")
+        with torch.cuda.stream(stream):
+            steps_on_device(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            hs_df, _, _, _ = steps_on_device(args.steps)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        df_step = e0.elapsed_time(e1) / args.steps
+        df_comm = time_comm()
+        dh_df = G.rhs(h0, xs0, stream=stream)[0]
+        G.set_arithmetic("fp64")
+        dh_64 = G.rhs(h0, xs0, stream=stream)[0]
+        torch.cuda.synchronize()
+        dev_rel = float((dh_df - dh_64).abs().max() / dh_64.abs().max())
+        df = {"dtype": "f32x2 (double-float, ~48-bit significand)",
+              "value": job_throughput(4 * R, df_step, world), "unit": "records/s", "ms_per_step": df_step,
+              "max_rel_dev_vs_fp64_rhs": dev_rel,
+              "roofline": {"bound": "hbm", "achieved": comm_bytes / (df_comm * 1e-3) / 1e9, "peak": hbm_peak,
+                           "unit": "GB/s", "frac": comm_bytes / (df_comm * 1e-3) / 1e9 / hbm_peak,
+                           "peak_kind": peak_kind, "kernel": f"comm_stage_df<{nops}>", "launch_ms": df_comm,
+                           "traffic": None}}
 
     # ---- end to end through the public API with host buffers
     pin_h = torch.tensor(w.h, dtype=torch.float64).pin_memory()
@@ -286,6 +443,8 @@ def main():
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e_val = world * 4 * R / e2e_s
 
+    batched = None if args.no_batched else batched_vs_plain(cg, torch, dev, local)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_sample()
@@ -303,10 +462,9 @@ def main():
                            round(bstats["peak_rss_bytes"] / max(1, bstats["bytes_stored"]), 3),
                        "parallelism": f"{world} independent instance(s)"},
             "gpu_launches": int(args.steps * 4 * (1 + (nops + 3) // 4) + args.steps * 4),
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": "graph apply = gen_stage + comm_stage<3>",
-                         "apply_ms": apply_ms, "algorithmic_bytes": alg_bytes},
+            "roofline": roofline,
+            "df64": df,
+            "batched": batched,
             "clocks": ck,
             "e2e": {"value": e2e_val, "unit": "records/s",
                     "h2d_bytes_per_step": int(8 * n * nops), "d2h_bytes_per_step": int(8 * n * nops)},

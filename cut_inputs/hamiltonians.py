@@ -204,6 +204,7 @@ def workload(name, **kw):
 
 # Stress registry (16 spin-orbitals, about 3.3e8 records): every three-body
 # label sharing >= 1 orbital between its creator and annihilator sets and a
-# seeded 28% of the disjoint ones.
+# seeded ~28% of the disjoint ones (a pair is kept when the smaller of its
+# two draws is below 0.15).
 STRESS_KEEP_SHARED1 = 1.0
-STRESS_KEEP_SHARED0 = 0.28
+STRESS_KEEP_SHARED0 = 0.15

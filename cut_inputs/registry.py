@@ -99,9 +99,11 @@ def cfg2_registry(norb=16, keep_shared1=0.0, seed=2, keep_shared0=0.0):
     """
     rng = np.random.default_rng(seed)
     combos3 = list(combinations(range(norb), 3))
-    # one uniform draw per (creator, annihilator) pair, in registry order, so
-    # the selection is reproducible for any keep_shared1
+    # one uniform draw per unordered {creator set, annihilator set} pair, so
+    # that a label and its Hermitian conjugate are kept together (the
+    # registry is closed under conjugation) and the selection is reproducible
     draws = rng.random((len(combos3), len(combos3)))
+    draws = np.minimum(draws, draws.T)
     sel = []
     for ci, c in enumerate(combos3):
         cs = set(c)

@@ -60,6 +60,7 @@ typedef enum {
 enum { CUT_ALG_PAULI = 0, CUT_ALG_FERMION = 1 };
 enum { CUT_RK4 = 0, CUT_DP45 = 1 };
 enum { CUT_FP64 = 0, CUT_FP32REC_FP64STATE = 1 };
+enum { CUT_ARITH_FP64 = 0, CUT_ARITH_DF64 = 1 };
 
 /* Message of the last failing call on this thread ("" if none). */
 const char *cut_last_error(void);
@@ -138,6 +139,29 @@ cut_status cut_graph_records(const cut_graph *g, int stage, int64_t *row_ptr, in
 cut_status cut_rhs(const cut_graph *g, const double *h, int n_obs, const double *x, double *dh,
                    double *dx, double *xi_out, cut_stream_t stream);
 
+/* Arithmetic of the commutator stage for cut_rhs, cut_apply_L and cut_flow
+ * on this graph (a host-side setting of the handle; not thread-safe against
+ * calls in flight on other threads).
+ *   CUT_ARITH_FP64 (default): FP64 products and sums.
+ *   CUT_ARITH_DF64: products and sums as unevaluated pairs of FP32 numbers
+ *     (about 48 significant bits, error-free two-product and two-sum), run on
+ *     the FP32 pipes, which on B300 far outnumber the FP64 pipe that bounds
+ *     the FP64 stage.  Results agree with FP64 to about 1e-14 relative to the
+ *     largest term of a sum; coefficients below ~1e-38 lose relative
+ *     precision (FP32 range).  The generator stage, the RK state, the
+ *     adjoint and the batched path stay FP64 as documented there.
+ * Errors: INVALID_ARG (unknown mode), UNSUPPORTED (DF64 needs all stored
+ * factors of one magnitude, true for Pauli and fermion graphs). */
+cut_status cut_graph_set_arithmetic(cut_graph *g, int arith);
+
+/* The linear action L(h) x (Sec. 2.4, Eq. forward-coeff) for given generator
+ * coordinates: dx_o = sum_e beta_e xi[a_e] x_o[j_e] for n_ops operands, i.e.
+ * the commutator stage alone (xi from cut_rhs's xi_out).
+ * device in: xi[n_g], x[n_ops][n]; device out: dx[n_ops][n].
+ * Errors: INVALID_ARG, CUDA. */
+cut_status cut_apply_L(const cut_graph *g, const double *xi, int n_ops, const double *x, double *dx,
+                       cut_stream_t stream);
+
 /* Allocation-free variant of cut_rhs.  The paper has no counterpart; it
  * exists for callers that may not allocate device memory while they run
  * (for example a real-time or serving loop whose memory is fixed up front,
@@ -146,7 +170,8 @@ cut_status cut_rhs(const cut_graph *g, const double *h, int n_obs, const double 
  * is NULL.  Here that buffer is a fixed array of CUT_RHS_NOALLOC_MAX_NG
  * doubles (8 MiB) compiled into the library: every GPU that loads the
  * library holds it until the process exits.
- *   - Same inputs, outputs and results as cut_rhs with xi_out = NULL.
+ *   - Same inputs, outputs and results as cut_rhs with xi_out = NULL, always
+ *     in FP64 arithmetic.
  *   - Graphs with more than CUT_RHS_NOALLOC_MAX_NG generator coordinates are
  *     rejected with CUT_ERR_INVALID_ARG before anything is queued.
  *   - Makes no cudaMalloc, cudaFree or other allocating call.
@@ -249,6 +274,12 @@ cut_status cut_mlp_create(int n_in, int n_hidden, int n_out, uint64_t seed, int 
 cut_status cut_mlp_free(cut_mlp *m);
 /* host in: scale[n_out] (> 0), shift[n_out] */
 cut_status cut_mlp_set_output_affine(cut_mlp *m, const float *scale, const float *shift);
+/* Optional linear skip term: y = scale * y_hat + shift + J x with
+ * J[n_out][n_in] (host, FP32, copied), applied in FP32 on the CUDA cores in
+ * the last layer's epilogue and removed from the targets in training
+ * (t_hat = (t - shift - J x) / scale), so that the network learns only what
+ * a linear model misses.  J = NULL removes it. */
+cut_status cut_mlp_set_linear(cut_mlp *m, const float *J);
 /* number of parameters in the flat layout W1, b1, W2, b2, W3, b3 (W [out][in]) */
 int64_t cut_mlp_param_count(const cut_mlp *m);
 /* host out: parameters (grads = 0) or the gradients of the last backward

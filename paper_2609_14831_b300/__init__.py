@@ -89,12 +89,15 @@ def lib():
         "cut_rhs": (st, [VP, VP, i, VP, VP, VP, VP, VP]),
         "cut_rhs_adjoint": (st, [VP, VP, i, VP, VP, VP, VP, VP, VP]),
         "cut_rhs_noalloc": (st, [VP, VP, i, VP, VP, VP, VP]),
+        "cut_graph_set_arithmetic": (st, [VP, i]),
+        "cut_apply_L": (st, [VP, VP, i, VP, VP, VP]),
         "cut_flow": (st, [VP, VP, i, VP, ctypes.POINTER(FlowOpts), ctypes.POINTER(FlowStats), VP]),
         "cut_flow_vjp": (st, [VP, VP, i, VP, ctypes.POINTER(FlowOpts), i, VP, VP, VP, VP, VP]),
         "cut_flow_batched": (st, [VP, i, VP, i, VP, i, ctypes.POINTER(FlowOpts), i, VP, VP, VP]),
         "cut_mlp_create": (st, [i, i, i, ctypes.c_uint64, i, ctypes.POINTER(VP)]),
         "cut_mlp_free": (st, [VP]),
         "cut_mlp_set_output_affine": (st, [VP, VP, VP]),
+        "cut_mlp_set_linear": (st, [VP, VP]),
         "cut_mlp_param_count": (i64, [VP]),
         "cut_mlp_get_params": (st, [VP, VP, i]),
         "cut_mlp_set_params": (st, [VP, VP]),
@@ -223,6 +226,19 @@ class Graph:
         out = (dh, list(dx) if n_obs else [])
         return out + (xi[:self.n_g],) if want_xi else out
 
+    def set_arithmetic(self, mode):
+        """'fp64' (default) or 'df64' (FP32-pair products and sums)."""
+        check(lib().cut_graph_set_arithmetic(self._h, {"fp64": 0, "df64": 1}[mode]))
+
+    def apply_L(self, xi, xs, stream=None):
+        """L(h) x_o for generator coordinates xi (commutator stage alone)."""
+        torch = _torch()
+        xi = xi.to(device=self.device, dtype=torch.float64).contiguous()
+        x = torch.stack([_dev_f64(v, self.n, "x", self.device) for v in xs]).contiguous()
+        dx = torch.empty_like(x)
+        check(lib().cut_apply_L(self._h, _ptr(xi), x.shape[0], _ptr(x), _ptr(dx), _stream(stream)))
+        return list(dx)
+
     def rhs_adjoint(self, h, xs, w_h, w_xs, stream=None):
         """Vector-Jacobian product of rhs(): (h_bar, [x_bar_o])."""
         torch = _torch()
@@ -334,6 +350,15 @@ class MLP:
         sc = np.ascontiguousarray(scale, dtype=np.float32)
         sh = np.ascontiguousarray(shift, dtype=np.float32)
         check(lib().cut_mlp_set_output_affine(self._h, sc.ctypes.data, sh.ctypes.data))
+
+    def set_linear(self, J):
+        """Linear skip y += J x (J: [n_out, n_in]); None removes it."""
+        if J is None:
+            check(lib().cut_mlp_set_linear(self._h, None))
+            return
+        J = np.ascontiguousarray(J, dtype=np.float32)
+        assert J.shape == (self.n_out, self.n_in)
+        check(lib().cut_mlp_set_linear(self._h, J.ctypes.data))
 
     def params(self, grads=False):
         out = np.empty(lib().cut_mlp_param_count(self._h), dtype=np.float32)

@@ -52,6 +52,7 @@ struct cut_graph {
     unsigned long long *wsign = nullptr;  // sign bit per code
     double wmag = 1.0;             // common magnitude when all factors share it
     int wuniform = 0;
+    int arith = CUT_ARITH_FP64;    // arithmetic of the commutator stage
     int64_t device_bytes = 0;
     std::mutex mu;
     ~cut_graph() {
@@ -119,22 +120,30 @@ static k::Weights weights_of(const cut_graph *g) {
     return w;
 }
 
+// lanes per CSR segment: commutator rows are long (hundreds to thousands of
+// records), generator rows short (tens)
+constexpr int kCommLanes = 8, kGenLanes = 4;
+
+static int grid_for_groups(int64_t rows, int lanes) {
+    return grid_for_rows((rows + (32 / lanes) - 1) / (32 / lanes));
+}
+
 static void launch_comm(const cut_graph *g, const double *xi, int nops, const double *const *xs,
                         double *const *dxs, cudaStream_t s, const int *done) {
     const DevCSR &c = g->st[1];
-    int grid = grid_for_rows(c.rows);
+    const int grid = grid_for_groups(c.rows, kCommLanes);
     const k::Weights w = weights_of(g);
     for (int o0 = 0; o0 < nops; o0 += 4) {
         int m = std::min(4, nops - o0);
         switch (m) {
-#define CASE(M)                                                                                        \
-    case M: {                                                                                          \
-        k::Ops<M> ops;                                                                                 \
-        for (int t = 0; t < M; t++) { ops.x[t] = xs[o0 + t]; ops.dx[t] = dxs[o0 + t]; }                  \
-        if (w.uniform)                                                                                 \
-            k::comm_stage<M, true><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, xi, ops, c.rows, done);    \
-        else                                                                                           \
-            k::comm_stage<M, false><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, xi, ops, c.rows, done);   \
+#define CASE(M)                                                                                          \
+    case M: {                                                                                            \
+        k::Ops<M> ops;                                                                                   \
+        for (int t = 0; t < M; t++) { ops.x[t] = xs[o0 + t]; ops.dx[t] = dxs[o0 + t]; }                    \
+        if (w.uniform)                                                                                   \
+            k::comm_stage<M, true, kCommLanes><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, xi, ops, c.rows, done); \
+        else                                                                                             \
+            k::comm_stage<M, false, kCommLanes><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, xi, ops, c.rows, done); \
     } break;
             CASE(1) CASE(2) CASE(3) CASE(4)
 #undef CASE
@@ -145,21 +154,63 @@ static void launch_comm(const cut_graph *g, const double *xi, int nops, const do
 static void launch_gen(const cut_graph *g, const double *h, double *xi, cudaStream_t s, const int *done) {
     const DevCSR &c = g->st[0];
     const k::Weights w = weights_of(g);
+    const int grid = grid_for_groups(c.rows, kGenLanes);
     if (w.uniform)
-        k::gen_stage<true><<<grid_for_rows(c.rows), k::kBlock, 0, s>>>(c.rp, c.rec, w, h, xi, c.rows, done);
+        k::gen_stage<true, kGenLanes><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, h, xi, c.rows, done);
     else
-        k::gen_stage<false><<<grid_for_rows(c.rows), k::kBlock, 0, s>>>(c.rp, c.rec, w, h, xi, c.rows, done);
+        k::gen_stage<false, kGenLanes><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, h, xi, c.rows, done);
 }
 
-// f(Y) for the stacked state Y[nops][n] into DY[nops][n].
+// Double-float commutator stage: split xi and up to three operands at a time
+// into FP32 pairs (xi2[n_g], X2[n][4]) and apply the records on the FP32 pipes.
+static void launch_comm_df(const cut_graph *g, const double *xi, float2 *xi2, float2 *X2, int nops,
+                           const double *const *xs, double *const *dxs, cudaStream_t s, const int *done) {
+    const DevCSR &c = g->st[1];
+    const int64_t n = g->host.n(), ng = g->host.n_g();
+    const k::Weights w = weights_of(g);
+    const int grid = grid_for_groups(c.rows, kCommLanes);
+    if (ng > 0) k::split_pairs<<<grid_for_len(ng), 256, 0, s>>>(xi, ng, xi2, 1, 0, done);
+    for (int o0 = 0; o0 < nops; o0 += 3) {
+        const int m = std::min(3, nops - o0);
+        for (int t = 0; t < m; t++) k::split_pairs<<<grid_for_len(n), 256, 0, s>>>(xs[o0 + t], n, X2, 4, t, done);
+        const float4 *X4 = reinterpret_cast<const float4 *>(X2);
+        switch (m) {
+#define CASE(M)                                                                                           \
+    case M: {                                                                                             \
+        k::Ops<M> ops;                                                                                    \
+        for (int t = 0; t < M; t++) { ops.x[t] = xs[o0 + t]; ops.dx[t] = dxs[o0 + t]; }                     \
+        k::comm_stage_df<M, kCommLanes><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, xi2, X4, ops, c.rows, done); \
+    } break;
+            CASE(1) CASE(2) CASE(3)
+#undef CASE
+        }
+    }
+}
+
+// L(h) x_o for given xi (either arithmetic); df buffers may be null for FP64
+static void apply_L(const cut_graph *g, const double *xi, float2 *xi2, float2 *X2, int nops,
+                    const double *const *xs, double *const *dxs, cudaStream_t s, const int *done) {
+    // without double-float scratch (adjoint recomputation) the stage runs in FP64
+    if (g->arith == CUT_ARITH_DF64 && xi2 && X2) launch_comm_df(g, xi, xi2, X2, nops, xs, dxs, s, done);
+    else launch_comm(g, xi, nops, xs, dxs, s, done);
+}
+
+static size_t df_scratch_bytes(const cut_graph *g) {
+    return g->arith == CUT_ARITH_DF64 ? (size_t)(std::max<int64_t>(1, g->host.n_g()) + 4 * g->host.n()) * 8 : 0;
+}
+
+// f(Y) for the stacked state Y[nops][n] into DY[nops][n].  df: scratch of
+// df_scratch_bytes(g) bytes (double-float arithmetic only).
 static void stacked_rhs(const cut_graph *g, const double *Y, double *DY, int nops, double *xi,
-                        cudaStream_t s, const int *done) {
+                        cudaStream_t s, const int *done, void *df = nullptr) {
     const int64_t n = g->host.n();
     launch_gen(g, Y, xi, s, done);
     const double *xs[64];
     double *dxs[64];
     for (int o = 0; o < nops; o++) { xs[o] = Y + o * n; dxs[o] = DY + o * n; }
-    launch_comm(g, xi, nops, xs, dxs, s, done);
+    float2 *xi2 = (float2 *)df;
+    float2 *X2 = df ? xi2 + std::max<int64_t>(1, g->host.n_g()) : nullptr;
+    apply_L(g, xi, xi2, X2, nops, xs, dxs, s, done);
 }
 
 }  // namespace cut
@@ -282,15 +333,47 @@ cut_status cut_rhs(const cut_graph *g, const double *h, int n_obs, const double 
     const int64_t n = g->host.n();
     double *xi = xi_out;
     if (!xi) CUDA_TRY(cudaMallocAsync(&xi, std::max<int64_t>(1, g->host.n_g()) * 8, s));
+    void *df = nullptr;
+    if (df_scratch_bytes(g)) CUDA_TRY(cudaMallocAsync(&df, df_scratch_bytes(g), s));
     launch_gen(g, h, xi, s, nullptr);
     const double *xs[64];
     double *dxs[64];
     xs[0] = h;
     dxs[0] = dh;
     for (int o = 0; o < n_obs; o++) { xs[o + 1] = x + o * n; dxs[o + 1] = dx + o * n; }
-    launch_comm(g, xi, n_obs + 1, xs, dxs, s, nullptr);
+    float2 *xi2 = (float2 *)df;
+    apply_L(g, xi, xi2, df ? xi2 + std::max<int64_t>(1, g->host.n_g()) : nullptr, n_obs + 1, xs, dxs, s, nullptr);
     CUDA_TRY(cudaGetLastError());
     if (!xi_out) CUDA_TRY(cudaFreeAsync(xi, s));
+    if (df) CUDA_TRY(cudaFreeAsync(df, s));
+    return set_ok();
+}
+
+cut_status cut_graph_set_arithmetic(cut_graph *g, int arith) {
+    if (!g || (arith != CUT_ARITH_FP64 && arith != CUT_ARITH_DF64))
+        return set_error(CUT_ERR_INVALID_ARG, "cut_graph_set_arithmetic: unknown arithmetic");
+    if (arith == CUT_ARITH_DF64 && !g->wuniform)
+        return set_error(CUT_ERR_UNSUPPORTED, "cut_graph_set_arithmetic: double-float needs factors of one magnitude");
+    g->arith = arith;
+    return set_ok();
+}
+
+cut_status cut_apply_L(const cut_graph *g, const double *xi, int n_ops, const double *x, double *dx,
+                       cut_stream_t stream) {
+    if (!g || g->device < 0 || !xi || n_ops < 1 || n_ops > 64 || !x || !dx)
+        return set_error(CUT_ERR_INVALID_ARG, "cut_apply_L: bad argument");
+    DeviceGuard dg(g->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = g->host.n();
+    void *df = nullptr;
+    if (df_scratch_bytes(g)) CUDA_TRY(cudaMallocAsync(&df, df_scratch_bytes(g), s));
+    const double *xs[64];
+    double *dxs[64];
+    for (int o = 0; o < n_ops; o++) { xs[o] = x + o * n; dxs[o] = dx + o * n; }
+    float2 *xi2 = (float2 *)df;
+    apply_L(g, xi, xi2, df ? xi2 + std::max<int64_t>(1, g->host.n_g()) : nullptr, n_ops, xs, dxs, s, nullptr);
+    CUDA_TRY(cudaGetLastError());
+    if (df) CUDA_TRY(cudaFreeAsync(df, s));
     return set_ok();
 }
 
@@ -466,11 +549,13 @@ struct FlowWork {
     k::Control *ctl;
     double *replay, *record;
     int *flag;
+    void *df = nullptr;            // double-float scratch (or null)
     void *base = nullptr;
 };
 
-static cut_status alloc_work(FlowWork &w, int64_t L, int64_t ng, int64_t nrec, cudaStream_t s) {
-    size_t doubles = (size_t)(3 + 7) * L + ng + 2 * nrec + 64;
+static cut_status alloc_work(FlowWork &w, int64_t L, int64_t ng, int64_t nrec, cudaStream_t s,
+                             size_t df_bytes = 0) {
+    size_t doubles = (size_t)(3 + 7) * L + ng + 2 * nrec + 64 + df_bytes / 8 + 1;
     size_t bytes = doubles * 8 + sizeof(k::Control) + 64;
     CUDA_TRY(cudaMallocAsync(&w.base, bytes, s));
     double *p = (double *)w.base;
@@ -482,6 +567,8 @@ static cut_status alloc_work(FlowWork &w, int64_t L, int64_t ng, int64_t nrec, c
     w.replay = p; p += nrec;
     w.record = p; p += nrec;
     w.flag = (int *)p; p += 8;
+    w.df = df_bytes ? (void *)p : nullptr;
+    p += df_bytes / 8 + 1;
     w.ctl = (k::Control *)p;
     return CUT_OK;
 }
@@ -506,7 +593,7 @@ static void rk4_step(const cut_graph *g, FlowWork &w, int nops, double ds, cudaS
             stage_input(w, RK4_A[i], i, L, nullptr, ds, s, nullptr, w.U);
             in = w.U;
         }
-        stacked_rhs(g, in, w.K[i], nops, w.xi, s, nullptr);
+        stacked_rhs(g, in, w.K[i], nops, w.xi, s, nullptr, w.df);
     }
     k::Combine cb;
     cb.base = w.Y;
@@ -523,10 +610,10 @@ static void dp_attempt(const cut_graph *g, FlowWork &w, int nops, cudaStream_t s
     const double *dsp = &w.ctl->ds;
     for (int i = 1; i < 6; i++) {
         stage_input(w, DP_A[i], i, L, dsp, 0.0, s, done, w.U);
-        stacked_rhs(g, w.U, w.K[i], nops, w.xi, s, done);
+        stacked_rhs(g, w.U, w.K[i], nops, w.xi, s, done, w.df);
     }
     stage_input(w, DP_A[6], 6, L, dsp, 0.0, s, done, w.Y5);
-    stacked_rhs(g, w.Y5, w.K[6], nops, w.xi, s, done);
+    stacked_rhs(g, w.Y5, w.K[6], nops, w.xi, s, done, w.df);
     if (!replay) {
         k::ErrTerms et;
         for (int i = 0; i < 7; i++) { et.K[i] = w.K[i]; et.e[i] = DP_B[i] - DP_BS[i]; }
@@ -615,7 +702,7 @@ extern "C" cut_status cut_flow(const cut_graph *g, double *h, int n_obs, double 
     const int64_t max_steps = o->max_steps > 0 ? o->max_steps : 1000000;
     const int64_t nrec = dp ? (replay ? o->n_replay : std::min<int64_t>(max_steps, 1 << 22)) : 1;
     FlowWork w;
-    st = alloc_work(w, L, ng, nrec, s);
+    st = alloc_work(w, L, ng, nrec, s, df_scratch_bytes(g));
     if (st != CUT_OK) { end_work(sp); return st; }
     auto fail = [&](cut_status e) { cudaFreeAsync(w.base, s); end_work(sp); return e; };
     cudaMemcpyAsync(w.Y, h, n * 8, cudaMemcpyDeviceToDevice, s);
@@ -653,7 +740,7 @@ extern "C" cut_status cut_flow(const cut_graph *g, double *h, int n_obs, double 
         c.done = (replay || o->s1 > o->s0) ? 0 : 1;
         cudaMemcpyAsync(w.ctl, &c, sizeof(c), cudaMemcpyHostToDevice, s);
         if (replay) cudaMemcpyAsync(w.replay, o->replay_steps, o->n_replay * 8, cudaMemcpyHostToDevice, s);
-        stacked_rhs(g, w.Y, w.K[0], nops, w.xi, s, nullptr);
+        stacked_rhs(g, w.Y, w.K[0], nops, w.xi, s, nullptr, w.df);
         const int64_t chunk = 16;
         cudaGraph_t graph;
         cudaGraphExec_t exec;

@@ -56,41 +56,52 @@ __device__ __forceinline__ double signed_by(double v, unsigned long long sbit) {
     return __longlong_as_double(__double_as_longlong(v) ^ (long long)sbit);
 }
 
+// Sub-warp rows: LANES lanes share one CSR segment (32 / LANES segments per
+// warp).  Short segments waste fewer lanes and the closing shuffle reduction
+// costs log2(LANES) FP64 adds per operand instead of 5.
+template <int LANES>
+__device__ __forceinline__ double group_sum(double v) {
+#pragma unroll
+    for (int o = LANES / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // Generator stage: xi[a] = sum_e alpha_e h[i_e] h[j_e]   (Eq. graph-actions, line 1)
-template <bool UNIFORM>
+template <bool UNIFORM, int LANES>
 __global__ void __launch_bounds__(kBlock) gen_stage(const uint64_t *__restrict__ rp,
                                                     const uint2 *__restrict__ rec, Weights wt,
                                                     const double *__restrict__ h,
                                                     double *__restrict__ xi, int64_t rows,
                                                     const int *done) {
+    constexpr int RPW = 32 / LANES;
     __shared__ double ws[256];
     __shared__ unsigned long long sg[256];
     if (skip(done)) return;
     load_weights(ws, sg, wt);
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, sub = lane / LANES, sl = lane % LANES;
     const int64_t nw = (int64_t)gridDim.x * kWarpsPerBlock;
-    for (int64_t r = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); r < rows; r += nw) {
-        const uint64_t b = rp[r], e = rp[r + 1];
+    for (int64_t rg = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); rg * RPW < rows; rg += nw) {
+        const int64_t r = rg * RPW + sub;
         double acc = 0.0;
-        uint64_t p = b + lane;
+        if (r < rows) {
+            const uint64_t e = rp[r + 1];
 #define TERM(q)                                                                   \
     (UNIFORM ? signed_by(h[(q).x & kIdx], sg[(q).x >> 24]) * h[(q).y]             \
              : ws[(q).x >> 24] * h[(q).x & kIdx] * h[(q).y])
-        for (; p + 96 < e; p += 128) {
-            uint2 q0 = __ldcs(rec + p), q1 = __ldcs(rec + p + 32), q2 = __ldcs(rec + p + 64),
-                  q3 = __ldcs(rec + p + 96);
-            acc += TERM(q0);
-            acc += TERM(q1);
-            acc += TERM(q2);
-            acc += TERM(q3);
-        }
-        for (; p < e; p += 32) {
-            uint2 q = __ldcs(rec + p);
-            acc += TERM(q);
-        }
+            uint64_t p = rp[r] + sl;
+            for (; p + LANES < e; p += 2 * LANES) {
+                const uint2 q0 = __ldcs(rec + p), q1 = __ldcs(rec + p + LANES);
+                acc += TERM(q0);
+                acc += TERM(q1);
+            }
+            if (p < e) {
+                const uint2 q = __ldcs(rec + p);
+                acc += TERM(q);
+            }
 #undef TERM
-        acc = warp_sum(acc);
-        if (lane == 0) xi[r] = UNIFORM ? acc * wt.mag : acc;
+        }
+        acc = group_sum<LANES>(acc);
+        if (sl == 0 && r < rows) xi[r] = UNIFORM ? acc * wt.mag : acc;
     }
 }
 
@@ -102,45 +113,157 @@ struct Ops {
 
 // Commutator stage: dx_o[k] = sum_e beta_e xi[a_e] x_o[j_e]  (Eq. graph-actions,
 // line 2) for NOPS operands at once: one record read serves every operand.
-template <int NOPS, bool UNIFORM>
+template <int NOPS, bool UNIFORM, int LANES>
 __global__ void __launch_bounds__(kBlock) comm_stage(const uint64_t *__restrict__ rp,
                                                      const uint2 *__restrict__ rec, Weights wt,
                                                      const double *__restrict__ xi, Ops<NOPS> ops,
                                                      int64_t rows, const int *done) {
+    constexpr int RPW = 32 / LANES;
     __shared__ double ws[256];
     __shared__ unsigned long long sg[256];
     if (skip(done)) return;
     load_weights(ws, sg, wt);
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, sub = lane / LANES, sl = lane % LANES;
     const int64_t nw = (int64_t)gridDim.x * kWarpsPerBlock;
-    for (int64_t r = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); r < rows; r += nw) {
-        const uint64_t b = rp[r], e = rp[r + 1];
+    for (int64_t rg = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); rg * RPW < rows; rg += nw) {
+        const int64_t r = rg * RPW + sub;
         double acc[NOPS];
 #pragma unroll
         for (int o = 0; o < NOPS; o++) acc[o] = 0.0;
-        uint64_t p = b + lane;
+        if (r < rows) {
+            const uint64_t e = rp[r + 1];
 #define COEF(q) (UNIFORM ? signed_by(xi[(q).x & kIdx], sg[(q).x >> 24]) : ws[(q).x >> 24] * xi[(q).x & kIdx])
-        for (; p + 32 < e; p += 64) {
-            uint2 q0 = __ldcs(rec + p), q1 = __ldcs(rec + p + 32);
-            const double c0 = COEF(q0), c1 = COEF(q1);
+            uint64_t p = rp[r] + sl;
+            // four records per lane per step, every load issued before the
+            // arithmetic: the gathers are L2 round trips, the FMAs are not
+            for (; p + 3 * LANES < e; p += 4 * LANES) {
+                uint2 q[4];
 #pragma unroll
-            for (int o = 0; o < NOPS; o++) {
-                acc[o] += c0 * ops.x[o][q0.y];
-                acc[o] += c1 * ops.x[o][q1.y];
+                for (int u = 0; u < 4; u++) q[u] = __ldcs(rec + p + u * LANES);
+                double c[4], xv[4][NOPS];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    c[u] = COEF(q[u]);
+#pragma unroll
+                    for (int o = 0; o < NOPS; o++) xv[u][o] = ops.x[o][q[u].y];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+#pragma unroll
+                    for (int o = 0; o < NOPS; o++) acc[o] += c[u] * xv[u][o];
             }
-        }
-        for (; p < e; p += 32) {
-            uint2 q = __ldcs(rec + p);
-            const double c = COEF(q);
+            for (; p < e; p += LANES) {
+                const uint2 q = __ldcs(rec + p);
+                const double c = COEF(q);
 #pragma unroll
-            for (int o = 0; o < NOPS; o++) acc[o] += c * ops.x[o][q.y];
-        }
+                for (int o = 0; o < NOPS; o++) acc[o] += c * ops.x[o][q.y];
+            }
 #undef COEF
+        }
 #pragma unroll
         for (int o = 0; o < NOPS; o++) {
-            double v = warp_sum(acc[o]);
-            if (lane == 0) ops.dx[o][r] = UNIFORM ? v * wt.mag : v;
+            const double v = group_sum<LANES>(acc[o]);
+            if (sl == 0 && r < rows) ops.dx[o][r] = UNIFORM ? v * wt.mag : v;
         }
+    }
+}
+
+// ---------------------------------------------------------------- double-float
+// The same commutator stage with the products and sums carried as unevaluated
+// pairs of FP32 numbers (hi + lo, about 48 significant bits), on the FP32
+// pipes instead of the FP64 pipe.  Each product is formed with an exact
+// two-product (FMA residual) plus the two cross terms; each sum with an
+// exact two-sum whose error is accumulated separately.  Partial sums are
+// converted to FP64 for the closing reduction.  Inputs: xi and the operands
+// split into FP32 pairs, the operands interleaved as X2[j][4] (32 bytes).
+__device__ __forceinline__ void df_madd(float ch, float cl, float xh, float xl, float &s, float &c) {
+    const float p = __fmul_rn(ch, xh);
+    const float pe = __fmaf_rn(ch, xh, -p);
+    const float pl = __fmaf_rn(ch, xl, __fmaf_rn(cl, xh, pe));
+    const float t = __fadd_rn(s, p);
+    const float bp = __fsub_rn(t, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+    c = __fadd_rn(c, __fadd_rn(e, pl));
+    s = t;
+}
+
+template <int NOPS, int LANES>
+__global__ void __launch_bounds__(kBlock) comm_stage_df(const uint64_t *__restrict__ rp,
+                                                        const uint2 *__restrict__ rec, Weights wt,
+                                                        const float2 *__restrict__ xi2,
+                                                        const float4 *__restrict__ X2, Ops<NOPS> ops,
+                                                        int64_t rows, const int *done) {
+    static_assert(NOPS <= 3, "three operands per interleaved pair block");
+    constexpr int RPW = 32 / LANES;
+    __shared__ double ws[256];
+    __shared__ unsigned long long sg[256];
+    if (skip(done)) return;
+    load_weights(ws, sg, wt);
+    const int lane = threadIdx.x & 31, sub = lane / LANES, sl = lane % LANES;
+    const int64_t nw = (int64_t)gridDim.x * kWarpsPerBlock;
+    for (int64_t rg = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); rg * RPW < rows; rg += nw) {
+        const int64_t r = rg * RPW + sub;
+        float s[NOPS], c[NOPS];
+#pragma unroll
+        for (int o = 0; o < NOPS; o++) { s[o] = 0.0f; c[o] = 0.0f; }
+        if (r < rows) {
+            const uint64_t e = rp[r + 1];
+            uint64_t p = rp[r] + sl;
+            // four records per lane per step, all loads ahead of the arithmetic
+            for (; p + 3 * LANES < e; p += 4 * LANES) {
+                uint2 q[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) q[u] = __ldcs(rec + p + u * LANES);
+                float2 cf[4];
+                float4 a[4], b[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    cf[u] = xi2[q[u].x & kIdx];
+                    a[u] = X2[2 * (int64_t)q[u].y];
+                    if (NOPS > 2) b[u] = X2[2 * (int64_t)q[u].y + 1];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const unsigned int sb = (unsigned int)(sg[q[u].x >> 24] >> 32);
+                    const float ch = __uint_as_float(__float_as_uint(cf[u].x) ^ sb);
+                    const float cl = __uint_as_float(__float_as_uint(cf[u].y) ^ sb);
+                    df_madd(ch, cl, a[u].x, a[u].y, s[0], c[0]);
+                    if (NOPS > 1) df_madd(ch, cl, a[u].z, a[u].w, s[1], c[1]);
+                    if (NOPS > 2) df_madd(ch, cl, b[u].x, b[u].y, s[2], c[2]);
+                }
+            }
+            for (; p < e; p += LANES) {
+                const uint2 q = __ldcs(rec + p);
+                float2 cf = xi2[q.x & kIdx];
+                const unsigned int sb = (unsigned int)(sg[q.x >> 24] >> 32);
+                cf.x = __uint_as_float(__float_as_uint(cf.x) ^ sb);
+                cf.y = __uint_as_float(__float_as_uint(cf.y) ^ sb);
+                const float4 a = X2[2 * (int64_t)q.y];
+                df_madd(cf.x, cf.y, a.x, a.y, s[0], c[0]);
+                if (NOPS > 1) df_madd(cf.x, cf.y, a.z, a.w, s[1], c[1]);
+                if (NOPS > 2) {
+                    const float4 b = X2[2 * (int64_t)q.y + 1];
+                    df_madd(cf.x, cf.y, b.x, b.y, s[2], c[2]);
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 0; o < NOPS; o++) {
+            const double v = group_sum<LANES>((double)s[o] + (double)c[o]);
+            if (sl == 0 && r < rows) ops.dx[o][r] = v * wt.mag;
+        }
+    }
+}
+
+// Split doubles into FP32 pairs: out[i * stride + slot] = (hi, lo)
+__global__ void split_pairs(const double *__restrict__ in, int64_t len, float2 *__restrict__ out, int stride,
+                            int slot, const int *done) {
+    if (skip(done)) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = in[i];
+        const float hi = __double2float_rn(v);
+        const float lo = __double2float_rn(v - (double)hi);
+        out[i * stride + slot] = make_float2(hi, lo);
     }
 }
 

@@ -40,11 +40,12 @@ __global__ void pack_input(const float *__restrict__ x, int batch, int n_in, int
     }
 }
 
-// dZ = 2 (Y - (T - shift) / scale) / (batch n_out) on valid entries; loss sum
+// dZ = 2 (Y - t_hat) / (batch n_out) on valid entries, t_hat = (T - shift -
+// J x) / scale (J, x optional: the linear skip term); loss sum
 __global__ void mse_grad(const float *__restrict__ Y, int ldy, const float *__restrict__ T, int batch, int n_out,
                          const float *__restrict__ scale, const float *__restrict__ shift, int Mp, int Np,
                          bf16 *__restrict__ dz, bf16 *__restrict__ dzt, float *__restrict__ dz32,
-                         float *__restrict__ loss) {
+                         float *__restrict__ loss, const float *__restrict__ J, const float *__restrict__ x, int K) {
     __shared__ float red[256];
     float acc = 0.0f;
     const float inv = 1.0f / ((float)batch * (float)n_out);
@@ -53,7 +54,10 @@ __global__ void mse_grad(const float *__restrict__ Y, int ldy, const float *__re
         const int m = (int)(e / Np), c = (int)(e % Np);
         float g = 0.0f;
         if (m < batch && c < n_out) {
-            const float t = (T[(int64_t)m * n_out + c] - shift[c]) / scale[c];
+            float lin = 0.0f;
+            if (J)
+                for (int k = 0; k < K; k++) lin = fmaf(J[(int64_t)c * K + k], x[(int64_t)m * K + k], lin);
+            const float t = (T[(int64_t)m * n_out + c] - shift[c] - lin) / scale[c];
             const float r = Y[(int64_t)m * ldy + c] - t;
             acc += r * r;
             g = 2.0f * r * inv;
@@ -197,6 +201,7 @@ struct cut_mlp {
     int device = 0, n_in = 0, n_hid = 0, n_out = 0;
     Layer L[3];
     float *scale = nullptr, *shift = nullptr;   // output affine (targets standardised)
+    float *J = nullptr;                         // linear skip [n_out][n_in] (FP32), or null
     int *err = nullptr;
     long long t = 0;                            // Adam step
     // activations for the largest padded batch seen
@@ -274,11 +279,14 @@ static cut_status forward(cut_mlp *m, int batch, const float *x, cudaStream_t s,
             e.out_t = m->ht[l];
             e.ld_t = Mp;
         } else if (y_out) {
-            // inference: valid region only, with the output affine
+            // inference: valid region only, with the output affine and skip
             e.M = batch;
             e.N = m->n_out;
             e.post_scale = post_scale;
             e.post_shift = post_shift;
+            e.lin_J = m->J;
+            e.lin_x = x;
+            e.lin_k = m->n_in;
             e.out_f32 = y_out;
             e.ld_f32 = m->n_out;
         }
@@ -356,6 +364,23 @@ cut_status cut_mlp_set_output_affine(cut_mlp *m, const float *scale, const float
     return set_ok();
 }
 
+cut_status cut_mlp_set_linear(cut_mlp *m, const float *J) {
+    if (!m) return set_error(CUT_ERR_INVALID_ARG, "cut_mlp_set_linear: null model");
+    cudaSetDevice(m->device);
+    if (!J) {
+        m->J = nullptr;
+        return set_ok();
+    }
+    if (!m->J) {
+        float *d = nullptr;
+        if (m->alloc(&d, (size_t)m->n_out * m->n_in) != cudaSuccess)
+            return set_error(CUT_ERR_OUT_OF_MEMORY, "cut_mlp_set_linear");
+        m->J = d;
+    }
+    cudaMemcpy(m->J, J, (size_t)m->n_out * m->n_in * 4, cudaMemcpyHostToDevice);
+    return set_ok();
+}
+
 int64_t cut_mlp_param_count(const cut_mlp *m) {
     if (!m) return -1;
     int64_t c = 0;
@@ -425,7 +450,7 @@ cut_status cut_mlp_backward(cut_mlp *m, int batch, const float *x, const float *
     // output layer
     mlpk::mse_grad<<<grid_of((int64_t)Mp * L[2].out_p), 256, 0, s>>>(m->z[2], L[2].out_p, target, batch, m->n_out,
                                                                        m->scale, m->shift, Mp, L[2].out_p, m->dzb,
-                                                                       m->dzt, m->dz32, loss);
+                                                                       m->dzt, m->dz32, loss, m->J, x, m->n_in);
     bf16 *dzb = m->dzb, *dzt = m->dzt, *nb = m->dzb2, *nt = m->dzt2;
     float *dz32 = m->dz32, *n32 = m->dz32b;
     for (int l = 2; l >= 0; l--) {

@@ -36,6 +36,9 @@ struct Epi {
     float alpha;                // scale of the product
     const float *post_scale;    // optional per-column affine after bias: v * scale + shift
     const float *post_shift;
+    const float *lin_J;         // optional linear skip: + sum_k J[col][k] x[row][k] (FP32)
+    const float *lin_x;
+    int lin_k;
     float *out_f32;             // [M][ld_f32] or null
     int ld_f32;
     __nv_bfloat16 *out_bf16;    // [M][ld_bf16] or null
@@ -207,6 +210,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 float v = __uint_as_float(r[i]) * ep.alpha;
                 if (ep.bias) v += ep.bias[col];
                 if (ep.post_scale) v = v * ep.post_scale[col] + ep.post_shift[col];
+                if (ep.lin_J) {
+                    float l = 0.0f;
+                    for (int k = 0; k < ep.lin_k; k++)
+                        l = fmaf(ep.lin_J[(int64_t)col * ep.lin_k + k], ep.lin_x[(int64_t)row * ep.lin_k + k], l);
+                    v += l;
+                }
                 if (ep.dgelu_z) v *= dgelu(ep.dgelu_z[(int64_t)row * ep.ldz + col]);
                 if (ep.out_f32) ep.out_f32[(int64_t)row * ep.ld_f32 + col] = v;
                 const float a = ep.act ? gelu(v) : v;

@@ -66,10 +66,15 @@ class Surrogate:
         targets = torch.as_tensor(targets, dtype=torch.float64, device=self.dev)
         self.theta_scale = float(theta.abs().max().item()) or 1.0
         x = (theta / self.theta_scale).contiguous()
-        mu = targets.mean(0)
-        sd = targets.std(0).clamp_min(1e-8)
-        self.mu, self.sd = mu, sd
+        # linear part by least squares (FP64), the network learns the rest
+        A = torch.cat([torch.ones(x.shape[0], 1, dtype=torch.float64, device=self.dev), x.double()], dim=1)
+        coef = torch.linalg.lstsq(A, targets).solution               # [1 + n_in, n]
+        mu, J = coef[0], coef[1:].T.contiguous()
+        resid = targets - A @ coef
+        sd = resid.std(0).clamp_min(1e-9)
+        self.mu, self.sd, self.J = mu, sd, J
         self.net.set_output_affine(sd.float().cpu().numpy(), mu.float().cpu().numpy())
+        self.net.set_linear(J.float().cpu().numpy())
         t32 = targets.float()
         g = torch.Generator(device="cpu").manual_seed(seed)
         N = x.shape[0]

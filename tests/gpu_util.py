@@ -15,13 +15,24 @@ _TMP = tempfile.mkdtemp(prefix="cutg_tests_")
 RTOL = 1e-10
 
 
-def assert_close(got, want, rtol=RTOL, what=""):
+def rhs_floor(h, xs=()):
+    """Absolute floor for right-hand-side comparisons: the terms of
+    P[eta, X] are products xi * x with |xi| <= O(|h|^2), so both sides carry
+    rounding of about 1e-16 of max|h|^2 max|x| times the number of terms.
+    A vector whose exact value is zero (e.g. the particle number, which
+    commutes with every generator) is compared against this floor."""
+    hm = float(np.max(np.abs(h)))
+    xm = max([hm] + [float(np.max(np.abs(x))) for x in xs])
+    return 1e-12 * hm * hm * xm
+
+
+def assert_close(got, want, rtol=RTOL, what="", atol=0.0):
     got = np.asarray(got, dtype=np.float64)
     want = np.asarray(want, dtype=np.float64)
     assert got.shape == want.shape, (got.shape, want.shape)
     scale = float(np.max(np.abs(want))) if want.size else 0.0
     err = np.abs(got - want)
-    lim = rtol * (np.abs(want) + scale) + 1e-300
+    lim = rtol * (np.abs(want) + scale) + atol + 1e-300
     bad = np.nonzero(err > lim)[0]
     assert bad.size == 0, f"{what}: {bad.size} elements off, worst {err.max():.3e} (scale {scale:.3e}) at {bad[:5]}"
 

@@ -1,0 +1,136 @@
+"""Double-float arithmetic, the linear action L(h)x, and the full-size stress
+graph (16 spin-orbitals, ~3.4e8 records) in the launch configuration the
+benchmark times.
+
+Full-size parity is checked on sparse inputs: the Hamiltonian and the
+operands keep a seeded few hundred coefficients, so the oracle's exact
+commutators stay cheap while the kernels still stream every record of the
+real graph; the zero entries must come out exactly zero and every other
+entry within RTOL of the oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import RTOL, assert_close, graph_for, np64, rhs_floor
+from cut_inputs import (ALG_FERMION, cfg2_registry, dipole_operator, molecular_hamiltonian, number_operator,
+                        workload)
+
+pytestmark = pytest.mark.gpu
+
+
+def _mol5():
+    labels = cfg2_registry(5, keep_shared1=0.3, seed=3)
+    h = molecular_hamiltonian(labels, 5, seed=22, scale=0.3)
+    return labels, h, [number_operator(labels, 5), dipole_operator(labels, 5, seed=22)]
+
+
+@pytest.mark.parametrize("name", ["mol8", "mol5_3body", "pauli4"])
+def test_df64_rhs_matches_oracle(name):
+    if name == "mol8":
+        w = workload("molecular_8so")
+        alg, nm, labels, h, xs = w.alg, w.nmodes, w.labels, w.h, w.observables
+    elif name == "pauli4":
+        w = workload("closed_pauli_4q")
+        alg, nm, labels, h = w.alg, w.nmodes, w.labels, w.h
+        xs = [np.random.default_rng(70).normal(size=len(labels))]
+    else:
+        labels, h, xs = _mol5()
+        alg, nm = ALG_FERMION, 5
+    G = graph_for(name + "_df", alg, nm, labels)
+    G.set_arithmetic("df64")
+    dh, dxs = G.rhs(h, xs)
+    want_dh, want_dxs = oracle.rhs(alg, nm, labels, h, xs)
+    fl = rhs_floor(h, xs)
+    assert_close(np64(dh), want_dh, what="dh (df64)", atol=fl)
+    for g_, w_ in zip(dxs, want_dxs):
+        assert_close(np64(g_), w_, what="dx (df64)", atol=fl)
+
+
+def test_df64_flows_match_oracle():
+    from cut_inputs import fermion_registry
+    norb = 4
+    labels = fermion_registry(norb)
+    h = molecular_hamiltonian(labels, norb, seed=71, scale=0.2)
+    xs = [number_operator(labels, norb), dipole_operator(labels, norb, seed=71)]
+    G = graph_for("mol4_df", ALG_FERMION, norb, labels)
+    G.set_arithmetic("df64")
+    hs, xo, st, steps = G.flow(h, xs, method="dp45", s0=0.0, s1=1.0, ds=1e-2, rtol=1e-10, atol=1e-12)
+    f = oracle.stacked_rhs(ALG_FERMION, norb, labels, 2)
+    y, _, _ = oracle.dp45_flow(f, np.concatenate([h] + xs), 0.0, 1.0, 1e-2, 1e-10, 1e-12, replay=steps)
+    n = len(labels)
+    assert_close(np64(hs), y[:n], what="h")
+    assert_close(np64(xo[1]), y[2 * n:], what="D")
+    hs4, _, _, _ = G.flow(h, xs, method="rk4", s0=0.0, s1=0.2, ds=0.02)
+    y4 = oracle.rk4_flow(f, np.concatenate([h] + xs), 0.02, 10)
+    assert_close(np64(hs4), y4[:n], what="h rk4")
+
+
+def test_apply_L_is_the_commutator_stage():
+    import torch
+    labels, h, xs = _mol5()
+    G = graph_for("mol5_3body", ALG_FERMION, 5, labels)
+    dh, dxs, xi = G.rhs(h, xs, want_xi=True)
+    rng = np.random.default_rng(72)
+    extra = [rng.normal(size=len(labels)) for _ in range(5)]
+    got = G.apply_L(xi, [h] + xs + extra)
+    assert torch.equal(got[0], dh) and torch.equal(got[1], dxs[0]) and torch.equal(got[2], dxs[1])
+    _, want = oracle.rhs(ALG_FERMION, 5, labels, h, extra)
+    for g_, w_ in zip(got[3:], want):
+        assert_close(np64(g_), w_, what="L(h) x")
+
+
+def _sparse(v, keep, rng):
+    out = np.zeros_like(v)
+    idx = rng.choice(len(v), keep, replace=False)
+    out[idx] = v[idx]
+    return out
+
+
+@pytest.fixture(scope="module")
+def stress():
+    w = workload("stress_16so")
+    G = graph_for("stress16", w.alg, w.nmodes, w.labels)
+    return w, G
+
+
+@pytest.mark.parametrize("arith", ["fp64", "df64"])
+def test_stress_graph_full_size_sparse_input_parity(stress, arith):
+    w, G = stress
+    assert G.R_g + G.R_L > 3e8
+    rng = np.random.default_rng(73)
+    diag = np.array([int(l) & 0xFFFFFFFF == int(l) >> 32 for l in w.labels])
+    h = _sparse(w.h, 200, rng)
+    d_idx = np.nonzero(diag)[0]
+    keep_d = rng.choice(d_idx, 40, replace=False)
+    h[keep_d] = w.h[keep_d]
+    xs = [_sparse(w.observables[1], 40, rng), _sparse(rng.normal(size=len(w.labels)), 150, rng)]
+    G.set_arithmetic(arith)
+    try:
+        dh, dxs = G.rhs(h, xs)
+    finally:
+        G.set_arithmetic("fp64")
+    want_dh, want_dxs = oracle.rhs(w.alg, w.nmodes, w.labels, h, xs)
+    assert np.count_nonzero(want_dh) > 100
+    for got, want in [(np64(dh), want_dh)] + [(np64(a), b) for a, b in zip(dxs, want_dxs)]:
+        assert np.all(got[want == 0] == 0.0)
+        assert_close(got, want, what=f"stress {arith}")
+
+
+def test_stress_graph_full_size_properties(stress):
+    """Dense seeded input at full size: the particle number commutes with
+    every generator (its right-hand side is exactly zero), and the
+    right-hand side of a Hermitian H is Hermitian: dh(C, A) = dh(A, C)."""
+    w, G = stress
+    dh, (dN, dD) = G.rhs(w.h, w.observables)
+    assert np.all(np64(dN) == 0.0)
+    dh = np64(dh)
+    pos = {int(l): k for k, l in enumerate(w.labels)}
+    mirror = np.array([pos[((int(l) & 0xFFFFFFFF) << 32) | (int(l) >> 32)] for l in w.labels])
+    assert_close(dh[mirror], dh, rtol=1e-12, what="Hermiticity of dH")
+    G.set_arithmetic("df64")
+    try:
+        dh2, _ = G.rhs(w.h, w.observables)
+    finally:
+        G.set_arithmetic("fp64")
+    assert_close(np64(dh2), dh, rtol=1e-12, what="df64 vs fp64 at full size")

@@ -96,3 +96,24 @@ def test_training_reduces_loss():
         m.step(lr=3e-3)
     m.status()
     assert losses[-1] < 0.05 * losses[0], (losses[0], losses[-1])
+
+
+def test_linear_skip_term():
+    """y = scale * y_hat + shift + J x, with J x in FP32 on the CUDA cores."""
+    n_in, n_hid, n_out, B = 32, 512, 848, 200
+    m, layers, X, T, scale, shift = _setup(n_in, n_hid, n_out, B, seed=45)
+    rng = np.random.default_rng(45)
+    J = (rng.normal(size=(n_out, n_in)) * 0.3).astype(np.float32)
+    m.set_linear(J)
+    y = m.forward(X).cpu().numpy().astype(np.float64)
+    Yh, _ = omlp.forward(layers, X.astype(np.float64), emulate=True)
+    want = scale * Yh + shift + X.astype(np.float64) @ J.astype(np.float64).T
+    assert _rel(y, want) < 5e-3
+    # the loss sees targets with the linear part removed: T = shift + J x
+    # (+ scale * network) gives zero residual for the network's own output
+    T_exact = (want).astype(np.float32)
+    loss = m.backward(X, T_exact).cpu().numpy()[0]
+    assert loss < 1e-4
+    m.set_linear(None)
+    y0 = m.forward(X).cpu().numpy().astype(np.float64)
+    assert _rel(y0, scale * Yh + shift) < 5e-3
