@@ -216,6 +216,73 @@ def batched_vs_plain(cg, torch, dev, local, batch=1024, plain_sample=8):
     return out
 
 
+def paper_workload(cg, torch, dev, local, diagnostics=False):
+    """The paper's own stress workload (Sec. 3.2-3.3): the complete five-mode
+    degree-four Pauli-boson registry (4,004 coordinates; 7,017,036 production
+    records, 352,405,216 with the outside-space diagnostics).  Times one
+    retained action for a batch of eight operators (H and seven seeded
+    operators through one generator pass), a 100-step RK4 flow of the same
+    batch, and optionally the action including the diagnostics.  The paper's
+    H100 times are quoted beside them as context (other hardware, unstated
+    kernels and integrator)."""
+    from cut_inputs import pauli_boson_hamiltonian, workload
+    w = workload("pauli_boson_5m4")
+    d = tempfile.mkdtemp(prefix="cutpb_")
+    path = os.path.join(d, "pb5.cutg")
+    st = cg.build_graph(w.alg, w.nmodes, w.labels, path)
+    G = cg.Graph(path, device=local)
+    os.remove(path)
+    h = torch.tensor(w.h, device=dev)
+    xs = [torch.tensor(pauli_boson_hamiltonian(w.labels, 5, seed=100 + i), device=dev) for i in range(7)]
+    R = G.R_g + G.R_L
+
+    def time_call(fn, reps=20):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    X = torch.stack(xs).contiguous()
+    dh, dX = torch.empty_like(h), torch.empty_like(X)
+    import ctypes
+    P = lambda t: ctypes.c_void_p(t.data_ptr())
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    act = lambda: cg.lib().cut_rhs(G._h, P(h), 7, P(X), P(dh), P(dX), None, stream)
+    ms = time_call(act)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    G.flow(h, xs, method="rk4", s0=0.0, s1=0.1, ds=1e-3)
+    torch.cuda.synchronize()
+    flow_s = time.perf_counter() - t0
+    out = {"workload": "Pauli-boson, 5 modes, degree 4 (4,004 coordinates), 8 operators",
+           "records": int(R), "build_s": round(st["seconds_total"], 2),
+           "retained_action_ms": ms, "retained_records_per_s": R / (ms * 1e-3),
+           "paper_h100_retained_action_ms": 0.632,
+           "flow_100_rk4_steps_s": flow_s, "paper_h100_flow_100_steps_s": 0.498}
+    G.close()
+    if diagnostics:
+        path = os.path.join(d, "pb5d.cutg")
+        st = cg.build_graph(w.alg, w.nmodes, w.labels, path, diagnostics=True)
+        Gd = cg.Graph(path, device=local)
+        os.remove(path)
+        C = torch.empty(8, Gd.n_out, dtype=torch.float64, device=dev)
+        act_d = lambda: (cg.lib().cut_rhs(Gd._h, P(h), 7, P(X), P(dh), P(dX), None, stream),
+                         cg.lib().cut_rhs_outside(Gd._h, P(h), 7, P(X), P(C), stream))
+        msd = time_call(act_d, reps=5)
+        out.update({"diag_records": int(Gd.R_g + Gd.R_L + Gd.R_C), "diag_action_ms": msd,
+                    "diag_records_per_s": (Gd.R_g + Gd.R_L + Gd.R_C) / (msd * 1e-3),
+                    "paper_h100_diag_action_ms": 48.439, "diag_build_s": round(st["seconds_total"], 1),
+                    "diag_bundle_gb": round(st["bytes_stored"] / 1e9, 2),
+                    "diag_build_peak_over_stored": round(st["peak_rss_bytes"] / st["bytes_stored"], 3)})
+        Gd.close()
+    return out
+
+
 def run_surrogate(args):
     """Surrogate workload: 50k FP32 batched flows of the 8-orbital model
     (32 parameters theta ~ U(-0.1, 0.1)) train the MLP with the library's
@@ -245,22 +312,27 @@ def run_surrogate(args):
     hist = sur.fit(th_tr, Htr, epochs=args.surrogate_epochs, batch=1024, lr=3e-3)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
+    from cut_inputs import make_label
     diag = np.nonzero([int(l) & 0xFFFFFFFF == int(l) >> 32 for l in w.labels])[0]
+    k0 = int(np.nonzero(w.labels == np.uint64(make_label(1, 1)))[0][0])
     t0 = time.perf_counter()
     exact, _ = sur.flows(th_te, "fp64")
     torch.cuda.synchronize()
     t_fp64 = time.perf_counter() - t0
     pred = sur.predict(th_te)
     err_net = (pred[:, diag] - exact[:, diag]).abs().max(dim=1).values.cpu().numpy()
-    out, ok, tm = sur.screen(th_te, diag, tol=1e-4)
+    err_k0 = (pred[:, k0] - exact[:, k0]).abs().cpu().numpy()
+    out, ok, tm = sur.screen(th_te, [k0], tol=1e-4)
     torch.cuda.synchronize()
     t_screen = tm["predict_s"] + tm["loose_s"] + tm["fallback_s"]
-    err = (out[:, diag] - exact[:, diag]).abs().max(dim=1).values.cpu().numpy()
-    line = {"metric": "surrogate-screened flows per second vs FP64 batched flows", "unit": "flows/s",
-            "value": n_test / t_screen, "baseline_fp64_flows_per_s": n_test / t_fp64,
+    err = (out[:, k0] - exact[:, k0]).abs().cpu().numpy()
+    line = {"metric": "surrogate-screened flows per second vs FP64 batched flows (gate 1e-4 on n_0)",
+            "unit": "flows/s", "value": n_test / t_screen, "baseline_fp64_flows_per_s": n_test / t_fp64,
             "accepted_fraction": float(ok.float().mean().item()),
-            "max_err_diag_served": float(err.max()), "median_net_err_diag": float(np.median(err_net)),
-            "p90_net_err_diag": float(np.percentile(err_net, 90)),
+            "max_err_n0_served": float(err.max()), "median_net_err_n0": float(np.median(err_k0)),
+            "p99_net_err_n0": float(np.percentile(err_k0, 99)),
+            "median_net_err_36diag": float(np.median(err_net)),
+            "frac_queries_36diag_within_1e-4": float(np.mean(err_net <= 1e-4)),
             "train_flows": n_train, "train_flows_s": t_data, "train_s": t_train,
             "loss_first_last": [hist[0], hist[-1]], "timings": tm, "dtype": "bf16 mlp / f32+f64 flows",
             "config": {"workload": "molecular_8so surrogate, 32 parameters", "gate": 1e-4}}
@@ -292,6 +364,9 @@ def main():
     ap.add_argument("--no-df64", action="store_true", help="skip the double-float measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-flow measurement")
     ap.add_argument("--surrogate", action="store_true", help="run the surrogate workload instead")
+    ap.add_argument("--no-paper", action="store_true", help="skip the paper's Pauli-boson workload")
+    ap.add_argument("--paper-diagnostics", action="store_true",
+                    help="also time the 352M-record diagnostic action (builds a 2.8 GB graph)")
     ap.add_argument("--surrogate-train", type=int, default=50000)
     ap.add_argument("--surrogate-epochs", type=int, default=60)
     args = ap.parse_args()
@@ -444,6 +519,7 @@ def main():
     e2e_val = world * 4 * R / e2e_s
 
     batched = None if args.no_batched else batched_vs_plain(cg, torch, dev, local)
+    paper = None if args.no_paper else paper_workload(cg, torch, dev, local, args.paper_diagnostics)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -465,6 +541,7 @@ def main():
             "roofline": roofline,
             "df64": df,
             "batched": batched,
+            "paper_workload": paper,
             "clocks": ck,
             "e2e": {"value": e2e_val, "unit": "records/s",
                     "h2d_bytes_per_step": int(8 * n * nops), "d2h_bytes_per_step": int(8 * n * nops)},

@@ -12,10 +12,10 @@ Label encoding (one uint64 per operator):
     a+_{c1}..a+_{cm} a_{am}..a_{a1} (creators ascending, annihilators
     descending): low 32 bits = creator mask, high 32 bits = annihilator mask.
 """
-from .registry import (ALG_PAULI, ALG_FERMION, pauli_registry, fermion_registry,
+from .registry import (ALG_PAULI, ALG_FERMION, ALG_PAULI_BOSON, pauli_registry, fermion_registry,
                        label_lo, label_hi, make_label, pauli_string, fermion_string,
-                       cfg2_registry)
-from .hamiltonians import (pauli_hamiltonian, molecular_hamiltonian,
+                       cfg2_registry, pauli_boson_label, pauli_boson_parts, pauli_boson_registry)
+from .hamiltonians import (pauli_hamiltonian, molecular_hamiltonian, pauli_boson_hamiltonian,
                            number_operator, dipole_operator, batched_parameters,
                            parameter_directions, Workload, workload)
 

@@ -23,8 +23,9 @@ from itertools import combinations
 
 import numpy as np
 
-from .registry import (ALG_PAULI, ALG_FERMION, pauli_registry, fermion_registry,
-                       cfg2_registry, label_lo, label_hi, make_label, _mask)
+from .registry import (ALG_PAULI, ALG_FERMION, ALG_PAULI_BOSON, pauli_registry, fermion_registry,
+                       cfg2_registry, label_lo, label_hi, make_label, _mask, pauli_boson_label,
+                       pauli_boson_parts, pauli_boson_registry)
 
 
 def _popcount(v):
@@ -153,6 +154,38 @@ def parameter_directions(labels, norb, n_two_body=24, seed=4):
     return np.stack(cols, axis=1)
 
 
+def pauli_boson_hamiltonian(labels, M, seed=5, sigma_od=0.05):
+    """Seeded real-symmetric Pauli-boson Hamiltonian on a registry.
+
+    Real basis {I, X, iY, Z} x boson monomials: the transpose of label
+    (tau, c, a) is s_tau (tau, a, c) with s = -1 for iY, so a real symmetric
+    H has h(tau, a, c) = s_tau h(tau, c, a).  Diagonal labels (tau in {I, Z},
+    c = a): U(-1, 1) / (1 + |c|); the others N(0, sigma_od) / (1 + |c| + |a|).
+    (The paper's HBQ parameters are not available; this recipe only fixes the
+    structure.)
+    """
+    idx = _index(labels)
+    rng = np.random.default_rng(seed)
+    h = np.zeros(len(labels))
+    for k, lab in enumerate(labels):
+        tau, c, a = pauli_boson_parts(lab, M)
+        deg = sum(c) + sum(a)
+        if tau in (0, 3) and c == a:
+            h[k] = rng.uniform(-1.0, 1.0) / (1 + sum(c))
+            continue
+        t = idx.get(pauli_boson_label(tau, a, c))
+        if t is None or t < k:
+            continue
+        sgn = -1.0 if tau == 2 else 1.0
+        if t == k:
+            h[k] = 0.0 if sgn < 0 else rng.normal(0.0, sigma_od) / (1 + deg)
+            continue
+        v = rng.normal(0.0, sigma_od) / (1 + deg)
+        h[k] = v
+        h[t] = sgn * v
+    return h
+
+
 @dataclass
 class Workload:
     name: str
@@ -190,6 +223,13 @@ def workload(name, **kw):
         hmax = np.max(np.abs(h))
         return Workload(name, ALG_FERMION, norb, labels, h, obs, "dp45", 10.0, 1e-2,
                         1e-10, 1e-12 * hmax, max(ranks))
+    if name.startswith("pauli_boson_"):
+        # pauli_boson_<M>m<p>: M modes, complete degree-p registry
+        M, p = name[len("pauli_boson_"):].split("m")
+        M, p = int(M), int(p)
+        labels = pauli_boson_registry(M, p)
+        h = pauli_boson_hamiltonian(labels, M, seed=kw.get("seed", 5))
+        return Workload(name, ALG_PAULI_BOSON, M, labels, h, [], "rk4", 1.0, 1e-3, 1e-10, 0.0, p)
     if name.startswith("stress_") and name.endswith("so"):
         norb = int(name[len("stress_"):-2])
         labels = cfg2_registry(norb, keep_shared1=STRESS_KEEP_SHARED1, keep_shared0=STRESS_KEEP_SHARED0,

@@ -8,6 +8,14 @@ import numpy as np
 
 ALG_PAULI = 0
 ALG_FERMION = 1
+ALG_PAULI_BOSON = 2
+
+# Pauli-boson labels sigma_tau prod_m (b_m^+)^{c_m} b_m^{a_m} (Sec. 2.1, Eq.
+# monomial), with the Pauli factor taken from the real basis
+# {I, X, iY, Z} (tau = 0, 1, 2, 3) so that every coefficient is real:
+# bits 0-1 tau, then per mode m: c_m in bits 2+10m .. 6+10m, a_m in bits
+# 7+10m .. 11+10m (degrees up to 31, at most 6 modes).
+PB_BITS = 5
 
 _PAULI_DIGIT = {"I": (0, 0), "X": (1, 0), "Y": (1, 1), "Z": (0, 1)}
 
@@ -114,3 +122,43 @@ def cfg2_registry(norb=16, keep_shared1=0.0, seed=2, keep_shared0=0.0):
                 sel.append(make_label(_mask(c), _mask(a)))
     base = fermion_registry(norb, ranks=(1, 2))
     return np.concatenate([base, np.array(sel, dtype=np.uint64)])
+
+
+def pauli_boson_label(tau, c, a):
+    lab = int(tau) & 3
+    for m, (cm, am) in enumerate(zip(c, a)):
+        assert 0 <= cm < 32 and 0 <= am < 32
+        lab |= int(cm) << (2 + 10 * m)
+        lab |= int(am) << (7 + 10 * m)
+    return lab
+
+
+def pauli_boson_parts(label, M):
+    label = int(label)
+    tau = label & 3
+    c = tuple((label >> (2 + 10 * m)) & 31 for m in range(M))
+    a = tuple((label >> (7 + 10 * m)) & 31 for m in range(M))
+    return tau, c, a
+
+
+def _multi_indices(nvar, deg):
+    """All tuples of nvar non-negative integers with sum exactly deg."""
+    if nvar == 1:
+        yield (deg,)
+        return
+    for first in range(deg, -1, -1):
+        for rest in _multi_indices(nvar - 1, deg - first):
+            yield (first,) + rest
+
+
+def pauli_boson_registry(M, p):
+    """Complete degree-p registry: every (tau, c, a) with |c| + |a| <= p,
+    ordered by total degree, then tau, then the exponents.  Its size is
+    N_op(M, p) = 4 C(2M + p, p) (Eq. basis-size)."""
+    out = []
+    for deg in range(p + 1):
+        idx = list(_multi_indices(2 * M, deg))
+        for tau in range(4):
+            for ca in idx:
+                out.append(pauli_boson_label(tau, ca[:M], ca[M:]))
+    return np.array(out, dtype=np.uint64)

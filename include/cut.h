@@ -13,8 +13,11 @@
  * Conventions shared by every entry point
  *   - Coefficients are real doubles.  For Pauli strings H = sum_k h_k P_k with
  *     Hermitian P_k and eta = i sum_a xi_a G_a; for fermion monomials
- *     H = sum_k h_k O_k and eta = sum_a xi_a G_a.  All stored factors are
- *     exact integers (or rationals num/den), never rounded.
+ *     H = sum_k h_k O_k and eta = sum_a xi_a G_a; for Pauli-boson monomials
+ *     (Sec. 2.1, Eq. monomial) the Pauli factor is taken from the real basis
+ *     {I, X, iY, Z}, so H = sum_k h_k B_k and eta = sum_a xi_a G_a with real
+ *     coefficients as well.  All stored factors are exact integers (or
+ *     rationals num/den), never rounded.
  *   - A coefficient vector has n entries in the order of the registry the
  *     graph was built from (cut_graph_labels); xi has n_g entries in the
  *     order of the generator registry.
@@ -57,7 +60,7 @@ typedef enum {
     CUT_ERR_UNSUPPORTED = 11
 } cut_status;
 
-enum { CUT_ALG_PAULI = 0, CUT_ALG_FERMION = 1 };
+enum { CUT_ALG_PAULI = 0, CUT_ALG_FERMION = 1, CUT_ALG_PAULI_BOSON = 2 };
 enum { CUT_RK4 = 0, CUT_DP45 = 1 };
 enum { CUT_FP64 = 0, CUT_FP32REC_FP64STATE = 1 };
 enum { CUT_ARITH_FP64 = 0, CUT_ARITH_DF64 = 1 };
@@ -70,12 +73,15 @@ const char *cut_version(void);
 /* Compile (Sec. 2.2-2.3): registry -> two-traversal build -> bundle    */
 /* ------------------------------------------------------------------ */
 typedef struct {
-    int algebra;   /* CUT_ALG_PAULI or CUT_ALG_FERMION */
-    int nmodes;    /* qubits / spin-orbitals, 1..32 */
+    int algebra;   /* CUT_ALG_PAULI, CUT_ALG_FERMION or CUT_ALG_PAULI_BOSON */
+    int nmodes;    /* qubits / spin-orbitals 1..32, boson modes 1..6 */
     int max_rank;  /* fermion: highest rank of generator coordinates kept
                       (terms of eta of higher rank cannot reach a registry of
                       that rank); 0 = the registry's highest rank */
     int threads;   /* host threads, 0 = all cores */
+    int diagnostics; /* 1: also store the outside-space records gamma of
+                        Eq. graph-actions (terms of [eta, X] outside the
+                        registry, Eq. projected-flow), with eta exact */
 } cut_build_opts;
 
 typedef struct {
@@ -115,17 +121,21 @@ typedef struct {
     uint8_t sha256[32];      /* digest of the bundle payload */
     int64_t device_bytes;    /* graph bytes resident on the device */
     int64_t record_bytes;    /* bytes of one stored record (both stages) */
+    int64_t n_out, R_C;      /* outside-space labels and records (0 without diagnostics) */
 } cut_graph_desc;
 
 cut_status cut_graph_query(const cut_graph *g, cut_graph_desc *out);
 /* host out: labels[n], gen_labels[n_g], diag[n] (1 = block-diagonal
  * coordinate, the mask D of Sec. 2.2); any pointer may be NULL. */
 cut_status cut_graph_labels(const cut_graph *g, uint64_t *labels, uint64_t *gen_labels, uint8_t *diag);
+/* host out: the outside-space labels out[n_out] (diagnostic graphs). */
+cut_status cut_graph_outside_labels(const cut_graph *g, uint64_t *out);
 /* host out: exact factor table, value of code c = num[c] / den[c]. */
 cut_status cut_graph_weights(const cut_graph *g, int32_t *num, int32_t *den);
 /* host out: the stored records of one stage (0 = generator, rows are
  * generator coordinates a, inputs (i, j); 1 = commutator, rows are outputs
- * k, inputs (a, j)).  row_ptr[rows+1], in1[R], in2[R], code[R]. */
+ * k, inputs (a, j); 2 = outside space, rows are outside labels q, inputs
+ * (a, j)).  row_ptr[rows+1], in1[R], in2[R], code[R]. */
 cut_status cut_graph_records(const cut_graph *g, int stage, int64_t *row_ptr, int32_t *in1,
                              int32_t *in2, uint8_t *code);
 
@@ -161,6 +171,36 @@ cut_status cut_graph_set_arithmetic(cut_graph *g, int arith);
  * Errors: INVALID_ARG, CUDA. */
 cut_status cut_apply_L(const cut_graph *g, const double *xi, int n_ops, const double *x, double *dx,
                        cut_stream_t stream);
+
+/* Outside-space diagnostic action (Eq. graph-actions, third line; Eq.
+ * projected-flow): C_q = sum_e gamma_e xi_{a_e} x_{j_e} for the operands
+ * X_0 = H and X_1.. of cut_rhs, for every label q outside the registry that
+ * [eta, X] generates.  Needs a graph built with diagnostics; it neither
+ * reads nor changes anything the retained flow uses.
+ * device in : h[n], x[n_obs][n]; device out: c[(1 + n_obs)][n_out]
+ * Errors: INVALID_ARG (no diagnostic records), CUDA. */
+cut_status cut_rhs_outside(const cut_graph *g, const double *h, int n_obs, const double *x, double *c,
+                           cut_stream_t stream);
+
+/* Multi-operator assembly (Sec. 2.4, last paragraph): from a library of
+ * already transformed source operators X_i (coefficient vectors), form
+ * out_m = sum_i C[m][i] X_i for n_out combinations, without touching the
+ * graph.  The sum runs over i in index order with FMA, so results are the
+ * same bits on every run.  Uses the current CUDA device.
+ * device in : X[n_src][n], C[n_out][n_src]; device out: out[n_out][n]
+ * Errors: INVALID_ARG (1 <= n_src <= 3000), CUDA. */
+cut_status cut_assemble(int n_src, int64_t n, const double *X, int n_out, const double *C, double *out,
+                        cut_stream_t stream);
+
+/* Forward tangent (Sec. 2.4, Eq. directional-derivative): the directional
+ * derivative of cut_rhs along (dh, dx),
+ *   d F_o = dF_o/dh . dh + L(h) dx_o      (X_0 = H, so dx_0 = dh),
+ * including the induced variation of the generator.
+ * device in : h[n], x[n_obs][n], dh[n], dx[n_obs][n]
+ * device out: out_h[n], out_x[n_obs][n]
+ * Errors: INVALID_ARG, CUDA. */
+cut_status cut_rhs_jvp(const cut_graph *g, const double *h, int n_obs, const double *x, const double *dh,
+                       const double *dx, double *out_h, double *out_x, cut_stream_t stream);
 
 /* Allocation-free variant of cut_rhs.  The paper has no counterpart; it
  * exists for callers that may not allocate device memory while they run

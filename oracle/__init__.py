@@ -32,6 +32,7 @@ from . import build as _build
 
 ALG_PAULI = 0
 ALG_FERMION = 1
+ALG_PAULI_BOSON = 2
 
 _lib = None
 
@@ -101,6 +102,10 @@ def is_diagonal(alg, label):
     lo, hi = label & 0xFFFFFFFF, label >> 32
     if alg == ALG_PAULI:
         return lo == 0                 # no X or Y factor
+    if alg == ALG_PAULI_BOSON:         # I or Z Pauli factor, c = a in every mode
+        if (label & 3) in (1, 2):
+            return False
+        return all(((label >> (2 + 10 * m)) & 31) == ((label >> (7 + 10 * m)) & 31) for m in range(6))
     return lo == hi                    # creator set == annihilator set
 
 
@@ -199,6 +204,24 @@ def rhs_vjp(alg, nmodes, labels, h, xs, w_h, w_xs):
         h_bar[i] = sum(c_of(g) * v for g, v in d_eta.items() if v != 0)
     h_bar += x_bar[0]
     return _real(h_bar, "h_bar"), [_real(v, "x_bar") for v in x_bar[1:]]
+
+
+def rhs_jvp(alg, nmodes, labels, h, xs, dh, dxs, eps=0.25):
+    """Directional derivative of the right-hand side (Sec. 2.4, Eq.
+    directional-derivative).  The right-hand side is a polynomial of degree 3
+    in (h, x), so the five-point central formula
+    (-f(2e) + 8 f(e) - 8 f(-e) + f(-2e)) / (12 e) is exact up to rounding."""
+    h = np.asarray(h, dtype=np.float64)
+    dh = np.asarray(dh, dtype=np.float64)
+    xs = [np.asarray(x, dtype=np.float64) for x in xs]
+    dxs = [np.asarray(x, dtype=np.float64) for x in dxs]
+
+    def f(t):
+        a, b = rhs(alg, nmodes, labels, h + t * dh, [x + t * d for x, d in zip(xs, dxs)])
+        return [a] + list(b)
+    fm2, fm1, fp1, fp2 = f(-2 * eps), f(-eps), f(eps), f(2 * eps)
+    out = [(-p2 + 8 * p1 - 8 * m1 + m2) / (12 * eps) for m2, m1, p1, p2 in zip(fm2, fm1, fp1, fp2)]
+    return out[0], out[1:]
 
 
 # ---------------------------------------------------------------------------

@@ -22,7 +22,7 @@
  *
  * Operators are sums of (label, complex coefficient); the label encoding is
  * the one of the cut_inputs package (Pauli: x mask | z mask << 32; fermion:
- * creator mask | annihilator mask << 32).
+ * creator mask | annihilator mask << 32; Pauli-boson: see pb_product).
  */
 #include <complex.h>
 #include <stdint.h>
@@ -206,8 +206,93 @@ static void fermion_product(uint64_t a, uint64_t b, cplx coef, oracle_op *out) {
     normal_order(ops, n, coef, out);
 }
 
+/* ------------------------------------------------------------------ */
+/* Pauli-boson monomials sigma_tau prod_m (b_m+)^c_m b_m^a_m            */
+/* ------------------------------------------------------------------ */
+/* The Pauli factor lives in the real basis I, X, iY, Z (2x2 real matrices);
+ * a product of two basis matrices is decomposed back onto the basis with
+ * the trace inner product (the four matrices are orthogonal, norm^2 = 2).
+ * Each boson mode is handled on its own (modes commute): the normal-ordered
+ * factor of A is multiplied on the right by the ladder operators of B one at
+ * a time, using
+ *   (b+)^c b^a . b  = (b+)^c b^(a+1)
+ *   (b+)^c b^a . b+ = (b+)^(c+1) b^a + a (b+)^c b^(a-1)     ([b^a, b+] = a b^(a-1)).
+ * Label: bits 0-1 tau, mode m: c at bits 2+10m (5 bits), a at bits 7+10m. */
+#define ALG_PAULI_BOSON 2
+#define PB_MAXDEG 64
+
+static const double RMAT[4][2][2] = {{{1, 0}, {0, 1}}, {{0, 1}, {1, 0}}, {{0, 1}, {-1, 0}}, {{1, 0}, {0, -1}}};
+
+static int pb_get(uint64_t l, int shift) { return (int)((l >> shift) & 31); }
+
+/* one mode: coefficients of (b+)^C b^A, returned in poly[C][A] */
+static void boson_mode_product(int c1, int a1, int c2, int a2, double poly[PB_MAXDEG][PB_MAXDEG]) {
+    static double cur[PB_MAXDEG][PB_MAXDEG], nxt[PB_MAXDEG][PB_MAXDEG];
+    memset(cur, 0, sizeof(cur));
+    cur[c1][a1] = 1.0;
+    for (int step = 0; step < c2 + a2; step++) {
+        const int create = step < c2;   /* B = (b+)^c2 b^a2: the b+ factors first */
+        memset(nxt, 0, sizeof(nxt));
+        for (int c = 0; c < PB_MAXDEG; c++)
+            for (int a = 0; a < PB_MAXDEG; a++) {
+                double v = cur[c][a];
+                if (v == 0.0) continue;
+                if (!create) {
+                    nxt[c][a + 1] += v;
+                } else {
+                    nxt[c + 1][a] += v;
+                    if (a > 0) nxt[c][a - 1] += a * v;
+                }
+            }
+        memcpy(cur, nxt, sizeof(cur));
+    }
+    memcpy(poly, cur, sizeof(cur));
+}
+
+static void pb_product(int nmodes, uint64_t x, uint64_t y, cplx coef, oracle_op *out) {
+    /* Pauli part */
+    double P[2][2] = {{0, 0}, {0, 0}};
+    const int t1 = (int)(x & 3), t2 = (int)(y & 3);
+    for (int i = 0; i < 2; i++)
+        for (int j = 0; j < 2; j++)
+            for (int k = 0; k < 2; k++) P[i][j] += RMAT[t1][i][k] * RMAT[t2][k][j];
+    /* boson part: list of (label bits, coefficient), mode by mode */
+    static uint64_t lab[2][65536];
+    static double val[2][65536];
+    static double poly[PB_MAXDEG][PB_MAXDEG];
+    int n = 1, cur = 0;
+    lab[0][0] = 0;
+    val[0][0] = 1.0;
+    for (int m = 0; m < nmodes; m++) {
+        const int sc = 2 + 10 * m, sa = 7 + 10 * m;
+        boson_mode_product(pb_get(x, sc), pb_get(x, sa), pb_get(y, sc), pb_get(y, sa), poly);
+        int nn = 0;
+        for (int c = 0; c < PB_MAXDEG; c++)
+            for (int a = 0; a < PB_MAXDEG; a++) {
+                if (poly[c][a] == 0.0) continue;
+                if (c > 31 || a > 31) abort();   /* beyond the 5-bit label fields */
+                for (int i = 0; i < n; i++) {
+                    lab[1 - cur][nn] = lab[cur][i] | ((uint64_t)c << sc) | ((uint64_t)a << sa);
+                    val[1 - cur][nn] = val[cur][i] * poly[c][a];
+                    nn++;
+                }
+            }
+        cur = 1 - cur;
+        n = nn;
+    }
+    for (int t = 0; t < 4; t++) {
+        double tr = 0.0;   /* Tr(R_t^T P) / 2 */
+        for (int i = 0; i < 2; i++)
+            for (int j = 0; j < 2; j++) tr += RMAT[t][i][j] * P[i][j];
+        tr *= 0.5;
+        if (tr == 0.0) continue;
+        for (int i = 0; i < n; i++) op_add(out, lab[cur][i] | (uint64_t)t, coef * tr * val[cur][i]);
+    }
+}
+
 static void product_into(int alg, int nmodes, uint64_t a, uint64_t b, cplx coef, oracle_op *out) {
     if (alg == ALG_PAULI) pauli_product(nmodes, a, b, coef, out);
+    else if (alg == ALG_PAULI_BOSON) pb_product(nmodes, a, b, coef, out);
     else fermion_product(a, b, coef, out);
 }
 

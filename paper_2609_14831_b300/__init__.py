@@ -32,7 +32,7 @@ class CutError(RuntimeError):
 
 class BuildOpts(ctypes.Structure):
     _fields_ = [("algebra", ctypes.c_int), ("nmodes", ctypes.c_int), ("max_rank", ctypes.c_int),
-                ("threads", ctypes.c_int)]
+                ("threads", ctypes.c_int), ("diagnostics", ctypes.c_int)]
 
 
 class BuildStats(ctypes.Structure):
@@ -47,7 +47,8 @@ class GraphDesc(ctypes.Structure):
     _fields_ = [("algebra", ctypes.c_int), ("nmodes", ctypes.c_int), ("max_rank", ctypes.c_int),
                 ("n_codes", ctypes.c_int), ("n", ctypes.c_int64), ("n_g", ctypes.c_int64),
                 ("R_g", ctypes.c_int64), ("R_L", ctypes.c_int64), ("sha256", ctypes.c_uint8 * 32),
-                ("device_bytes", ctypes.c_int64), ("record_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("record_bytes", ctypes.c_int64),
+                ("n_out", ctypes.c_int64), ("R_C", ctypes.c_int64)]
 
 
 class FlowOpts(ctypes.Structure):
@@ -85,12 +86,16 @@ def lib():
         "cut_graph_query": (st, [VP, ctypes.POINTER(GraphDesc)]),
         "cut_graph_labels": (st, [VP, VP, VP, VP]),
         "cut_graph_weights": (st, [VP, VP, VP]),
+        "cut_graph_outside_labels": (st, [VP, VP]),
+        "cut_rhs_outside": (st, [VP, VP, i, VP, VP, VP]),
         "cut_graph_records": (st, [VP, i, VP, VP, VP, VP]),
         "cut_rhs": (st, [VP, VP, i, VP, VP, VP, VP, VP]),
         "cut_rhs_adjoint": (st, [VP, VP, i, VP, VP, VP, VP, VP, VP]),
         "cut_rhs_noalloc": (st, [VP, VP, i, VP, VP, VP, VP]),
         "cut_graph_set_arithmetic": (st, [VP, i]),
         "cut_apply_L": (st, [VP, VP, i, VP, VP, VP]),
+        "cut_rhs_jvp": (st, [VP, VP, i, VP, VP, VP, VP, VP, VP]),
+        "cut_assemble": (st, [i, i64, VP, i, VP, VP, VP]),
         "cut_flow": (st, [VP, VP, i, VP, ctypes.POINTER(FlowOpts), ctypes.POINTER(FlowStats), VP]),
         "cut_flow_vjp": (st, [VP, VP, i, VP, ctypes.POINTER(FlowOpts), i, VP, VP, VP, VP, VP]),
         "cut_flow_batched": (st, [VP, i, VP, i, VP, i, ctypes.POINTER(FlowOpts), i, VP, VP, VP]),
@@ -120,10 +125,10 @@ def check(status):
         raise CutError(status, lib().cut_last_error().decode())
 
 
-def build_graph(algebra, nmodes, labels, path, max_rank=0, threads=0):
+def build_graph(algebra, nmodes, labels, path, max_rank=0, threads=0, diagnostics=False):
     """Compile the operation graph of a registry into a bundle file."""
     labels = np.ascontiguousarray(labels, dtype=np.uint64)
-    opts = BuildOpts(int(algebra), int(nmodes), int(max_rank), int(threads))
+    opts = BuildOpts(int(algebra), int(nmodes), int(max_rank), int(threads), 1 if diagnostics else 0)
     st = BuildStats()
     check(lib().cut_build(ctypes.byref(opts), len(labels), labels.ctypes.data, os.fsencode(path),
                           ctypes.byref(st)))
@@ -155,6 +160,16 @@ def _dev_f64(t, n, name, device):
     return t
 
 
+def assemble(X, C, stream=None):
+    """out[m] = sum_i C[m, i] X[i] (multi-operator assembly, FP64, fixed order)."""
+    torch = _torch()
+    X = X.to(dtype=torch.float64).contiguous()
+    C = C.to(device=X.device, dtype=torch.float64).contiguous()
+    out = torch.empty(C.shape[0], X.shape[1], dtype=torch.float64, device=X.device)
+    check(lib().cut_assemble(X.shape[0], X.shape[1], _ptr(X), C.shape[0], _ptr(C), _ptr(out), _stream(stream)))
+    return out
+
+
 class Graph:
     """A loaded operation graph resident on one CUDA device."""
 
@@ -168,6 +183,7 @@ class Graph:
                      for f, _ in GraphDesc._fields_}
         self.n, self.n_g = d.n, d.n_g
         self.R_g, self.R_L = d.R_g, d.R_L
+        self.n_out, self.R_C = d.n_out, d.R_C
 
     def close(self):
         if self._h:
@@ -199,9 +215,24 @@ class Graph:
         check(lib().cut_graph_weights(self._h, num.ctypes.data, den.ctypes.data))
         return num, den
 
+    def outside_labels(self):
+        out = np.empty(max(1, self.n_out), dtype=np.uint64)
+        check(lib().cut_graph_outside_labels(self._h, out.ctypes.data))
+        return out[:self.n_out]
+
+    def rhs_outside(self, h, xs=(), stream=None):
+        """Outside-space diagnostic C_q for H and the operands: [1 + n_obs, n_out]."""
+        torch = _torch()
+        h = _dev_f64(h, self.n, "h", self.device)
+        n_obs = len(xs)
+        x = torch.stack([_dev_f64(v, self.n, "x", self.device) for v in xs]) if n_obs else None
+        c = torch.empty(1 + n_obs, max(1, self.n_out), dtype=torch.float64, device=self.device)
+        check(lib().cut_rhs_outside(self._h, _ptr(h), n_obs, _ptr(x), _ptr(c), _stream(stream)))
+        return c[:, :self.n_out]
+
     def records(self, stage):
-        rows = self.n_g if stage == 0 else self.n
-        R = self.R_g if stage == 0 else self.R_L
+        rows = (self.n_g, self.n, self.n_out)[stage]
+        R = (self.R_g, self.R_L, self.R_C)[stage]
         rp = np.empty(rows + 1, dtype=np.int64)
         a = np.empty(max(R, 1), dtype=np.int32)
         b = np.empty(max(R, 1), dtype=np.int32)
@@ -238,6 +269,20 @@ class Graph:
         dx = torch.empty_like(x)
         check(lib().cut_apply_L(self._h, _ptr(xi), x.shape[0], _ptr(x), _ptr(dx), _stream(stream)))
         return list(dx)
+
+    def rhs_jvp(self, h, xs, dh, dxs, stream=None):
+        """Directional derivative of rhs() along (dh, dxs)."""
+        torch = _torch()
+        h = _dev_f64(h, self.n, "h", self.device)
+        dh = _dev_f64(dh, self.n, "dh", self.device)
+        n_obs = len(xs)
+        x = torch.stack([_dev_f64(v, self.n, "x", self.device) for v in xs]) if n_obs else None
+        dx = torch.stack([_dev_f64(v, self.n, "dx", self.device) for v in dxs]) if n_obs else None
+        oh = torch.empty_like(h)
+        ox = torch.empty_like(x) if n_obs else None
+        check(lib().cut_rhs_jvp(self._h, _ptr(h), n_obs, _ptr(x), _ptr(dh), _ptr(dx), _ptr(oh), _ptr(ox),
+                                _stream(stream)))
+        return oh, (list(ox) if n_obs else [])
 
     def rhs_adjoint(self, h, xs, w_h, w_xs, stream=None):
         """Vector-Jacobian product of rhs(): (h_bar, [x_bar_o])."""

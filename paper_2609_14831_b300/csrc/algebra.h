@@ -78,16 +78,82 @@ static inline int fermion_mul(uint64_t a, uint64_t b, uint64_t *out, int *sgn) {
     return cnt;
 }
 
+// Pauli-boson label: bits 0-1 tau (real Pauli basis I, X, iY, Z), mode m:
+// c_m = bits 2+10m..6+10m, a_m = bits 7+10m..11+10m.
+constexpr int kPBModes = 6;
+static inline int pb_tau(uint64_t l) { return (int)(l & 3); }
+static inline int pb_c(uint64_t l, int m) { return (int)((l >> (2 + 10 * m)) & 31); }
+static inline int pb_a(uint64_t l, int m) { return (int)((l >> (7 + 10 * m)) & 31); }
+static inline int pb_degree(uint64_t l) {
+    int d = 0;
+    for (int m = 0; m < kPBModes; m++) d += pb_c(l, m) + pb_a(l, m);
+    return d;
+}
+
+// Real Pauli basis R = {I, X, iY, Z}: R_a R_b = PB_SGN[a][b] R_{a^b}.
+static const int PB_SGN[4][4] = {{1, 1, 1, 1}, {1, 1, -1, -1}, {1, 1, -1, -1}, {1, 1, 1, 1}};
+
+static inline int64_t binom(int n, int k) {
+    if (k < 0 || k > n) return 0;
+    int64_t r = 1;
+    for (int i = 1; i <= k; i++) r = r * (n - k + i) / i;
+    return r;
+}
+
+// sigma_t1 B(c1,a1) sigma_t2 B(c2,a2): the Pauli factors multiply in the real
+// basis; per mode (b+)^{c1} b^{a1} (b+)^{c2} b^{a2} =
+//   sum_k k! C(a1,k) C(c2,k) (b+)^{c1+c2-k} b^{a1+a2-k}  (normal ordering).
+// Writes the terms (at most prod_m (min(a1_m, c2_m) + 1)); returns the count,
+// or -1 when an exponent would exceed 31 or a factor would not stay an exact
+// 32-bit integer.
+static inline int pb_mul(uint64_t x, uint64_t y, uint64_t *out, int64_t *coef, int cap) {
+    const int t1 = pb_tau(x), t2 = pb_tau(y);
+    int n = 1;
+    out[0] = (uint64_t)(t1 ^ t2);
+    coef[0] = PB_SGN[t1][t2];
+    for (int m = 0; m < kPBModes; m++) {
+        const int c1 = pb_c(x, m), a1 = pb_a(x, m), c2 = pb_c(y, m), a2 = pb_a(y, m);
+        if (!(c1 | a1 | c2 | a2)) continue;
+        const int kmax = a1 < c2 ? a1 : c2;
+        if (c1 + c2 > 31 || a1 + a2 > 31) return -1;
+        const int n0 = n;
+        if (n0 * (kmax + 1) > cap) return -1;
+        for (int k = kmax; k >= 0; k--) {
+            int64_t f = binom(a1, k) * binom(c2, k);
+            for (int t = 2; t <= k; t++) f *= t;
+            const uint64_t bits = ((uint64_t)(c1 + c2 - k) << (2 + 10 * m)) | ((uint64_t)(a1 + a2 - k) << (7 + 10 * m));
+            for (int i = 0; i < n0; i++) {
+                const int dst = k == 0 ? i : n + i;
+                out[dst] = out[i] | bits;
+                coef[dst] = coef[i] * f;
+                if (coef[dst] > 0x3FFFFFFFll || coef[dst] < -0x3FFFFFFFll) return -1;  // keep factors exact in int32
+            }
+            if (k > 0) n += n0;
+        }
+    }
+    return n;
+}
+
 static inline void add_term(Term *buf, int &n, uint64_t label, int re, int im) {
     for (int i = 0; i < n; i++)
         if (buf[i].label == label) { buf[i].re += re; buf[i].im += im; return; }
     buf[n++] = {label, re, im};
 }
 
-// [A, B] = AB - BA with like terms combined and zeros dropped.  buf >= 64.
+// [A, B] = AB - BA with like terms combined and zeros dropped.  buf >= 512
+// for Pauli-boson labels (returns -1 if the product leaves the label range).
 static inline int commutator(int alg, uint64_t a, uint64_t b, Term *buf) {
     int n = 0;
-    if (alg == 0) {
+    if (alg == 2) {
+        uint64_t lab[256];
+        int64_t cf[256];
+        int m = pb_mul(a, b, lab, cf, 256);
+        if (m < 0) return -1;
+        for (int i = 0; i < m; i++) add_term(buf, n, lab[i], (int)cf[i], 0);
+        m = pb_mul(b, a, lab, cf, 256);
+        if (m < 0) return -1;
+        for (int i = 0; i < m; i++) add_term(buf, n, lab[i], -(int)cf[i], 0);
+    } else if (alg == 0) {
         static const int RE[4] = {1, 0, -1, 0}, IM[4] = {0, 1, 0, -1};
         uint64_t c;
         int k = pauli_mul(a, b, &c);
@@ -109,10 +175,18 @@ static inline int commutator(int alg, uint64_t a, uint64_t b, Term *buf) {
 }
 
 static inline bool is_diagonal(int alg, uint64_t l) {
+    if (alg == 2) {  // I or Z Pauli factor and c = a in every mode
+        if (pb_tau(l) == 1 || pb_tau(l) == 2) return false;
+        for (int m = 0; m < kPBModes; m++)
+            if (pb_c(l, m) != pb_a(l, m)) return false;
+        return true;
+    }
     return alg == 0 ? lo32(l) == 0 : lo32(l) == hi32(l);
 }
 
+// fermion: particle rank; Pauli: weight; Pauli-boson: total boson degree
 static inline int rank_of(int alg, uint64_t l) {
+    if (alg == 2) return pb_degree(l);
     return alg == 0 ? popc(lo32(l) | hi32(l)) : popc(lo32(l));
 }
 

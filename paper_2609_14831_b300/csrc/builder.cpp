@@ -128,6 +128,7 @@ struct Ctx {
     std::vector<std::vector<int32_t>> byC, byA;  // fermion: operands with p in C / in A
     std::unordered_map<uint32_t, std::vector<int32_t>> byCset, byAset;  // operands by exact C / A set
     int reg_rank = 0;                            // highest rank in the registry
+    int diagnostics = 0;                         // keep outside-space records
     LabelIndex *reg = nullptr;
 };
 
@@ -135,37 +136,46 @@ struct Ctx {
 // off-diagonal j, with rank(g) <= max_rank.
 template <class F>
 void gen_terms(const Ctx &c, int64_t lo, int64_t hi, F emit) {
-    Term buf[64];
+    Term buf[512];
     const int64_t no = (int64_t)c.off_idx.size();
     for (int64_t f = lo; f < hi; f++) {
         int32_t i = c.diag_idx[f / no], j = c.off_idx[f % no];
         int m = commutator(c.alg, c.labels[i], c.labels[j], buf);
+        if (m < 0) throw std::invalid_argument("a product leaves the label range (boson degree > 31) or its factor is not an exact 32-bit integer");
         for (int t = 0; t < m; t++) {
-            if (c.alg == 1 && rank_of(1, buf[t].label) > c.max_rank) continue;
+            if (c.alg != 0 && rank_of(c.alg, buf[t].label) > c.max_rank) continue;
             emit(buf[t].label, i, j, gen_factor(c.alg, buf[t]));
         }
     }
 }
 
 // Visit every commutator-stage term for generator labels gl[lo..hi):
-// (k registry index, a, j, beta) with O_k in the registry (projection P).
-template <class F>
+// (k registry index, a, j, beta) with O_k in the registry (projection P);
+// with diagnostics, terms outside the registry go to emit_out(label, a, j,
+// gamma) (the outside-space action of Eq. projected-flow).
+struct NoOut {
+    void operator()(uint64_t, int32_t, int32_t, int) const {}
+};
+
+template <class F, class FO = NoOut>
 void comm_terms(const Ctx &c, const std::vector<uint64_t> &gl, int64_t lo, int64_t hi,
-                std::vector<int32_t> &stamp, F emit) {
-    Term buf[64];
+                std::vector<int32_t> &stamp, F emit, FO emit_out = FO()) {
+    Term buf[512];
     const int32_t n = (int32_t)c.labels.size();
     for (int64_t a = lo; a < hi; a++) {
         uint64_t G = gl[a];
         auto visit = [&](int32_t j) {
             int m = commutator(c.alg, G, c.labels[j], buf);
+            if (m < 0) throw std::invalid_argument("a product leaves the label range (boson degree > 31) or its factor is not an exact 32-bit integer");
             for (int t = 0; t < m; t++) {
                 int32_t k = c.reg->find(buf[t].label);
                 if (k >= 0) emit(k, (int32_t)a, j, comm_factor(c.alg, buf[t]));
+                else if (c.diagnostics) emit_out(buf[t].label, (int32_t)a, j, comm_factor(c.alg, buf[t]));
             }
         };
-        if (c.alg == 0) {
+        if (c.alg != 1) {
             for (int32_t j = 0; j < n; j++) visit(j);
-        } else if (popc(lo32(G)) >= c.reg_rank) {
+        } else if (!c.diagnostics && popc(lo32(G)) >= c.reg_rank) {
             // A generator of the registry's top rank r: a term of G O_j has
             // rank r + r_j - |K| with K the contracted part of C_j, so it stays
             // within rank r only if every creator of O_j is contracted
@@ -248,14 +258,25 @@ void build_graph(const cut_build_opts &o, int64_t n, const uint64_t *labels, Hos
     c.labels.assign(labels, labels + n);
     int reg_rank = 0;
     for (auto l : c.labels) {
-        uint32_t lo = lo32(l), hi = hi32(l);
-        uint64_t modes = o.nmodes == 32 ? 0xFFFFFFFFull : ((1ull << o.nmodes) - 1);
-        if ((lo & ~modes) || (hi & ~modes)) throw std::invalid_argument("label uses a mode beyond nmodes");
-        if (c.alg == 1 && popc(lo) != popc(hi)) throw std::invalid_argument("fermion label is not number conserving");
-        if (c.alg == 1 && popc(lo) == 0) throw std::invalid_argument("the identity is not a registry coordinate");
+        if (c.alg == 2) {
+            if (o.nmodes > kPBModes) throw std::invalid_argument("Pauli-boson labels hold at most 6 modes");
+            const uint64_t used_bits = (o.nmodes == kPBModes) ? ~0ull >> 2 : ((1ull << (2 + 10 * o.nmodes)) - 1);
+            if (l & ~used_bits) throw std::invalid_argument("label uses a mode beyond nmodes");
+        } else {
+            uint32_t lo = lo32(l), hi = hi32(l);
+            uint64_t modes = o.nmodes == 32 ? 0xFFFFFFFFull : ((1ull << o.nmodes) - 1);
+            if ((lo & ~modes) || (hi & ~modes)) throw std::invalid_argument("label uses a mode beyond nmodes");
+            if (c.alg == 1 && popc(lo) != popc(hi)) throw std::invalid_argument("fermion label is not number conserving");
+            if (c.alg == 1 && popc(lo) == 0) throw std::invalid_argument("the identity is not a registry coordinate");
+        }
         reg_rank = std::max(reg_rank, rank_of(c.alg, l));
     }
-    c.max_rank = o.max_rank > 0 ? o.max_rank : reg_rank;
+    c.diagnostics = o.diagnostics ? 1 : 0;
+    // diagnostics need every generator term (eta exact); for fermions terms of
+    // rank above the registry's cannot reach it otherwise.  Pauli-boson
+    // generators are always kept exact (no rank lemma there: contractions
+    // lower the boson degree).
+    c.max_rank = o.max_rank > 0 ? o.max_rank : ((c.diagnostics || c.alg == 2) ? 64 : reg_rank);
     c.reg_rank = reg_rank;
     LabelIndex reg(c.labels);
     c.reg = &reg;
@@ -292,16 +313,34 @@ void build_graph(const cut_build_opts &o, int64_t n, const uint64_t *labels, Hos
     //      generator coordinates reach the registry at all
     std::vector<uint32_t> comm_cnt(n, 0);
     std::vector<uint8_t> used(cand.size(), 0);
+    std::vector<std::unordered_map<uint64_t, uint32_t>> tl_out(T);
     {
         std::vector<std::vector<int32_t>> stamps(T, std::vector<int32_t>(n, -1));
         parallel_chunks(T, (int64_t)cand.size(), 16, [&](int t, int64_t lo, int64_t hi) {
-            comm_terms(c, cand, lo, hi, stamps[t], [&](int32_t k, int32_t a, int32_t, int w) {
-                __atomic_fetch_add(&comm_cnt[k], 1u, __ATOMIC_RELAXED);
-                __atomic_store_n(&used[a], (uint8_t)1, __ATOMIC_RELAXED);
-                tl_w[t].insert(w);
-            });
+            comm_terms(
+                c, cand, lo, hi, stamps[t],
+                [&](int32_t k, int32_t a, int32_t, int w) {
+                    __atomic_fetch_add(&comm_cnt[k], 1u, __ATOMIC_RELAXED);
+                    __atomic_store_n(&used[a], (uint8_t)1, __ATOMIC_RELAXED);
+                    tl_w[t].insert(w);
+                },
+                [&](uint64_t lab, int32_t a, int32_t, int w) {
+                    tl_out[t][lab]++;
+                    __atomic_store_n(&used[a], (uint8_t)1, __ATOMIC_RELAXED);
+                    tl_w[t].insert(w);
+                });
         });
     }
+    // outside-space labels (diagnostics): sorted by rank, then label
+    std::map<uint64_t, uint32_t> out_cnt_map;
+    for (auto &m : tl_out) {
+        for (auto &kv : m) out_cnt_map[kv.first] += kv.second;
+        m.clear();
+    }
+    std::vector<uint64_t> out_labels;
+    for (auto &kv : out_cnt_map) out_labels.push_back(kv.first);
+    std::sort(out_labels.begin(), out_labels.end(), [&](uint64_t x, uint64_t y) { return gen_less(c.alg, x, y); });
+    if ((int64_t)out_labels.size() > (int64_t)kIndexMask) throw std::invalid_argument("outside space beyond 2^24 labels");
     g.gen_labels.clear();
     for (size_t a = 0; a < cand.size(); a++)
         if (used[a]) g.gen_labels.push_back(cand[a]);
@@ -354,6 +393,13 @@ void build_graph(const cut_build_opts &o, int64_t n, const uint64_t *labels, Hos
     if (ng > (int64_t)kIndexMask || n > (int64_t)kIndexMask) throw std::invalid_argument("index beyond 2^24");
     g.rec[0].assign(2 * g.rp[0][ng], 0);
     g.rec[1].assign(2 * g.rp[1][n], 0);
+    g.out_labels = out_labels;
+    const int64_t nout = (int64_t)out_labels.size();
+    g.rp[2].assign(nout + 1, 0);
+    for (int64_t q = 0; q < nout; q++) g.rp[2][q + 1] = g.rp[2][q] + out_cnt_map[out_labels[q]];
+    g.rec[2].assign(2 * g.rp[2][nout], 0);
+    out_cnt_map.clear();
+    LabelIndex oidx(g.out_labels);
     auto t1 = clk::now();
 
     // ---- traversal 2: write every record into its final slot
@@ -372,18 +418,29 @@ void build_graph(const cut_build_opts &o, int64_t n, const uint64_t *labels, Hos
     }
     {
         std::vector<uint64_t> cur(g.rp[1].begin(), g.rp[1].end() - 1);
+        std::vector<uint64_t> ocur(g.rp[2].begin(), g.rp[2].end() - 1);
         uint32_t *rc = g.rec[1].data();
+        uint32_t *oc = g.rec[2].data();
         std::vector<std::vector<int32_t>> stamps(T, std::vector<int32_t>(n, -1));
         parallel_chunks(T, ng, 16, [&](int t, int64_t lo, int64_t hi) {
-            comm_terms(c, g.gen_labels, lo, hi, stamps[t], [&](int32_t k, int32_t a, int32_t j, int w) {
-                uint64_t p = __atomic_fetch_add(&cur[k], 1ull, __ATOMIC_RELAXED);
-                rc[2 * p] = (code_of(w) << kIndexBits) | (uint32_t)a;
-                rc[2 * p + 1] = (uint32_t)j;
-            });
+            comm_terms(
+                c, g.gen_labels, lo, hi, stamps[t],
+                [&](int32_t k, int32_t a, int32_t j, int w) {
+                    uint64_t p = __atomic_fetch_add(&cur[k], 1ull, __ATOMIC_RELAXED);
+                    rc[2 * p] = (code_of(w) << kIndexBits) | (uint32_t)a;
+                    rc[2 * p + 1] = (uint32_t)j;
+                },
+                [&](uint64_t lab, int32_t a, int32_t j, int w) {
+                    const int32_t q = oidx.find(lab);
+                    uint64_t p = __atomic_fetch_add(&ocur[q], 1ull, __ATOMIC_RELAXED);
+                    oc[2 * p] = (code_of(w) << kIndexBits) | (uint32_t)a;
+                    oc[2 * p + 1] = (uint32_t)j;
+                });
         });
     }
     sort_segments(T, g.rp[0], g.rec[0]);
     sort_segments(T, g.rp[1], g.rec[1]);
+    sort_segments(T, g.rp[2], g.rec[2]);
     auto t2 = clk::now();
     if (st) {
         st->n = n;
@@ -402,7 +459,7 @@ extern "C" cut_status cut_build(const cut_build_opts *opts, int64_t n, const uin
                                 const char *path, cut_build_stats *stats) {
     using namespace cut;
     if (!opts || !labels || !path || n <= 0) return set_error(CUT_ERR_INVALID_ARG, "cut_build: null argument or empty registry");
-    if (opts->algebra != CUT_ALG_PAULI && opts->algebra != CUT_ALG_FERMION)
+    if (opts->algebra != CUT_ALG_PAULI && opts->algebra != CUT_ALG_FERMION && opts->algebra != CUT_ALG_PAULI_BOSON)
         return set_error(CUT_ERR_INVALID_ARG, "cut_build: unknown algebra");
     if (opts->nmodes < 1 || opts->nmodes > 32) return set_error(CUT_ERR_INVALID_ARG, "cut_build: nmodes must be 1..32");
     auto t0 = std::chrono::steady_clock::now();

@@ -91,11 +91,12 @@ struct FileHeader {
     uint32_t n_codes, reserved;
     uint64_t payload_bytes;
     uint8_t sha256[32];
-    uint8_t pad[160 - 8 - 16 - 32 - 8 - 8 - 32];
+    uint64_t n_out, R2;   // outside-space labels and records (0 without diagnostics)
+    uint8_t pad[160 - 8 - 16 - 32 - 8 - 8 - 32 - 16];
 };
 static_assert(sizeof(FileHeader) == 160, "header size");
 static const char kMagic[8] = {'C', 'U', 'T', 'G', 'R', 'A', 'P', 'H'};
-static const uint32_t kVersion = 1;
+static const uint32_t kVersion = 2;
 
 static size_t pad64(size_t b) { return (b + 63) & ~size_t(63); }
 
@@ -106,7 +107,8 @@ static std::vector<Section> sections(HostGraph &g) {
             {g.diag.data(), g.diag.size()},               {g.num.data(), g.num.size() * 4},
             {g.den.data(), g.den.size() * 4},             {g.rp[0].data(), g.rp[0].size() * 8},
             {g.rec[0].data(), g.rec[0].size() * 4},       {g.rp[1].data(), g.rp[1].size() * 8},
-            {g.rec[1].data(), g.rec[1].size() * 4}};
+            {g.rec[1].data(), g.rec[1].size() * 4},       {g.out_labels.data(), g.out_labels.size() * 8},
+            {g.rp[2].data(), g.rp[2].size() * 8},         {g.rec[2].data(), g.rec[2].size() * 4}};
 }
 
 std::string write_bundle(HostGraph &g, const std::string &path, int64_t *bytes) {
@@ -122,6 +124,9 @@ std::string write_bundle(HostGraph &g, const std::string &path, int64_t *bytes) 
     hd.R0 = (uint64_t)g.R(0);
     hd.R1 = (uint64_t)g.R(1);
     hd.n_codes = (uint32_t)g.num.size();
+    if (g.rp[2].empty()) g.rp[2].assign(1, 0);
+    hd.n_out = (uint64_t)g.n_out();
+    hd.R2 = (uint64_t)(g.rec[2].size() / 2);
     auto secs = sections(g);
     static const uint8_t zeros[64] = {0};
     Sha256 sh;
@@ -161,7 +166,7 @@ int read_bundle(const std::string &path, HostGraph &g, std::string *err) {
     if (memcmp(hd.magic, kMagic, 8) != 0) { *err = "not a CUT graph bundle (bad magic)"; return 3; }
     if (hd.version != kVersion) { *err = "unsupported bundle version"; return 3; }
     if (hd.n == 0 || hd.n > kIndexMask || hd.n_g > kIndexMask || hd.n_codes == 0 ||
-        hd.n_codes > (uint32_t)kMaxCodes || hd.nmodes == 0 || hd.nmodes > 32 || hd.algebra > 1) {
+        hd.n_codes > (uint32_t)kMaxCodes || hd.nmodes == 0 || hd.nmodes > 32 || hd.algebra > 2) {
         *err = "bundle header out of range"; return 3;
     }
     g.algebra = (int)hd.algebra; g.nmodes = (int)hd.nmodes; g.max_rank = (int)hd.max_rank;
@@ -170,6 +175,7 @@ int read_bundle(const std::string &path, HostGraph &g, std::string *err) {
         g.num.resize(hd.n_codes); g.den.resize(hd.n_codes);
         g.rp[0].resize(hd.n_g + 1); g.rec[0].resize(2 * hd.R0);
         g.rp[1].resize(hd.n + 1); g.rec[1].resize(2 * hd.R1);
+        g.out_labels.resize(hd.n_out); g.rp[2].resize(hd.n_out + 1); g.rec[2].resize(2 * hd.R2);
     } catch (...) { *err = "out of host memory reading bundle"; return 5; }
     auto secs = sections(g);
     uint64_t expect = 0;
@@ -191,7 +197,8 @@ int read_bundle(const std::string &path, HostGraph &g, std::string *err) {
     if (memcmp(dg, hd.sha256, 32) != 0) { *err = "payload SHA-256 mismatch"; return 4; }
     memcpy(g.sha, dg, 32);
     // structural validation
-    for (int s = 0; s < 2; s++) {
+    if (hd.n_out > kIndexMask) { *err = "outside-space index beyond 2^24"; return 3; }
+    for (int s = 0; s < 3; s++) {
         const auto &rp = g.rp[s];
         uint64_t rows = rp.size() - 1;
         uint64_t lim1 = s == 0 ? hd.n : hd.n_g;

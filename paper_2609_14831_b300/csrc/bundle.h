@@ -27,18 +27,21 @@ struct Sha256 {
 
 // In-memory graph (host).  Stage 0 = generator (rows: generator coordinate
 // a; inputs i = diagonal coordinate, j = off-diagonal coordinate).  Stage 1 =
-// commutator (rows: output coordinate k; inputs a, j).
+// commutator (rows: output coordinate k; inputs a, j).  Stage 2 = optional
+// outside-space records (rows: labels outside the registry, inputs a, j).
 struct HostGraph {
     int algebra = 0, nmodes = 0, max_rank = 0;
     std::vector<uint64_t> labels;      // [n]
     std::vector<uint64_t> gen_labels;  // [n_g]
+    std::vector<uint64_t> out_labels;  // [n_out] outside-space labels (diagnostics)
     std::vector<uint8_t> diag;         // [n]
     std::vector<int32_t> num, den;     // factor table
-    std::vector<uint64_t> rp[2];       // row pointers
-    std::vector<uint32_t> rec[2];      // 2 words per record
+    std::vector<uint64_t> rp[3];       // row pointers
+    std::vector<uint32_t> rec[3];      // 2 words per record
     uint8_t sha[32] = {0};
     int64_t n() const { return (int64_t)labels.size(); }
     int64_t n_g() const { return (int64_t)gen_labels.size(); }
+    int64_t n_out() const { return (int64_t)out_labels.size(); }
     int64_t R(int s) const { return (int64_t)(rec[s].size() / 2); }
 };
 

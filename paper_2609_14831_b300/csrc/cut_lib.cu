@@ -44,7 +44,7 @@ struct DevCSR {
 struct cut_graph {
     int device = 0;
     cut::HostGraph host;
-    cut::DevCSR st[2];             // forward stages
+    cut::DevCSR st[3];             // forward stages (2: outside space, optional)
     cut::DevCSR tx, txi, th;       // transposed orders (adjoint), built lazily
     bool have_T = false;
     double *wtab = nullptr;        // exact factors as doubles
@@ -60,7 +60,7 @@ struct cut_graph {
         int cur = 0;
         cudaGetDevice(&cur);
         cudaSetDevice(device);
-        for (auto *c : {&st[0], &st[1], &tx, &txi, &th}) {
+        for (auto *c : {&st[0], &st[1], &st[2], &tx, &txi, &th}) {
             cudaFree(c->rp);
             cudaFree(c->rec);
         }
@@ -129,12 +129,13 @@ static int grid_for_groups(int64_t rows, int lanes) {
 }
 
 static void launch_comm(const cut_graph *g, const double *xi, int nops, const double *const *xs,
-                        double *const *dxs, cudaStream_t s, const int *done) {
-    const DevCSR &c = g->st[1];
+                        double *const *dxs, cudaStream_t s, const int *done, int stage = 1) {
+    const DevCSR &c = g->st[stage];
     const int grid = grid_for_groups(c.rows, kCommLanes);
     const k::Weights w = weights_of(g);
-    for (int o0 = 0; o0 < nops; o0 += 4) {
-        int m = std::min(4, nops - o0);
+    // up to eight operands share one pass over the records
+    for (int o0 = 0; o0 < nops; o0 += 8) {
+        int m = std::min(8, nops - o0);
         switch (m) {
 #define CASE(M)                                                                                          \
     case M: {                                                                                            \
@@ -145,7 +146,7 @@ static void launch_comm(const cut_graph *g, const double *xi, int nops, const do
         else                                                                                             \
             k::comm_stage<M, false, kCommLanes><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, xi, ops, c.rows, done); \
     } break;
-            CASE(1) CASE(2) CASE(3) CASE(4)
+            CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
 #undef CASE
         }
     }
@@ -240,12 +241,13 @@ cut_status cut_graph_load(const char *path, int device, unsigned flags, cut_grap
     if (device == -1) {  // host-only handle: query, labels, weights, records
         g->st[0].rows = g->host.n_g(); g->st[0].R = g->host.R(0);
         g->st[1].rows = g->host.n(); g->st[1].R = g->host.R(1);
+        g->st[2].rows = g->host.n_out(); g->st[2].R = g->host.R(2);
         *out = g.release();
         return set_ok();
     }
     DeviceGuard dg(device);
     int64_t bytes = 0;
-    for (int s = 0; s < 2; s++) {
+    for (int s = 0; s < 3; s++) {
         cut_status st = upload_csr(g->st[s], g->host.rp[s], g->host.rec[s], bytes);
         if (st != CUT_OK) return st;
     }
@@ -290,6 +292,37 @@ cut_status cut_graph_query(const cut_graph *g, cut_graph_desc *out) {
     memcpy(out->sha256, g->host.sha, 32);
     out->device_bytes = g->device_bytes;
     out->record_bytes = 8;
+    out->n_out = g->host.n_out();
+    out->R_C = g->st[2].R;
+    return set_ok();
+}
+
+cut_status cut_graph_outside_labels(const cut_graph *g, uint64_t *out) {
+    if (!g || !out) return set_error(CUT_ERR_INVALID_ARG, "cut_graph_outside_labels: null argument");
+    memcpy(out, g->host.out_labels.data(), g->host.out_labels.size() * 8);
+    return set_ok();
+}
+
+cut_status cut_rhs_outside(const cut_graph *g, const double *h, int n_obs, const double *x, double *c,
+                           cut_stream_t stream) {
+    if (!g || g->device < 0 || !h || !c || n_obs < 0 || n_obs > 63 || (n_obs > 0 && !x))
+        return set_error(CUT_ERR_INVALID_ARG, "cut_rhs_outside: bad argument");
+    if (g->host.n_out() == 0)
+        return set_error(CUT_ERR_INVALID_ARG, "cut_rhs_outside: the graph was built without diagnostics");
+    DeviceGuard dg(g->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = g->host.n(), nout = g->host.n_out();
+    double *xi = nullptr;
+    CUDA_TRY(cudaMallocAsync(&xi, std::max<int64_t>(1, g->host.n_g()) * 8, s));
+    launch_gen(g, h, xi, s, nullptr);
+    const double *xs[64];
+    double *cs[64];
+    xs[0] = h;
+    cs[0] = c;
+    for (int o = 0; o < n_obs; o++) { xs[o + 1] = x + o * n; cs[o + 1] = c + (o + 1) * nout; }
+    launch_comm(g, xi, n_obs + 1, xs, cs, s, nullptr, 2);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaFreeAsync(xi, s));
     return set_ok();
 }
 
@@ -310,7 +343,7 @@ cut_status cut_graph_weights(const cut_graph *g, int32_t *num, int32_t *den) {
 
 cut_status cut_graph_records(const cut_graph *g, int stage, int64_t *row_ptr, int32_t *in1, int32_t *in2,
                              uint8_t *code) {
-    if (!g || stage < 0 || stage > 1) return set_error(CUT_ERR_INVALID_ARG, "cut_graph_records: bad argument");
+    if (!g || stage < 0 || stage > 2) return set_error(CUT_ERR_INVALID_ARG, "cut_graph_records: bad argument");
     const auto &rp = g->host.rp[stage];
     const auto &rc = g->host.rec[stage];
     if (rc.size() / 2 != (size_t)g->st[stage].R)
@@ -378,6 +411,62 @@ cut_status cut_apply_L(const cut_graph *g, const double *xi, int n_ops, const do
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------- assembly
+extern "C" cut_status cut_assemble(int n_src, int64_t n, const double *X, int n_out, const double *C, double *out,
+                                   cut_stream_t stream) {
+    if (n_src < 1 || n_src > 3000 || n < 1 || n_out < 1 || !X || !C || !out)
+        return set_error(CUT_ERR_INVALID_ARG, "cut_assemble: bad argument (1 <= n_src <= 3000)");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t smem = (size_t)n_src * 32 * 8;
+    if (smem > 48 * 1024)
+        CUDA_TRY(cudaFuncSetAttribute(k::assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int64_t blocks = (n + 31) / 32;
+    k::assemble<<<(unsigned)blocks, 256, smem, s>>>(X, n_src, n, C, n_out, out);
+    CUDA_TRY(cudaGetLastError());
+    return set_ok();
+}
+
+// ----------------------------------------------------------------- tangent
+extern "C" cut_status cut_rhs_jvp(const cut_graph *g, const double *h, int n_obs, const double *x, const double *dh,
+                                  const double *dx, double *out_h, double *out_x, cut_stream_t stream) {
+    if (!g || g->device < 0 || !h || !dh || !out_h || n_obs < 0 || n_obs > 63 ||
+        (n_obs > 0 && (!x || !dx || !out_x)))
+        return set_error(CUT_ERR_INVALID_ARG, "cut_rhs_jvp: bad argument");
+    DeviceGuard dg(g->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = g->host.n(), ng = std::max<int64_t>(1, g->host.n_g());
+    double *buf = nullptr;
+    CUDA_TRY(cudaMallocAsync(&buf, 2 * ng * 8, s));
+    double *xi = buf, *dxi = buf + ng;
+    const k::Weights w = weights_of(g);
+    launch_gen(g, h, xi, s, nullptr);
+    const DevCSR &c0 = g->st[0], &c1 = g->st[1];
+    k::gen_jvp<<<grid_for_rows(c0.rows), k::kBlock, 0, s>>>(c0.rp, c0.rec, w, h, dh, dxi, c0.rows);
+    const int nops = n_obs + 1;
+    const double *xs[64], *dxs[64];
+    double *outs[64];
+    xs[0] = h;
+    dxs[0] = dh;
+    outs[0] = out_h;
+    for (int o = 0; o < n_obs; o++) { xs[o + 1] = x + o * n; dxs[o + 1] = dx + o * n; outs[o + 1] = out_x + o * n; }
+    for (int o0 = 0; o0 < nops; o0 += 4) {
+        const int m = std::min(4, nops - o0);
+        switch (m) {
+#define CASE(M)                                                                                     \
+    case M: {                                                                                       \
+        k::TanOps<M> t;                                                                             \
+        for (int u = 0; u < M; u++) { t.x[u] = xs[o0 + u]; t.dx[u] = dxs[o0 + u]; t.out[u] = outs[o0 + u]; } \
+        k::comm_jvp<M><<<grid_for_rows(c1.rows), k::kBlock, 0, s>>>(c1.rp, c1.rec, w, xi, dxi, t, c1.rows); \
+    } break;
+            CASE(1) CASE(2) CASE(3) CASE(4)
+#undef CASE
+        }
+    }
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaFreeAsync(buf, s));
+    return set_ok();
+}
 
 // ----------------------------------------------------------------- adjoint
 namespace cut {

@@ -134,21 +134,22 @@ __global__ void __launch_bounds__(kBlock) comm_stage(const uint64_t *__restrict_
             const uint64_t e = rp[r + 1];
 #define COEF(q) (UNIFORM ? signed_by(xi[(q).x & kIdx], sg[(q).x >> 24]) : ws[(q).x >> 24] * xi[(q).x & kIdx])
             uint64_t p = rp[r] + sl;
-            // four records per lane per step, every load issued before the
+            // several records per lane per step, every load issued before the
             // arithmetic: the gathers are L2 round trips, the FMAs are not
-            for (; p + 3 * LANES < e; p += 4 * LANES) {
-                uint2 q[4];
+            constexpr int U = NOPS <= 4 ? 4 : 2;
+            for (; p + (U - 1) * LANES < e; p += U * LANES) {
+                uint2 q[U];
 #pragma unroll
-                for (int u = 0; u < 4; u++) q[u] = __ldcs(rec + p + u * LANES);
-                double c[4], xv[4][NOPS];
+                for (int u = 0; u < U; u++) q[u] = __ldcs(rec + p + u * LANES);
+                double c[U], xv[U][NOPS];
 #pragma unroll
-                for (int u = 0; u < 4; u++) {
+                for (int u = 0; u < U; u++) {
                     c[u] = COEF(q[u]);
 #pragma unroll
                     for (int o = 0; o < NOPS; o++) xv[u][o] = ops.x[o][q[u].y];
                 }
 #pragma unroll
-                for (int u = 0; u < 4; u++)
+                for (int u = 0; u < U; u++)
 #pragma unroll
                     for (int o = 0; o < NOPS; o++) acc[o] += c[u] * xv[u][o];
             }
@@ -209,21 +210,23 @@ __global__ void __launch_bounds__(kBlock) comm_stage_df(const uint64_t *__restri
         if (r < rows) {
             const uint64_t e = rp[r + 1];
             uint64_t p = rp[r] + sl;
-            // four records per lane per step, all loads ahead of the arithmetic
-            for (; p + 3 * LANES < e; p += 4 * LANES) {
-                uint2 q[4];
+            // eight records per lane per step, all loads ahead of the
+            // arithmetic (measured best on the 3.4e8-record graph)
+            constexpr int U = 8;
+            for (; p + (U - 1) * LANES < e; p += U * LANES) {
+                uint2 q[U];
 #pragma unroll
-                for (int u = 0; u < 4; u++) q[u] = __ldcs(rec + p + u * LANES);
-                float2 cf[4];
-                float4 a[4], b[4];
+                for (int u = 0; u < U; u++) q[u] = __ldcs(rec + p + u * LANES);
+                float2 cf[U];
+                float4 a[U], b[U];
 #pragma unroll
-                for (int u = 0; u < 4; u++) {
+                for (int u = 0; u < U; u++) {
                     cf[u] = xi2[q[u].x & kIdx];
                     a[u] = X2[2 * (int64_t)q[u].y];
                     if (NOPS > 2) b[u] = X2[2 * (int64_t)q[u].y + 1];
                 }
 #pragma unroll
-                for (int u = 0; u < 4; u++) {
+                for (int u = 0; u < U; u++) {
                     const unsigned int sb = (unsigned int)(sg[q[u].x >> 24] >> 32);
                     const float ch = __uint_as_float(__float_as_uint(cf[u].x) ^ sb);
                     const float cl = __uint_as_float(__float_as_uint(cf[u].y) ^ sb);
@@ -264,6 +267,93 @@ __global__ void split_pairs(const double *__restrict__ in, int64_t len, float2 *
         const float hi = __double2float_rn(v);
         const float lo = __double2float_rn(v - (double)hi);
         out[i * stride + slot] = make_float2(hi, lo);
+    }
+}
+
+// ---------------------------------------------------------------- assembly
+// Multi-operator assembly (Sec. 2.4, last paragraph): output operator m is
+// the combination sum_i C[m][i] X_i(s) of transformed source operators.
+// One thread per (m, k) output coefficient sums the sources in index order
+// (a fixed FMA chain), so every run gives the same bits.  The sources for a
+// tile of 32 coefficients are staged in shared memory once per CTA.
+__global__ void __launch_bounds__(256) assemble(const double *__restrict__ X, int n_src, int64_t n,
+                                                const double *__restrict__ C, int n_out,
+                                                double *__restrict__ out) {
+    extern __shared__ double xs[];                     // [n_src][32]
+    const int64_t k0 = (int64_t)blockIdx.x * 32;
+    const int kc = threadIdx.x & 31;
+    for (int e = threadIdx.x; e < n_src * 32; e += blockDim.x) {
+        const int i = e / 32, c = e % 32;
+        xs[e] = (k0 + c < n) ? X[(int64_t)i * n + k0 + c] : 0.0;
+    }
+    __syncthreads();
+    if (k0 + kc >= n) return;
+    for (int m = threadIdx.x >> 5; m < n_out; m += blockDim.x >> 5) {
+        const double *cm = C + (int64_t)m * n_src;
+        double acc = 0.0;
+        for (int i = 0; i < n_src; i++) acc = fma(cm[i], xs[i * 32 + kc], acc);
+        out[(int64_t)m * n + k0 + kc] = acc;
+    }
+}
+
+// ---------------------------------------------------------------- tangent
+// Directional derivative (Sec. 2.4, Eq. directional-derivative): the product
+// rule applied record by record.
+//   d xi[a]   = sum alpha (dh[i] h[j] + h[i] dh[j])
+//   d F_o[k]  = sum beta (d xi[a] x_o[j] + xi[a] dx_o[j])
+__global__ void __launch_bounds__(kBlock) gen_jvp(const uint64_t *__restrict__ rp, const uint2 *__restrict__ rec,
+                                                  Weights wt, const double *__restrict__ h,
+                                                  const double *__restrict__ dh, double *__restrict__ dxi,
+                                                  int64_t rows) {
+    __shared__ double ws[256];
+    __shared__ unsigned long long sg[256];
+    load_weights(ws, sg, wt);
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * kWarpsPerBlock;
+    for (int64_t r = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); r < rows; r += nw) {
+        double acc = 0.0;
+        for (uint64_t p = rp[r] + lane; p < rp[r + 1]; p += 32) {
+            const uint2 q = __ldcs(rec + p);
+            const uint32_t i = q.x & kIdx, j = q.y;
+            acc += ws[q.x >> 24] * (dh[i] * h[j] + h[i] * dh[j]);
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) dxi[r] = acc;
+    }
+}
+
+template <int NOPS>
+struct TanOps {
+    const double *x[NOPS], *dx[NOPS];
+    double *out[NOPS];
+};
+
+template <int NOPS>
+__global__ void __launch_bounds__(kBlock) comm_jvp(const uint64_t *__restrict__ rp, const uint2 *__restrict__ rec,
+                                                   Weights wt, const double *__restrict__ xi,
+                                                   const double *__restrict__ dxi, TanOps<NOPS> t, int64_t rows) {
+    __shared__ double ws[256];
+    __shared__ unsigned long long sg[256];
+    load_weights(ws, sg, wt);
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * kWarpsPerBlock;
+    for (int64_t r = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); r < rows; r += nw) {
+        double acc[NOPS];
+#pragma unroll
+        for (int o = 0; o < NOPS; o++) acc[o] = 0.0;
+        for (uint64_t p = rp[r] + lane; p < rp[r + 1]; p += 32) {
+            const uint2 q = __ldcs(rec + p);
+            const double w = ws[q.x >> 24];
+            const uint32_t a = q.x & kIdx, j = q.y;
+            const double c = w * xi[a], dc = w * dxi[a];
+#pragma unroll
+            for (int o = 0; o < NOPS; o++) acc[o] += dc * t.x[o][j] + c * t.dx[o][j];
+        }
+#pragma unroll
+        for (int o = 0; o < NOPS; o++) {
+            const double v = warp_sum(acc[o]);
+            if (lane == 0) t.out[o][r] = v;
+        }
     }
 }
 

@@ -134,3 +134,36 @@ def test_stress_graph_full_size_properties(stress):
     finally:
         G.set_arithmetic("fp64")
     assert_close(np64(dh2), dh, rtol=1e-12, what="df64 vs fp64 at full size")
+
+
+def test_outside_space_diagnostics_match_oracle():
+    """C_q = coefficients of [eta, X] outside the registry (Eq. projected-flow),
+    and the retained flow is the same with or without the diagnostic records."""
+    from cut_inputs import fermion_registry
+    from gpu_util import _TMP
+    import os
+    import paper_2609_14831_b300 as cg
+    norb = 5
+    labels = fermion_registry(norb)
+    h = molecular_hamiltonian(labels, norb, seed=74, scale=0.3)
+    xs = [dipole_operator(labels, norb, seed=74)]
+    G = graph_for("mol5_plain", ALG_FERMION, norb, labels)
+    path = os.path.join(_TMP, "mol5_diag.cutg")
+    cg.build_graph(ALG_FERMION, norb, labels, path, diagnostics=True)
+    Gd = cg.Graph(path, device=0)
+    out_labels = Gd.outside_labels()
+    C = Gd.rhs_outside(h, xs)
+    for o, v in enumerate([h] + xs):
+        full = oracle.rhs_unprojected(ALG_FERMION, norb, labels, h, v)
+        want = np.array([complex(full.get(int(l), 0.0)).real for l in out_labels])
+        # every generated term outside the registry has a row
+        reg = {int(l) for l in labels}
+        extra = {k for k, c in full.items() if abs(c) > 1e-13 and k not in reg} - {int(l) for l in out_labels}
+        assert not extra
+        assert_close(np64(C[o]), want, what=f"C operand {o}", atol=rhs_floor(h, xs))
+    a = G.rhs(h, xs)
+    b = Gd.rhs(h, xs)
+    assert_close(np64(b[0]), np64(a[0]), rtol=1e-14, what="retained dh")
+    fa = G.flow(h, xs, method="rk4", s0=0.0, s1=0.2, ds=0.02)
+    fb = Gd.flow(h, xs, method="rk4", s0=0.0, s1=0.2, ds=0.02)
+    assert_close(np64(fb[0]), np64(fa[0]), rtol=1e-13, what="retained flow")

@@ -203,3 +203,57 @@ def test_traversals_refuse_host_only_handles(tmp_path):
     G = cg.Graph(p, device=-1)
     rc = cg.lib().cut_rhs(G._h, None, 0, None, None, None, None, None)
     assert rc == 1
+
+
+def _expected_outside(alg, nmodes, labels, gen_labels, out_labels):
+    reg = {int(l) for l in labels}
+    qidx = {int(l): q for q, l in enumerate(out_labels)}
+    out = {}
+    for a, ga in enumerate(gen_labels):
+        for j, lj in enumerate(labels):
+            for k, v in oracle.commutator(alg, nmodes, {int(ga): 1.0}, {int(lj): 1.0}).items():
+                if v == 0 or k in reg:
+                    continue
+                val = v * 1j if alg == ALG_PAULI else v
+                assert val.imag == 0 and val.real == round(val.real)
+                out[(qidx[k], a, j)] = int(val.real)
+    return out
+
+
+@pytest.mark.parametrize("case", ["fermion4", "pauli3_sub"])
+def test_outside_space_records_match_oracle_probes(tmp_path, case):
+    if case == "fermion4":
+        alg, nmodes, labels = ALG_FERMION, 4, fermion_registry(4)
+    else:
+        alg, nmodes, labels = ALG_PAULI, 3, pauli_registry(3)[::3]   # not closed under products
+    path = str(tmp_path / f"{case}_d.cutg")
+    cg.build_graph(alg, nmodes, labels, path, diagnostics=True)
+    G = cg.Graph(path, device=-1)
+    _, gen_labels, _ = G.labels()
+    out_labels = G.outside_labels()
+    assert G.n_out > 0 and G.R_C > 0
+    reg = {int(l) for l in labels}
+    assert not (set(int(l) for l in out_labels) & reg)
+    assert _graph_records(G, 2) == _expected_outside(alg, nmodes, labels, gen_labels, out_labels)
+    assert _graph_records(G, 1) == _expected_comm(alg, nmodes, labels, gen_labels)
+    # the generator now holds every term of [H_d, H_od] (eta exact)
+    want_gen, dropped = _expected_gen(alg, nmodes, labels, gen_labels)
+    assert not dropped
+    assert _graph_records(G, 0) == want_gen
+
+
+def test_diagnostics_leave_the_retained_records_unchanged(tmp_path):
+    labels = fermion_registry(5)
+    p0, p1 = str(tmp_path / "a.cutg"), str(tmp_path / "b.cutg")
+    cg.build_graph(ALG_FERMION, 5, labels, p0)
+    cg.build_graph(ALG_FERMION, 5, labels, p1, diagnostics=True)
+    G0, G1 = cg.Graph(p0, device=-1), cg.Graph(p1, device=-1)
+    _, g0, _ = G0.labels()
+    _, g1, _ = G1.labels()
+
+    def by_label(G, gl):
+        rp, a, b, c = G.records(1)
+        num, _ = G.weights()
+        rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+        return {(int(r), int(gl[x]), int(y)): int(num[z]) for r, x, y, z in zip(rows, a, b, c)}
+    assert by_label(G0, g0) == by_label(G1, g1)

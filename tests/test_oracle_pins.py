@@ -339,3 +339,16 @@ def test_mlp_oracle_gradients_match_central_differences():
     assert mlp.bf16(np.array([1.0 + 2.0 ** -8]))[0] == 1.0                 # tie -> even
     assert mlp.bf16(np.array([1.0 + 3 * 2.0 ** -8]))[0] == 1.0 + 2.0 ** -6  # tie -> even (up)
     assert mlp.bf16(np.array([1.0 + 2.0 ** -7]))[0] == 1.0 + 2.0 ** -7      # representable
+
+
+def test_oracle_jvp_pairs_with_vjp():
+    """<w, J v> from the exact five-point tangent equals <J^T w, v>."""
+    labels = fermion_registry(3)
+    n = len(labels)
+    rng = np.random.default_rng(17)
+    h, x = rng.normal(size=n), rng.normal(size=n)
+    dh, dx = rng.normal(size=n), rng.normal(size=n)
+    wh, wx = rng.normal(size=n), rng.normal(size=n)
+    jh, (jx,) = oracle.rhs_jvp(ALG_FERMION, 3, labels, h, [x], dh, [dx])
+    bh, (bx,) = oracle.rhs_vjp(ALG_FERMION, 3, labels, h, [x], wh, [wx])
+    np.testing.assert_allclose(wh @ jh + wx @ jx, bh @ dh + bx @ dx, rtol=1e-12)
