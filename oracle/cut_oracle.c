@@ -225,16 +225,20 @@ static const double RMAT[4][2][2] = {{{1, 0}, {0, 1}}, {{0, 1}, {1, 0}}, {{0, 1}
 
 static int pb_get(uint64_t l, int shift) { return (int)((l >> shift) & 31); }
 
-/* one mode: coefficients of (b+)^C b^A, returned in poly[C][A] */
+/* one mode: coefficients of (b+)^C b^A, returned in poly[C][A] for
+ * C <= c1 + c2, A <= a1 + a2 (the only entries that can be nonzero) */
 static void boson_mode_product(int c1, int a1, int c2, int a2, double poly[PB_MAXDEG][PB_MAXDEG]) {
     static double cur[PB_MAXDEG][PB_MAXDEG], nxt[PB_MAXDEG][PB_MAXDEG];
-    memset(cur, 0, sizeof(cur));
+    const int cm = c1 + c2 + 1, am = a1 + a2 + 1;
+    for (int c = 0; c < cm; c++)
+        for (int a = 0; a < am; a++) cur[c][a] = 0.0;
     cur[c1][a1] = 1.0;
     for (int step = 0; step < c2 + a2; step++) {
         const int create = step < c2;   /* B = (b+)^c2 b^a2: the b+ factors first */
-        memset(nxt, 0, sizeof(nxt));
-        for (int c = 0; c < PB_MAXDEG; c++)
-            for (int a = 0; a < PB_MAXDEG; a++) {
+        for (int c = 0; c < cm; c++)
+            for (int a = 0; a < am; a++) nxt[c][a] = 0.0;
+        for (int c = 0; c < cm; c++)
+            for (int a = 0; a < am; a++) {
                 double v = cur[c][a];
                 if (v == 0.0) continue;
                 if (!create) {
@@ -244,9 +248,11 @@ static void boson_mode_product(int c1, int a1, int c2, int a2, double poly[PB_MA
                     if (a > 0) nxt[c][a - 1] += a * v;
                 }
             }
-        memcpy(cur, nxt, sizeof(cur));
+        for (int c = 0; c < cm; c++)
+            for (int a = 0; a < am; a++) cur[c][a] = nxt[c][a];
     }
-    memcpy(poly, cur, sizeof(cur));
+    for (int c = 0; c < cm; c++)
+        for (int a = 0; a < am; a++) poly[c][a] = cur[c][a];
 }
 
 static void pb_product(int nmodes, uint64_t x, uint64_t y, cplx coef, oracle_op *out) {
@@ -265,10 +271,11 @@ static void pb_product(int nmodes, uint64_t x, uint64_t y, cplx coef, oracle_op 
     val[0][0] = 1.0;
     for (int m = 0; m < nmodes; m++) {
         const int sc = 2 + 10 * m, sa = 7 + 10 * m;
-        boson_mode_product(pb_get(x, sc), pb_get(x, sa), pb_get(y, sc), pb_get(y, sa), poly);
+        const int cx = pb_get(x, sc), ax = pb_get(x, sa), cy = pb_get(y, sc), ay = pb_get(y, sa);
+        boson_mode_product(cx, ax, cy, ay, poly);
         int nn = 0;
-        for (int c = 0; c < PB_MAXDEG; c++)
-            for (int a = 0; a < PB_MAXDEG; a++) {
+        for (int c = 0; c <= cx + cy; c++)
+            for (int a = 0; a <= ax + ay; a++) {
                 if (poly[c][a] == 0.0) continue;
                 if (c > 31 || a > 31) abort();   /* beyond the 5-bit label fields */
                 for (int i = 0; i < n; i++) {

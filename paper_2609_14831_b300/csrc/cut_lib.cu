@@ -120,31 +120,43 @@ static k::Weights weights_of(const cut_graph *g) {
     return w;
 }
 
-// lanes per CSR segment: commutator rows are long (hundreds to thousands of
-// records), generator rows short (tens)
-constexpr int kCommLanes = 8, kGenLanes = 4;
+// lanes per CSR segment.  With many outputs, 8 lanes per commutator row
+// (4 per generator row) keep lanes busy and the closing reductions short;
+// with few outputs (a few thousand) a whole warp per row is needed to fill
+// the GPU's ~7000 resident warps.
+constexpr int kManyRows = 16384;
+static int comm_lanes(int64_t rows) { return rows >= kManyRows ? 8 : 32; }
+static int gen_lanes(int64_t rows) { return rows >= kManyRows ? 4 : 8; }
 
 static int grid_for_groups(int64_t rows, int lanes) {
     return grid_for_rows((rows + (32 / lanes) - 1) / (32 / lanes));
 }
 
+template <int M, int L>
+static void comm_launch(const DevCSR &c, const k::Weights &w, const double *xi, const k::Ops<M> &ops,
+                        cudaStream_t s, const int *done) {
+    const int grid = grid_for_groups(c.rows, L);
+    if (w.uniform)
+        k::comm_stage<M, true, L><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, xi, ops, c.rows, done);
+    else
+        k::comm_stage<M, false, L><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, xi, ops, c.rows, done);
+}
+
 static void launch_comm(const cut_graph *g, const double *xi, int nops, const double *const *xs,
                         double *const *dxs, cudaStream_t s, const int *done, int stage = 1) {
     const DevCSR &c = g->st[stage];
-    const int grid = grid_for_groups(c.rows, kCommLanes);
     const k::Weights w = weights_of(g);
+    const int lanes = comm_lanes(c.rows);
     // up to eight operands share one pass over the records
     for (int o0 = 0; o0 < nops; o0 += 8) {
         int m = std::min(8, nops - o0);
         switch (m) {
-#define CASE(M)                                                                                          \
-    case M: {                                                                                            \
-        k::Ops<M> ops;                                                                                   \
-        for (int t = 0; t < M; t++) { ops.x[t] = xs[o0 + t]; ops.dx[t] = dxs[o0 + t]; }                    \
-        if (w.uniform)                                                                                   \
-            k::comm_stage<M, true, kCommLanes><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, xi, ops, c.rows, done); \
-        else                                                                                             \
-            k::comm_stage<M, false, kCommLanes><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, xi, ops, c.rows, done); \
+#define CASE(M)                                                                        \
+    case M: {                                                                          \
+        k::Ops<M> ops;                                                                 \
+        for (int t = 0; t < M; t++) { ops.x[t] = xs[o0 + t]; ops.dx[t] = dxs[o0 + t]; }  \
+        if (lanes == 8) comm_launch<M, 8>(c, w, xi, ops, s, done);                     \
+        else comm_launch<M, 32>(c, w, xi, ops, s, done);                               \
     } break;
             CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
 #undef CASE
@@ -152,14 +164,21 @@ static void launch_comm(const cut_graph *g, const double *xi, int nops, const do
     }
 }
 
+template <int L>
+static void gen_launch(const DevCSR &c, const k::Weights &w, const double *h, double *xi, cudaStream_t s,
+                       const int *done) {
+    const int grid = grid_for_groups(c.rows, L);
+    if (w.uniform)
+        k::gen_stage<true, L><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, h, xi, c.rows, done);
+    else
+        k::gen_stage<false, L><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, h, xi, c.rows, done);
+}
+
 static void launch_gen(const cut_graph *g, const double *h, double *xi, cudaStream_t s, const int *done) {
     const DevCSR &c = g->st[0];
     const k::Weights w = weights_of(g);
-    const int grid = grid_for_groups(c.rows, kGenLanes);
-    if (w.uniform)
-        k::gen_stage<true, kGenLanes><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, h, xi, c.rows, done);
-    else
-        k::gen_stage<false, kGenLanes><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, h, xi, c.rows, done);
+    if (gen_lanes(c.rows) == 4) gen_launch<4>(c, w, h, xi, s, done);
+    else gen_launch<8>(c, w, h, xi, s, done);
 }
 
 // Double-float commutator stage: split xi and up to three operands at a time
@@ -169,18 +188,22 @@ static void launch_comm_df(const cut_graph *g, const double *xi, float2 *xi2, fl
     const DevCSR &c = g->st[1];
     const int64_t n = g->host.n(), ng = g->host.n_g();
     const k::Weights w = weights_of(g);
-    const int grid = grid_for_groups(c.rows, kCommLanes);
+    const int lanes = comm_lanes(c.rows);
+    const int grid = grid_for_groups(c.rows, lanes);
     if (ng > 0) k::split_pairs<<<grid_for_len(ng), 256, 0, s>>>(xi, ng, xi2, 1, 0, done);
     for (int o0 = 0; o0 < nops; o0 += 3) {
         const int m = std::min(3, nops - o0);
         for (int t = 0; t < m; t++) k::split_pairs<<<grid_for_len(n), 256, 0, s>>>(xs[o0 + t], n, X2, 4, t, done);
         const float4 *X4 = reinterpret_cast<const float4 *>(X2);
         switch (m) {
-#define CASE(M)                                                                                           \
-    case M: {                                                                                             \
-        k::Ops<M> ops;                                                                                    \
-        for (int t = 0; t < M; t++) { ops.x[t] = xs[o0 + t]; ops.dx[t] = dxs[o0 + t]; }                     \
-        k::comm_stage_df<M, kCommLanes><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, xi2, X4, ops, c.rows, done); \
+#define CASE(M)                                                                                                   \
+    case M: {                                                                                                     \
+        k::Ops<M> ops;                                                                                            \
+        for (int t = 0; t < M; t++) { ops.x[t] = xs[o0 + t]; ops.dx[t] = dxs[o0 + t]; }                             \
+        if (lanes == 8)                                                                                           \
+            k::comm_stage_df<M, 8><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, xi2, X4, ops, c.rows, done);        \
+        else                                                                                                      \
+            k::comm_stage_df<M, 32><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, xi2, X4, ops, c.rows, done);       \
     } break;
             CASE(1) CASE(2) CASE(3)
 #undef CASE

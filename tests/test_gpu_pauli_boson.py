@@ -20,7 +20,7 @@ def test_two_mode_rhs_and_flow_match_oracle():
     M, p = 2, 4
     labels = pauli_boson_registry(M, p)
     h = pauli_boson_hamiltonian(labels, M, seed=91)
-    xs = [pauli_boson_hamiltonian(labels, M, seed=92 + i) for i in range(7)]
+    xs = [pauli_boson_hamiltonian(labels, M, seed=92 + i) for i in range(7)]   # 8 operands, one record pass
     G = graph_for("pb2m4", ALG_PAULI_BOSON, M, labels)
     dh, dxs = G.rhs(h, xs)
     want_dh, want_dxs = oracle.rhs(ALG_PAULI_BOSON, M, labels, h, xs)
