@@ -388,10 +388,19 @@ def main():
             import torch.distributed as dist
             dist.barrier()
 
-    tmpdir = tempfile.mkdtemp(prefix="cutbench_")
-    w, path, bstats, tbuild = _build(args.workload, 2 + rank, tmpdir, rank)
-    G = cg.Graph(path, device=local)
-    os.remove(path)
+    # one compile per node: rank 0 writes the bundle, every rank loads it
+    # (the registry is the same; each rank flows its own seeded coefficients)
+    from cut_inputs import workload
+    shared = os.path.join(tempfile.gettempdir(), f"cutbench_{os.environ.get('MASTER_PORT', 'solo')}_{args.workload}.cutg")
+    if rank == 0:
+        w0, path, bstats, tbuild = _build(args.workload, 2, os.path.dirname(shared), 0)
+        os.replace(path, shared)
+    barrier()
+    w = workload(args.workload, seed=2 + rank)
+    G = cg.Graph(shared, device=local)
+    barrier()
+    if rank == 0:
+        os.remove(shared)
     R = G.R_g + G.R_L
     n = G.n
     nops = 1 + len(w.observables)
@@ -471,7 +480,7 @@ def main():
 
     # ---- the same flow and kernel in double-float arithmetic (FP32 pairs)
     df = None
-    if not args.no_df64:
+    if not args.no_df64 and rank == 0:
         G.set_arithmetic("df64")
         with torch.cuda.stream(stream):
             steps_on_device(1)
@@ -518,8 +527,9 @@ def main():
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e_val = world * 4 * R / e2e_s
 
-    batched = None if args.no_batched else batched_vs_plain(cg, torch, dev, local)
-    paper = None if args.no_paper else paper_workload(cg, torch, dev, local, args.paper_diagnostics)
+    batched = None if (args.no_batched or rank != 0) else batched_vs_plain(cg, torch, dev, local)
+    paper = None if (args.no_paper or rank != 0) else paper_workload(cg, torch, dev, local, args.paper_diagnostics)
+    barrier()
 
     cpu = None
     if rank == 0 and not args.no_cpu:

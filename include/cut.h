@@ -288,7 +288,9 @@ cut_status cut_flow_vjp(const cut_graph *g, const double *h0, int n_obs, const d
  * device in/out: h[batch][n], x[batch][n_obs][n] (instance-major, as a user
  * holds them; the library transposes internally).
  * precision: CUT_FP64 or CUT_FP32REC_FP64STATE (records, products and sums
- * in FP32; RK state and step control in FP64).
+ * in FP32, including the stage sums sum_j a_ij K_j of the FP32 slopes and
+ * the error estimate; the RK state and its updates Y + ds * (stage sum), the
+ * flow coordinate and the step size stay FP64).
  * Each instance has its own adaptive step sequence (DP45) and stops at s1.
  * device out: steps_out[batch] accepted steps, status_out[batch] cut_status.
  * host in: opts (replay/record fields ignored).  `tile` chooses the instance

@@ -30,7 +30,7 @@ namespace cut {
 namespace kb {
 
 constexpr uint32_t kIdx = (1u << 24) - 1;
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;   // 16 warps share one CTA's shared-memory tile
 constexpr int kWarps = kThreads / 32;
 
 struct Tableau {
@@ -76,7 +76,17 @@ __device__ void rhs_tile(const Args &a, const T *__restrict__ U, T *__restrict__
     // generator stage: xi[a][b] = sum alpha U0[i][b] U0[j][b]
     for (int64_t r = warp; r < a.n_g; r += kWarps) {
         T acc = T(0);
-        for (uint64_t p = a.rp0[r] + g; p < a.rp0[r + 1]; p += G) {
+        const uint64_t e = a.rp0[r + 1];
+        uint64_t p = a.rp0[r] + g;
+        for (; p + 3 * G < e; p += 4 * G) {   // four records in flight per group
+            uint2 q[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) q[u] = __ldg(a.rec0 + p + u * G);
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                acc += ws[q[u].x >> 24] * U[(q[u].x & kIdx) * TILE + b] * U[(int64_t)q[u].y * TILE + b];
+        }
+        for (; p < e; p += G) {
             uint2 q = __ldg(a.rec0 + p);
             acc += ws[q.x >> 24] * U[(q.x & kIdx) * TILE + b] * U[(int64_t)q.y * TILE + b];
         }
@@ -89,7 +99,26 @@ __device__ void rhs_tile(const Args &a, const T *__restrict__ U, T *__restrict__
         T acc[NOPS];
 #pragma unroll
         for (int o = 0; o < NOPS; o++) acc[o] = T(0);
-        for (uint64_t p = a.rp1[r] + g; p < a.rp1[r + 1]; p += G) {
+        const uint64_t e = a.rp1[r + 1];
+        uint64_t p = a.rp1[r] + g;
+        for (; p + 3 * G < e; p += 4 * G) {   // four records in flight per group
+            uint2 q[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) q[u] = __ldg(a.rec1 + p + u * G);
+            T c[4], xv[4][NOPS];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                c[u] = ws[q[u].x >> 24] * xis[(q[u].x & kIdx) * TILE + b];
+                const int64_t j = (int64_t)q[u].y * TILE + b;
+#pragma unroll
+                for (int o = 0; o < NOPS; o++) xv[u][o] = U[o * n * TILE + j];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+#pragma unroll
+                for (int o = 0; o < NOPS; o++) acc[o] += c[u] * xv[u][o];
+        }
+        for (; p < e; p += G) {
             uint2 q = __ldg(a.rec1 + p);
             const T c = ws[q.x >> 24] * xis[(q.x & kIdx) * TILE + b];
             const int64_t j = (int64_t)q.y * TILE + b;
@@ -174,12 +203,23 @@ __global__ void __launch_bounds__(kThreads, 1) flow_batched_kernel(Args a) {
         for (int st = 0; st < S; st++) {
             const bool fsal_first = tb.adaptive && st == 0;
             if (fsal_first && !any_new) continue;       // K1 = f(Y) carried over (FSAL)
-            // U = Y + ds sum_j a[st][j] K_j   (FP64, rounded to T into shared memory)
+            // U = Y + ds sum_j a[st][j] K_j, rounded to T into shared memory.
+            // FP32 slopes: the stage sum is formed in FP32 (the slopes carry
+            // FP32 precision anyway) and added to the FP64 state with one FP64
+            // FMA; FP64 slopes: all in FP64.
             for (int64_t e = threadIdx.x; e < L * TILE; e += kThreads) {
-                double u = Y[e];
                 const double ds = ds_[mb];
-                for (int j = 0; j < st; j++)
-                    if (tb.a[st][j] != 0.0) u += (tb.a[st][j] * ds) * (double)Kst(j)[e];
+                double u;
+                if (sizeof(T) == 4) {
+                    float inc = 0.0f;
+                    for (int j = 0; j < st; j++)
+                        if (tb.a[st][j] != 0.0) inc = fmaf((float)tb.a[st][j], (float)Kst(j)[e], inc);
+                    u = fma(ds, (double)inc, Y[e]);
+                } else {
+                    u = Y[e];
+                    for (int j = 0; j < st; j++)
+                        if (tb.a[st][j] != 0.0) u += (tb.a[st][j] * ds) * (double)Kst(j)[e];
+                }
                 if (tb.adaptive && st == S - 1) Y5[e] = u;
                 U[e] = T(u);
             }
@@ -199,17 +239,34 @@ __global__ void __launch_bounds__(kThreads, 1) flow_batched_kernel(Args a) {
             for (int64_t e = threadIdx.x; e < L * TILE; e += kThreads) {
                 const double ds = ds_[mb];
                 if (tb.adaptive) {
-                    double err = 0.0;
-                    for (int j = 0; j < S; j++)
-                        if (tb.e[j] != 0.0) err += (ds * tb.e[j]) * (double)Kst(j)[e];
-                    const double sc = a.atol + a.rtol * fmax(fabs(Y[e]), fabs(Y5[e]));
-                    const double r = fabs(err) / sc;
+                    double r;
+                    if (sizeof(T) == 4) {   // error ratio in FP32 from FP32 slopes
+                        float err = 0.0f;
+                        for (int j = 0; j < S; j++)
+                            if (tb.e[j] != 0.0) err = fmaf((float)tb.e[j], (float)Kst(j)[e], err);
+                        const float sc = (float)a.atol + (float)a.rtol * fmaxf(fabsf((float)Y[e]), fabsf((float)Y5[e]));
+                        r = (double)(fabsf((float)ds * err) / sc);
+                    } else {
+                        double err = 0.0;
+                        for (int j = 0; j < S; j++)
+                            if (tb.e[j] != 0.0) err += (ds * tb.e[j]) * (double)Kst(j)[e];
+                        const double sc = a.atol + a.rtol * fmax(fabs(Y[e]), fabs(Y5[e]));
+                        r = fabs(err) / sc;
+                    }
                     if (!(r == r) || !isfinite(Y5[e])) bad = true;
                     else m = fmax(m, r);
                 } else {
-                    double y = Y[e];
-                    for (int j = 0; j < S; j++)
-                        if (tb.b[j] != 0.0) y += (tb.b[j] * ds) * (double)Kst(j)[e];
+                    double y;
+                    if (sizeof(T) == 4) {
+                        float inc = 0.0f;
+                        for (int j = 0; j < S; j++)
+                            if (tb.b[j] != 0.0) inc = fmaf((float)tb.b[j], (float)Kst(j)[e], inc);
+                        y = fma(ds, (double)inc, Y[e]);
+                    } else {
+                        y = Y[e];
+                        for (int j = 0; j < S; j++)
+                            if (tb.b[j] != 0.0) y += (tb.b[j] * ds) * (double)Kst(j)[e];
+                    }
                     Y5[e] = y;
                     if (!isfinite(y)) bad = true;
                 }
