@@ -216,6 +216,55 @@ def batched_vs_plain(cg, torch, dev, local, batch=1024, plain_sample=8):
     return out
 
 
+def gradient_vs_fd(cg, torch, dev, local):
+    """Adjoint gradient of the flowed coefficient of n_0 with respect to 32
+    Hamiltonian parameters (8-orbital model, DP45 rtol 1e-10 to s = 10,
+    checkpoints every 64 steps) against the 64 central-difference flows it
+    replaces (same accepted steps)."""
+    from cut_inputs import make_label, parameter_directions, workload
+    from paper_2609_14831_b300 import autograd as ag
+    w = workload("molecular_8so")
+    path = os.path.join(tempfile.mkdtemp(prefix="cutgrad_"), "m8.cutg")
+    cg.build_graph(w.alg, w.nmodes, w.labels, path)
+    G = cg.Graph(path, device=local)
+    os.remove(path)
+    P = torch.tensor(parameter_directions(w.labels, 8), device=dev)
+    href = torch.tensor(w.h, device=dev)
+    x0 = torch.tensor(np.stack(w.observables), device=dev)
+    k0 = int(np.nonzero(w.labels == np.uint64(make_label(1, 1)))[0][0])
+    opts = dict(method="dp45", s0=0.0, s1=10.0, ds=1e-2, rtol=1e-10, atol=w.atol)
+
+    def grad():
+        theta = torch.zeros(32, dtype=torch.float64, device=dev, requires_grad=True)
+        hs, _ = ag.flow(G, href + P @ theta, x0, checkpoint_every=64, **opts)
+        hs[k0].backward()
+        return theta.grad
+    grad()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = grad()
+    torch.cuda.synchronize()
+    t_adj = time.perf_counter() - t0
+    _, _, st, acc = G.flow(w.h, list(w.observables), **opts)
+    Pn = P.cpu().numpy()
+    t0 = time.perf_counter()
+    fd = np.zeros(32)
+    for c in range(32):
+        v = []
+        for sgn in (1, -1):
+            hp, _, _, _ = G.flow(w.h + sgn * 1e-6 * Pn[:, c], list(w.observables), method="dp45", s0=0.0, s1=10.0,
+                                 replay=acc)
+            v.append(float(hp[k0]))
+        fd[c] = (v[0] - v[1]) / 2e-6
+    torch.cuda.synchronize()
+    t_fd = time.perf_counter() - t0
+    gn = g.cpu().numpy()
+    G.close()
+    return {"workload": "8-orbital model, d(flowed n_0)/d(32 parameters), DP45 to s = 10",
+            "accepted_steps": int(st["steps"]), "adjoint_s": t_adj, "fd_64_flows_s": t_fd,
+            "speedup": t_fd / t_adj, "max_rel_diff_vs_fd": float(np.max(np.abs(gn - fd)) / np.max(np.abs(fd)))}
+
+
 def paper_workload(cg, torch, dev, local, diagnostics=False):
     """The paper's own stress workload (Sec. 3.2-3.3): the complete five-mode
     degree-four Pauli-boson registry (4,004 coordinates; 7,017,036 production
@@ -365,6 +414,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-flow measurement")
     ap.add_argument("--surrogate", action="store_true", help="run the surrogate workload instead")
     ap.add_argument("--no-paper", action="store_true", help="skip the paper's Pauli-boson workload")
+    ap.add_argument("--no-gradient", action="store_true", help="skip the adjoint-gradient measurement")
     ap.add_argument("--paper-diagnostics", action="store_true",
                     help="also time the 352M-record diagnostic action (builds a 2.8 GB graph)")
     ap.add_argument("--surrogate-train", type=int, default=50000)
@@ -461,13 +511,14 @@ def main():
     fp64_flop = 2 * nops * G.R_L                # one FMA per record and operand
     hbm_peak, peak_kind = _peak_hbm()
     fp64_peak = FP64_NOMINAL_TFLOPS
-    traffic = None
+    traffic_table = {}
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tpath):
         try:
-            traffic = json.load(open(tpath)).get(f"{args.workload}:comm_stage_fp64")
-        except Exception:
-            traffic = None
+            traffic_table = json.load(open(tpath))
+        except ValueError:
+            traffic_table = {}
+    traffic = traffic_table.get(f"{args.workload}:comm_stage_fp64")
     roofline = {"bound": "alu", "achieved": fp64_flop / (comm_ms * 1e-3) / 1e12, "peak": fp64_peak,
                 "unit": "TFLOP/s", "frac": fp64_flop / (comm_ms * 1e-3) / 1e12 / fp64_peak, "traffic": traffic,
                 "peak_kind": "nominal B300 FP64 rate (profiling recipe table); the FP64 pipe is the "
@@ -502,7 +553,7 @@ def main():
               "roofline": {"bound": "hbm", "achieved": comm_bytes / (df_comm * 1e-3) / 1e9, "peak": hbm_peak,
                            "unit": "GB/s", "frac": comm_bytes / (df_comm * 1e-3) / 1e9 / hbm_peak,
                            "peak_kind": peak_kind, "kernel": f"comm_stage_df<{nops}>", "launch_ms": df_comm,
-                           "traffic": None}}
+                           "traffic": traffic_table.get(f"{args.workload}:comm_stage_df")}}
 
     # ---- end to end through the public API with host buffers
     pin_h = torch.tensor(w.h, dtype=torch.float64).pin_memory()
@@ -529,6 +580,7 @@ def main():
 
     batched = None if (args.no_batched or rank != 0) else batched_vs_plain(cg, torch, dev, local)
     paper = None if (args.no_paper or rank != 0) else paper_workload(cg, torch, dev, local, args.paper_diagnostics)
+    gradient = None if (args.no_gradient or rank != 0) else gradient_vs_fd(cg, torch, dev, local)
     barrier()
 
     cpu = None
@@ -552,6 +604,7 @@ def main():
             "df64": df,
             "batched": batched,
             "paper_workload": paper,
+            "gradient": gradient,
             "clocks": ck,
             "e2e": {"value": e2e_val, "unit": "records/s",
                     "h2d_bytes_per_step": int(8 * n * nops), "d2h_bytes_per_step": int(8 * n * nops)},
