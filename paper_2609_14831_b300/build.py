@@ -24,16 +24,32 @@ def _stale():
 
 
 def build(force=False, verbose=False):
+    """Compile every source to an object in parallel, then link libcut.so."""
     if not force and not _stale():
         return LIB
     nvcc = os.environ.get("NVCC", "nvcc")
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, "-O3", "-std=c++17", "-shared", "-Xcompiler", "-fPIC,-O3", *ARCH, "-lineinfo",
-           "-I", os.path.join(ROOT, "include"), "-I", CSRC, "-o", tmp, *sources(), "-lpthread"]
+    obj_dir = os.path.join(HERE, "_build")
+    os.makedirs(obj_dir, exist_ok=True)
+    flags = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC,-O3", *ARCH, "-lineinfo",
+             "-I", os.path.join(ROOT, "include"), "-I", CSRC]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-        print(" ".join(cmd), file=sys.stderr)
-    subprocess.check_call(cmd)
+        flags.insert(0, "-Xptxas=-v")
+    jobs = []
+    for src in sources():
+        obj = os.path.join(obj_dir, os.path.basename(src) + f".{os.getpid()}.o")
+        jobs.append((obj, [nvcc, *flags, "-c", src, "-o", obj]))
+    procs = []
+    for obj, cmd in jobs:
+        if verbose:
+            print(" ".join(cmd), file=sys.stderr)
+        procs.append(subprocess.Popen(cmd))
+    failed = [cmd for (obj, cmd), p in zip(jobs, procs) if p.wait() != 0]
+    if failed:
+        raise subprocess.CalledProcessError(1, failed[0])
+    tmp = LIB + f".tmp{os.getpid()}"
+    subprocess.check_call([nvcc, "-shared", *ARCH, "-o", tmp, *[o for o, _ in jobs], "-lpthread"])
+    for o, _ in jobs:
+        os.remove(o)
     os.replace(tmp, LIB)
     return LIB
 

@@ -59,78 +59,124 @@ struct Args {
     Tableau tb;
 };
 
-template <typename T>
-__device__ __forceinline__ T group_sum(T v, int tile) {
-    for (int o = 16; o >= tile; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+// first row index in [0, rows] whose offset is >= target (rps[rows] >= target)
+__device__ __forceinline__ int64_t lower_row(const uint32_t *rps, int64_t rows, uint32_t target) {
+    int64_t lo = 0, hi = rows;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (rps[mid] < target) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Row sums of one CSR stage (Eq. graph-actions) for the TILE slots of a CTA.
+// The 32/TILE lane groups of all warps (NG groups) each own a contiguous
+// range of rows holding about 1/NG of the records, rounded to whole rows, so
+// a group's records form one contiguous stream.  The TILE lanes of a group
+// (one instance each) load TILE consecutive records per instruction, M
+// instructions per chunk, the next chunk in flight while the current one is
+// applied; records reach the group's lanes by width-TILE shuffles.  Every
+// lane sums whole rows itself in record order: no cross-lane reduction.
+//   GEN:  out[r][b] = sum alpha U0[i][b] U0[j][b]            (xi, shared memory)
+//   else: out[o][r][b] = sum beta xi[a][b] U_o[j][b]         (slopes, global)
+template <typename T, int TILE, int NOPS, bool GEN>
+__device__ __forceinline__ void stage_stream(const uint32_t *__restrict__ rps, int64_t rows,
+                                             const uint2 *__restrict__ rec, const T *__restrict__ U,
+                                             const T *__restrict__ xis, const T *__restrict__ ws, int64_t n,
+                                             T *__restrict__ out) {
+    constexpr int G = 32 / TILE, NG = kWarps * G;
+    constexpr int M = TILE >= 8 ? 4 : 8;          // records per lane per chunk
+    constexpr int CH = M * TILE;                  // records per group per chunk
+    constexpr int SB = TILE < 8 ? TILE : 8;       // records gathered before they are summed
+    constexpr int NA = GEN ? 1 : NOPS;
+    const int lane = threadIdx.x & 31, b = lane % TILE, g = lane / TILE;
+    const int gi = (threadIdx.x >> 5) * G + g;
+    const unsigned gmask = TILE == 32 ? 0xffffffffu : (((1u << TILE) - 1u) << (g * TILE));
+    const uint32_t R = rps[rows];
+    const int64_t ra = lower_row(rps, rows, (uint32_t)((uint64_t)R * gi / NG));
+    const int64_t rb = gi + 1 == NG ? rows : lower_row(rps, rows, (uint32_t)((uint64_t)R * (gi + 1) / NG));
+    const uint32_t pe = rps[rb];
+    uint32_t c = rps[ra];
+    int64_t cur = ra;
+    uint32_t nb = ra < rb ? rps[ra + 1] : pe;     // end of the current row
+    T acc[NA];
+#pragma unroll
+    for (int o = 0; o < NA; o++) acc[o] = T(0);
+    auto flush = [&]() {
+#pragma unroll
+        for (int o = 0; o < NA; o++) {
+            out[((int64_t)o * (GEN ? 0 : n) + cur) * TILE + b] = acc[o];
+            acc[o] = T(0);
+        }
+        cur++;
+    };
+    uint2 v[M];
+#pragma unroll
+    for (int m = 0; m < M; m++) {
+        const uint32_t idx = c + m * TILE + b;
+        v[m] = idx < pe ? __ldg(rec + idx) : make_uint2(0u, 0u);
+    }
+    for (; c < pe; c += CH) {
+        uint2 nv[M];
+#pragma unroll
+        for (int m = 0; m < M; m++) {
+            const uint32_t idx = c + CH + m * TILE + b;
+            nv[m] = idx < pe ? __ldg(rec + idx) : make_uint2(0u, 0u);
+        }
+        // one TILE-record slice at a time from v[0]; the slices rotate down
+#pragma unroll 1
+        for (int m = 0; m < M; m++) {
+#pragma unroll
+            for (int s0 = 0; s0 < TILE; s0 += SB) {
+                // gather SB records (padding records read index 0: in bounds, never summed)
+                T cf[SB], uv[SB][NA];
+#pragma unroll
+                for (int s = 0; s < SB; s++) {
+                    uint2 q;
+                    q.x = __shfl_sync(gmask, v[0].x, s0 + s, TILE);
+                    q.y = __shfl_sync(gmask, v[0].y, s0 + s, TILE);
+                    const int64_t i = (int64_t)(q.x & kIdx) * TILE + b, j = (int64_t)q.y * TILE + b;
+                    if (GEN) {
+                        cf[s] = ws[q.x >> 24] * U[i];
+                        uv[s][0] = U[j];
+                    } else {
+                        cf[s] = ws[q.x >> 24] * xis[i];
+#pragma unroll
+                        for (int o = 0; o < NA; o++) uv[s][o] = U[(int64_t)o * n * TILE + j];
+                    }
+                }
+                // sum them in record order, closing rows at their ends
+#pragma unroll
+                for (int s = 0; s < SB; s++) {
+                    const uint32_t t = c + m * TILE + s0 + s;
+                    if (t < pe) {
+                        while (t >= nb) {
+                            flush();
+                            nb = rps[cur + 1];
+                        }
+#pragma unroll
+                        for (int o = 0; o < NA; o++) acc[o] += cf[s] * uv[s][o];
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k + 1 < M; k++) v[k] = v[k + 1];
+        }
+#pragma unroll
+        for (int m = 0; m < M; m++) v[m] = nv[m];
+    }
+    while (cur < rb) flush();   // the last row and any empty rows after it
 }
 
 // RHS of all TILE slots: U (smem, [nops][n][TILE]) -> K (global, [nops][n][TILE])
 template <typename T, int TILE, int NOPS>
-__device__ void rhs_tile(const Args &a, const T *__restrict__ U, T *__restrict__ xis, const T *__restrict__ ws,
+__device__ void rhs_tile(const Args &a, const uint32_t *__restrict__ rps0, const uint32_t *__restrict__ rps1,
+                         const T *__restrict__ U, T *__restrict__ xis, const T *__restrict__ ws,
                          T *__restrict__ K) {
-    constexpr int G = 32 / TILE;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane / TILE, b = lane % TILE;
-    const int64_t n = a.n;
-    // generator stage: xi[a][b] = sum alpha U0[i][b] U0[j][b]
-    for (int64_t r = warp; r < a.n_g; r += kWarps) {
-        T acc = T(0);
-        const uint64_t e = a.rp0[r + 1];
-        uint64_t p = a.rp0[r] + g;
-        for (; p + 3 * G < e; p += 4 * G) {   // four records in flight per group
-            uint2 q[4];
-#pragma unroll
-            for (int u = 0; u < 4; u++) q[u] = __ldg(a.rec0 + p + u * G);
-#pragma unroll
-            for (int u = 0; u < 4; u++)
-                acc += ws[q[u].x >> 24] * U[(q[u].x & kIdx) * TILE + b] * U[(int64_t)q[u].y * TILE + b];
-        }
-        for (; p < e; p += G) {
-            uint2 q = __ldg(a.rec0 + p);
-            acc += ws[q.x >> 24] * U[(q.x & kIdx) * TILE + b] * U[(int64_t)q.y * TILE + b];
-        }
-        acc = group_sum(acc, TILE);
-        if (g == 0) xis[r * TILE + b] = acc;
-    }
+    stage_stream<T, TILE, NOPS, true>(rps0, a.n_g, a.rec0, U, nullptr, ws, a.n, xis);
     __syncthreads();
-    // commutator stage: K_o[k][b] = sum beta xi[a][b] U_o[j][b]
-    for (int64_t r = warp; r < n; r += kWarps) {
-        T acc[NOPS];
-#pragma unroll
-        for (int o = 0; o < NOPS; o++) acc[o] = T(0);
-        const uint64_t e = a.rp1[r + 1];
-        uint64_t p = a.rp1[r] + g;
-        for (; p + 3 * G < e; p += 4 * G) {   // four records in flight per group
-            uint2 q[4];
-#pragma unroll
-            for (int u = 0; u < 4; u++) q[u] = __ldg(a.rec1 + p + u * G);
-            T c[4], xv[4][NOPS];
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                c[u] = ws[q[u].x >> 24] * xis[(q[u].x & kIdx) * TILE + b];
-                const int64_t j = (int64_t)q[u].y * TILE + b;
-#pragma unroll
-                for (int o = 0; o < NOPS; o++) xv[u][o] = U[o * n * TILE + j];
-            }
-#pragma unroll
-            for (int u = 0; u < 4; u++)
-#pragma unroll
-                for (int o = 0; o < NOPS; o++) acc[o] += c[u] * xv[u][o];
-        }
-        for (; p < e; p += G) {
-            uint2 q = __ldg(a.rec1 + p);
-            const T c = ws[q.x >> 24] * xis[(q.x & kIdx) * TILE + b];
-            const int64_t j = (int64_t)q.y * TILE + b;
-#pragma unroll
-            for (int o = 0; o < NOPS; o++) acc[o] += c * U[o * n * TILE + j];
-        }
-#pragma unroll
-        for (int o = 0; o < NOPS; o++) {
-            T v = group_sum(acc[o], TILE);
-            if (g == 0) K[(o * n + r) * TILE + b] = v;
-        }
-    }
+    stage_stream<T, TILE, NOPS, false>(rps1, a.n, a.rec1, U, xis, ws, a.n, K);
 }
 
 template <typename T, int TILE, int NOPS>
@@ -141,6 +187,8 @@ __global__ void __launch_bounds__(kThreads, 1) flow_batched_kernel(Args a) {
     T *U = reinterpret_cast<T *>(red + kThreads);       // [NOPS][n][TILE]
     T *xis = U + L * TILE;                              // [n_g][TILE]
     T *ws = xis + a.n_g * TILE;                         // [256]
+    uint32_t *rps0 = reinterpret_cast<uint32_t *>(ws + 256);   // [n_g + 1] record offsets
+    uint32_t *rps1 = rps0 + a.n_g + 1;                         // [n + 1]
     __shared__ int inst[TILE], status[TILE], need_k1[TILE], acc_flag[TILE];
     __shared__ double s_[TILE], ds_[TILE];
     __shared__ long long steps_[TILE], attempts_[TILE];
@@ -148,6 +196,8 @@ __global__ void __launch_bounds__(kThreads, 1) flow_batched_kernel(Args a) {
     __shared__ long long cta_attempts;
 
     for (int c = threadIdx.x; c < 256; c += kThreads) ws[c] = c < a.n_codes ? T(a.wtab[c]) : T(0);
+    for (int64_t r = threadIdx.x; r <= a.n_g; r += kThreads) rps0[r] = (uint32_t)a.rp0[r];
+    for (int64_t r = threadIdx.x; r <= a.n; r += kThreads) rps1[r] = (uint32_t)a.rp1[r];
     // workspace of this CTA: Y, Y5 (double) then K[7] (T), all [NOPS][n][TILE]
     double *Y = reinterpret_cast<double *>(reinterpret_cast<char *>(a.ws) + (int64_t)blockIdx.x * a.ws_stride);
     double *Y5 = Y + L * TILE;
@@ -224,7 +274,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_batched_kernel(Args a) {
                 U[e] = T(u);
             }
             __syncthreads();
-            rhs_tile<T, TILE, NOPS>(a, U, xis, ws, fsal_first ? Kst(S) : Kst(st));
+            rhs_tile<T, TILE, NOPS>(a, rps0, rps1, U, xis, ws, fsal_first ? Kst(S) : Kst(st));
             __syncthreads();
             if (fsal_first) {   // only the new slots take the fresh K1
                 for (int64_t e = threadIdx.x; e < L * TILE; e += kThreads)
@@ -349,11 +399,13 @@ struct BatchedGraphView {
     int n_codes;
     int64_t n, n_g;
     const unsigned char *sha;
+    int64_t R0, R1;   // records of the two stages
 };
 
 template <typename T, int TILE, int NOPS>
 static size_t smem_bytes(const BatchedGraphView &v) {
-    return sizeof(T) * TILE * ((size_t)NOPS * v.n + v.n_g) + 256 * sizeof(T) + kb::kThreads * sizeof(double);
+    return sizeof(T) * TILE * ((size_t)NOPS * v.n + v.n_g) + 256 * sizeof(T) + kb::kThreads * sizeof(double) +
+           4 * ((size_t)v.n + v.n_g + 2);
 }
 
 template <typename T, int TILE, int NOPS>
@@ -427,7 +479,7 @@ static LaunchFn pick_any(bool fp32, int nops, int tile) {
 
 static size_t smem_for(bool fp32, int nops, int tile, const BatchedGraphView &v) {
     size_t e = fp32 ? 4 : 8;
-    return e * tile * ((size_t)nops * v.n + v.n_g) + 256 * e + kb::kThreads * 8;  // matches smem_bytes
+    return e * tile * ((size_t)nops * v.n + v.n_g) + 256 * e + kb::kThreads * 8 + 4 * ((size_t)v.n + v.n_g + 2);  // matches smem_bytes
 }
 
 static kb::Tableau make_tableau(int method) {
@@ -480,6 +532,8 @@ cut_status flow_batched_impl(const BatchedGraphView &v, int device, int batch, d
     for (int t : {2, 4, 8, 16, 32})
         if (smem_for(fp32, nops, t, v) <= (size_t)dev_smem - 1024) cands.push_back(t);
     if (cands.empty()) return set_error(CUT_ERR_UNSUPPORTED, "cut_flow_batched: registry too large for the shared-memory tile");
+    if (v.R0 >= (int64_t)1 << 32 || v.R1 >= (int64_t)1 << 32)
+        return set_error(CUT_ERR_UNSUPPORTED, "cut_flow_batched: more than 2^32 - 1 records in a stage");
     if (tile != 0 && std::find(cands.begin(), cands.end(), tile) == cands.end())
         return set_error(CUT_ERR_INVALID_ARG, "cut_flow_batched: tile must be one of 2,4,8,16,32 and fit in shared memory");
 

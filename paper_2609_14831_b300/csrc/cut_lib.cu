@@ -1035,6 +1035,7 @@ struct BatchedGraphView {
     int n_codes;
     int64_t n, n_g;
     const unsigned char *sha;
+    int64_t R0, R1;   // records of the two stages
 };
 cut_status flow_batched_impl(const BatchedGraphView &v, int device, int batch, double *h, int n_obs, double *x,
                              int precision, const cut_flow_opts *o, int tile, int *steps_out, int *status_out,
@@ -1053,7 +1054,8 @@ extern "C" cut_status cut_flow_batched(const cut_graph *g, int batch, double *h,
     if (o->replay_steps) return set_error(CUT_ERR_INVALID_ARG, "cut_flow_batched: replay is not supported");
     DeviceGuard dg(g->device);
     BatchedGraphView v{g->st[0].rp, g->st[1].rp, g->st[0].rec, g->st[1].rec, g->wtab,
-                       (int)g->host.num.size(), g->host.n(), g->host.n_g(), g->host.sha};
+                       (int)g->host.num.size(), g->host.n(), g->host.n_g(), g->host.sha,
+                       g->st[0].R, g->st[1].R};
     return flow_batched_impl(v, g->device, batch, h, n_obs, x, precision, o, tile, steps_out, status_out,
                              (cudaStream_t)stream, &g_last_tile);
 }

@@ -9,7 +9,9 @@
 //   warp 1, lane 0 : issues tcgen05.mma (M=128, N=BN, K=16 per instruction)
 //                    and tcgen05.commit to release each stage;
 //   all 4 warps    : epilogue, tcgen05.ld of their 32 TMEM lanes (rows),
-//                    fused bias / GELU / GELU-derivative / transposed stores.
+//                    staged through shared memory so that every global
+//                    access is coalesced; fused bias / GELU / GELU-derivative /
+//                    output affine / FP32 linear skip / transposed stores.
 // Every mbarrier wait is bounded; on expiry the kernel records an error,
 // still frees its tensor memory and returns.
 #pragma once
@@ -192,36 +194,81 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
 
     if (!failed) {
-        const int row = m0 + warp * 32 + lane;
+        // Epilogue through shared memory (the operand ring is idle once the
+        // accumulator is complete): each warp reads 32 rows x 32 columns of
+        // TMEM (thread = row), stages them transposed, and applies the
+        // epilogue with lane = column, so loads of bias / z and row-major
+        // stores are coalesced; the transposed output is written back from
+        // the row layout, where it is coalesced too.
+        static_assert(BN % 32 == 0, "epilogue works on 32-column slices");
+        static_assert(4 * 2 * 32 * 33 * 4 <= STAGES * (A_BYTES + B_BYTES), "staging fits in the ring");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        float *stile = reinterpret_cast<float *>(base) + warp * (2 * 32 * 33);
+        float *ltile = stile + 32 * 33;        // linear-skip terms, same layout
+        const int rbase = m0 + warp * 32;
+        const int myrow = rbase + lane;
 #pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 8) {
-            uint32_t r[8];
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+            uint32_t r[32];
             const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
             asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+                "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
                 : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (row >= ep.M) continue;
 #pragma unroll
-            for (int i = 0; i < 8; i++) {
-                const int col = n0 + c0 + i;
-                if (col >= ep.N) continue;
-                float v = __uint_as_float(r[i]) * ep.alpha;
-                if (ep.bias) v += ep.bias[col];
-                if (ep.post_scale) v = v * ep.post_scale[col] + ep.post_shift[col];
-                if (ep.lin_J) {
-                    float l = 0.0f;
-                    for (int k = 0; k < ep.lin_k; k++)
-                        l = fmaf(ep.lin_J[(int64_t)col * ep.lin_k + k], ep.lin_x[(int64_t)row * ep.lin_k + k], l);
-                    v += l;
+            for (int i = 0; i < 32; i++) stile[lane * 33 + i] = __uint_as_float(r[i]);
+            if (ep.lin_J) {
+                // skip terms sum_k J[col][k] x[row][k] in the row layout (J broadcast)
+                float l[32];
+#pragma unroll
+                for (int i = 0; i < 32; i++) l[i] = 0.0f;
+                if (myrow < ep.M) {
+                    for (int k = 0; k < ep.lin_k; k++) {
+                        const float xv = ep.lin_x[(int64_t)myrow * ep.lin_k + k];
+#pragma unroll
+                        for (int i = 0; i < 32; i++) {
+                            const int col = n0 + c0 + i;
+                            if (col < ep.N) l[i] = fmaf(ep.lin_J[(int64_t)col * ep.lin_k + k], xv, l[i]);
+                        }
+                    }
                 }
+#pragma unroll
+                for (int i = 0; i < 32; i++) ltile[lane * 33 + i] = l[i];
+            }
+            __syncwarp();
+            const int col = n0 + c0 + lane;
+            const bool colok = col < ep.N;
+            const float bias = (ep.bias && colok) ? ep.bias[col] : 0.0f;
+            const float psc = (ep.post_scale && colok) ? ep.post_scale[col] : 1.0f;
+            const float psh = (ep.post_scale && colok) ? ep.post_shift[col] : 0.0f;
+#pragma unroll 4
+            for (int rr = 0; rr < 32; rr++) {
+                const int row = rbase + rr;
+                if (!colok || row >= ep.M) continue;
+                float v = stile[rr * 33 + lane] * ep.alpha + bias;
+                if (ep.post_scale) v = v * psc + psh;
+                if (ep.lin_J) v += ltile[rr * 33 + lane];
                 if (ep.dgelu_z) v *= dgelu(ep.dgelu_z[(int64_t)row * ep.ldz + col]);
                 if (ep.out_f32) ep.out_f32[(int64_t)row * ep.ld_f32 + col] = v;
                 const float a = ep.act ? gelu(v) : v;
                 if (ep.out_bf16) ep.out_bf16[(int64_t)row * ep.ld_bf16 + col] = __float2bfloat16(a);
-                if (ep.out_t) ep.out_t[(int64_t)col * ep.ld_t + row] = __float2bfloat16(a);
+                stile[rr * 33 + lane] = a;
             }
+            __syncwarp();
+            if (ep.out_t && myrow < ep.M) {
+#pragma unroll 4
+                for (int i = 0; i < 32; i++) {
+                    const int cc = n0 + c0 + i;
+                    if (cc < ep.N) ep.out_t[(int64_t)cc * ep.ld_t + myrow] = __float2bfloat16(stile[lane * 33 + i]);
+                }
+            }
+            __syncwarp();
         }
     } else {
         if (threadIdx.x == 0) {
