@@ -429,12 +429,17 @@ class MLP:
         check(lib().cut_mlp_forward(self._h, x.shape[0], _ptr(x), _ptr(y), _stream(stream)))
         return y
 
-    def backward(self, x, target, stream=None):
-        """Gradients of the standardised MSE; returns the loss tensor (device)."""
+    def backward(self, x, target, loss=None, stream=None):
+        """Gradients of the standardised MSE; returns the loss tensor (device).
+
+        With ``loss`` (a one-element FP32 device tensor) the batch loss is
+        added to it.  Calls that repeat the same x, target and loss buffers
+        replay one captured CUDA graph of the whole forward and backward pass."""
         torch = _torch()
         x = self._f32(x, self.n_in)
         t = self._f32(target, self.n_out)
-        loss = torch.zeros(1, dtype=torch.float32, device=self.device)
+        if loss is None:
+            loss = torch.zeros(1, dtype=torch.float32, device=self.device)
         check(lib().cut_mlp_backward(self._h, x.shape[0], _ptr(x), _ptr(t), _ptr(loss), _stream(stream)))
         return loss
 

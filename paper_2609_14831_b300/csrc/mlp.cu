@@ -86,22 +86,39 @@ __global__ void col_sum(const float *__restrict__ dz, int ld, int rows, int cols
 
 // AdamW (Loshchilov & Hutter): decoupled weight decay; refreshes the BF16
 // copies W and W^T.  Parameters are [out][in] (bias: in = 1, no transpose).
-__global__ void adamw(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m, float *__restrict__ v,
-                      int64_t count, int in_p, float lr, float b1, float b2, float eps, float wd, float bc1, float bc2,
-                      bf16 *__restrict__ wb, bf16 *__restrict__ wt, int out_p) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
-        const float gr = g[e];
-        const float mm = b1 * m[e] + (1.0f - b1) * gr;
-        const float vv = b2 * v[e] + (1.0f - b2) * gr * gr;
-        m[e] = mm;
-        v[e] = vv;
-        float x = w[e];
-        x -= lr * ((mm / bc1) / (sqrtf(vv / bc2) + eps) + wd * x);
-        w[e] = x;
-        if (wb) {
-            const bf16 b = __float2bfloat16(x);
-            wb[e] = b;
-            if (wt) wt[(e % in_p) * (int64_t)out_p + e / in_p] = b;
+// AdamW over every parameter segment of the network in one launch.
+struct AdamSeg {
+    float *w, *g, *m, *v;
+    bf16 *wb, *wt;      // BF16 copies (weights only)
+    int64_t count, start;
+    int in_p, out_p;
+    float wd;
+};
+struct AdamSegs {
+    AdamSeg s[6];
+    int n;
+    int64_t total;
+};
+
+__global__ void adamw_all(AdamSegs segs, float lr, float b1, float b2, float eps, float bc1, float bc2) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < segs.total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int k = 0;
+        while (k + 1 < segs.n && t >= segs.s[k + 1].start) k++;
+        const AdamSeg &S = segs.s[k];
+        const int64_t e = t - S.start;
+        const float gr = S.g[e];
+        const float mm = b1 * S.m[e] + (1.0f - b1) * gr;
+        const float vv = b2 * S.v[e] + (1.0f - b2) * gr * gr;
+        S.m[e] = mm;
+        S.v[e] = vv;
+        float x = S.w[e];
+        x -= lr * ((mm / bc1) / (sqrtf(vv / bc2) + eps) + S.wd * x);
+        S.w[e] = x;
+        if (S.wb) {
+            const bf16 bv = __float2bfloat16(x);
+            S.wb[e] = bv;
+            S.wt[(e % S.in_p) * (int64_t)S.out_p + e / S.in_p] = bv;
         }
     }
 }
@@ -214,10 +231,29 @@ struct cut_mlp {
     bf16 *dzb2 = nullptr, *dzt2 = nullptr;
     float *dz32b = nullptr;
     std::vector<void *> allocs;
+    // forward + backward captured as one CUDA graph, replayed while the call
+    // keeps the same batch, buffers and skip term (captured on the second
+    // consecutive call with the same key)
+    struct GraphKey {
+        int batch = -1, Mcap = -1;
+        const void *x = nullptr, *t = nullptr, *loss = nullptr, *J = nullptr;
+        bool operator==(const GraphKey &o) const {
+            return batch == o.batch && Mcap == o.Mcap && x == o.x && t == o.t && loss == o.loss && J == o.J;
+        }
+    } gkey;
+    int gseen = 0;
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t gstream = nullptr;
+    void drop_graph() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        gexec = nullptr;
+    }
     ~cut_mlp() {
         int cur = 0;
         cudaGetDevice(&cur);
         cudaSetDevice(device);
+        drop_graph();
+        if (gstream) cudaStreamDestroy(gstream);
         for (void *p : allocs) cudaFree(p);
         cudaSetDevice(cur);
     }
@@ -438,11 +474,10 @@ cut_status cut_mlp_forward(cut_mlp *m, int batch, const float *x, float *y, cut_
     return set_ok();
 }
 
-cut_status cut_mlp_backward(cut_mlp *m, int batch, const float *x, const float *target, float *loss,
-                            cut_stream_t stream) {
-    if (!m || batch < 1 || !x || !target) return set_error(CUT_ERR_INVALID_ARG, "cut_mlp_backward: bad argument");
-    cudaSetDevice(m->device);
-    cudaStream_t s = (cudaStream_t)stream;
+}  // extern "C"
+
+static cut_status backward_body(cut_mlp *m, int batch, const float *x, const float *target, float *loss,
+                                cudaStream_t s) {
     cut_status st = forward(m, batch, x, s, nullptr, nullptr, nullptr);
     if (st != CUT_OK) return st;
     const int Mp = pad_to(batch, 128);
@@ -486,6 +521,48 @@ cut_status cut_mlp_backward(cut_mlp *m, int batch, const float *x, const float *
     return set_ok();
 }
 
+extern "C" {
+cut_status cut_mlp_backward(cut_mlp *m, int batch, const float *x, const float *target, float *loss,
+                            cut_stream_t stream) {
+    if (!m || batch < 1 || !x || !target) return set_error(CUT_ERR_INVALID_ARG, "cut_mlp_backward: bad argument");
+    cudaSetDevice(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cut_status st = ensure_batch(m, pad_to(batch, 128));   // no allocation inside a capture
+    if (st != CUT_OK) return st;
+    cut_mlp::GraphKey key;
+    key.batch = batch;
+    key.Mcap = m->Mcap;
+    key.x = x;
+    key.t = target;
+    key.loss = loss;
+    key.J = m->J;
+    if (!(key == m->gkey)) {
+        m->drop_graph();
+        m->gkey = key;
+        m->gseen = 0;
+    }
+    m->gseen++;
+    if (!m->gexec && m->gseen >= 2) {
+        if (!m->gstream) cudaStreamCreateWithFlags(&m->gstream, cudaStreamNonBlocking);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(m->gstream, cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) {
+            st = backward_body(m, batch, x, target, loss, m->gstream);
+            e = cudaStreamEndCapture(m->gstream, &graph);
+            if (st == CUT_OK && e == cudaSuccess && graph) e = cudaGraphInstantiate(&m->gexec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (st != CUT_OK || e != cudaSuccess) m->drop_graph();
+        }
+        cudaGetLastError();   // a failed capture falls back to direct launches
+    }
+    if (m->gexec) {
+        cudaError_t e = cudaGraphLaunch(m->gexec, s);
+        if (e != cudaSuccess) return set_error(CUT_ERR_CUDA, std::string("cut_mlp_backward: ") + cudaGetErrorString(e));
+        return set_ok();
+    }
+    return backward_body(m, batch, x, target, loss, s);
+}
+
 cut_status cut_mlp_adamw_step(cut_mlp *m, float lr, float beta1, float beta2, float eps, float weight_decay,
                               cut_stream_t stream) {
     if (!m || !(lr >= 0) || !(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1) || !(eps > 0))
@@ -495,14 +572,21 @@ cut_status cut_mlp_adamw_step(cut_mlp *m, float lr, float beta1, float beta2, fl
     m->t++;
     const float bc1 = 1.0f - (float)std::pow((double)beta1, (double)m->t);
     const float bc2 = 1.0f - (float)std::pow((double)beta2, (double)m->t);
+    mlpk::AdamSegs segs;
+    memset(&segs, 0, sizeof(segs));
+    int64_t start = 0;
     for (int l = 0; l < 3; l++) {
         Layer &Ly = m->L[l];
-        const int64_t cnt = (int64_t)Ly.in_p * Ly.out_p;
-        mlpk::adamw<<<grid_of(cnt), 256, 0, s>>>(Ly.w, Ly.gw, Ly.mw, Ly.vw, cnt, Ly.in_p, lr, beta1, beta2, eps,
-                                                 weight_decay, bc1, bc2, Ly.wb, Ly.wt, Ly.out_p);
-        mlpk::adamw<<<grid_of(Ly.out_p), 256, 0, s>>>(Ly.b, Ly.gb, Ly.mb, Ly.vb, Ly.out_p, 1, lr, beta1, beta2, eps, 0.0f,
-                                                      bc1, bc2, nullptr, nullptr, 1);
+        mlpk::AdamSeg &W = segs.s[segs.n++];
+        W = {Ly.w, Ly.gw, Ly.mw, Ly.vw, Ly.wb, Ly.wt, (int64_t)Ly.in_p * Ly.out_p, start, Ly.in_p, Ly.out_p,
+             weight_decay};
+        start += W.count;
+        mlpk::AdamSeg &B = segs.s[segs.n++];
+        B = {Ly.b, Ly.gb, Ly.mb, Ly.vb, nullptr, nullptr, (int64_t)Ly.out_p, start, 1, 1, 0.0f};
+        start += B.count;
     }
+    segs.total = start;
+    mlpk::adamw_all<<<grid_of(start), 256, 0, s>>>(segs, lr, beta1, beta2, eps, bc1, bc2);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(CUT_ERR_CUDA, std::string("cut_mlp_adamw_step: ") + cudaGetErrorString(e));
     return set_ok();

@@ -82,16 +82,24 @@ class Surrogate:
         total = epochs * steps
         hist = []
         it = 0
+        # fixed staging buffers: every step reuses the same device pointers, so
+        # the library replays its captured forward/backward graph
+        xs = torch.empty(min(batch, N), x.shape[1], dtype=torch.float32, device=self.dev)
+        ts = torch.empty(min(batch, N), t32.shape[1], dtype=torch.float32, device=self.dev)
+        loss = torch.zeros(1, dtype=torch.float32, device=self.dev)
         for ep in range(epochs):
             perm = torch.randperm(N, generator=g).to(self.dev)
+            loss.zero_()
             for s in range(steps):
                 idx = perm[s * batch:(s + 1) * batch]
+                torch.index_select(x, 0, idx, out=xs)
+                torch.index_select(t32, 0, idx, out=ts)
                 # cosine learning-rate decay
                 cur = lr * 0.5 * (1 + np.cos(np.pi * it / total))
-                loss = self.net.backward(x[idx].contiguous(), t32[idx].contiguous())
+                self.net.backward(xs, ts, loss=loss)
                 self.net.step(lr=cur, weight_decay=weight_decay)
                 it += 1
-            hist.append(float(loss.item()))
+            hist.append(float(loss.item()) / steps)   # mean batch loss of the epoch
             if log:
                 log(ep, hist[-1])
         self.net.status()

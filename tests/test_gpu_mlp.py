@@ -117,3 +117,27 @@ def test_linear_skip_term():
     m.set_linear(None)
     y0 = m.forward(X).cpu().numpy().astype(np.float64)
     assert _rel(y0, scale * Yh + shift) < 5e-3
+
+
+def test_replayed_backward_graph_equals_direct_launches():
+    """The second call with the same buffers captures the forward/backward
+    pass as a CUDA graph and later calls replay it: the gradients must equal
+    the first (direct) call's bit for bit, the loss accumulates into the
+    caller's buffer, and a new buffer falls back to direct launches."""
+    import torch
+    m, layers, X, T, scale, shift = _setup(32, 512, 848, 300, seed=44)
+    Xd, Td = torch.tensor(X, device="cuda"), torch.tensor(T, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    grads = []
+    for _ in range(4):                     # direct, capture + replay, replay, replay
+        m.backward(Xd, Td, loss=loss)
+        grads.append(m.params(grads=True))
+    m.status()
+    for g in grads[1:]:
+        np.testing.assert_array_equal(g, grads[0])
+    one = m.backward(Xd, Td).item()        # a new loss buffer: direct launches again
+    assert abs(loss.item() - 4 * one) <= 1e-5 * abs(4 * one)
+    np.testing.assert_array_equal(m.params(grads=True), grads[0])
+    want_loss, _ = omlp.loss_and_grads(layers, X.astype(np.float64), T.astype(np.float64), scale, shift,
+                                       emulate=True)
+    assert abs(one - want_loss) <= 5e-3 * abs(want_loss)
