@@ -46,8 +46,12 @@ struct Args {
     const uint2 *rec0, *rec1;
     const double *wtab;
     int n_codes;
+    int signs;                  // factors are +-mag with codes < 32: signs from negmask, no table
+    uint32_t negmask;
+    double mag;
     int64_t n, n_g;
     int nops, B;
+    int slots;                  // instance slots used per CTA (<= TILE)
     double *H, *X;              // user state, instance-major, in/out
     int *steps_out, *status_out;
     int *queue;                 // next instance to start
@@ -58,6 +62,12 @@ struct Args {
     long long probe_attempts;   // > 0: stop every CTA after that many attempts (autotuning)
     Tableau tb;
 };
+
+// v with its sign flipped when neg is 1 (an integer XOR, no multiply)
+__device__ __forceinline__ float flip_if(float v, uint32_t neg) { return __uint_as_float(__float_as_uint(v) ^ (neg << 31)); }
+__device__ __forceinline__ double flip_if(double v, uint32_t neg) {
+    return __longlong_as_double(__double_as_longlong(v) ^ ((long long)neg << 63));
+}
 
 // first row index in [0, rows] whose offset is >= target (rps[rows] >= target)
 __device__ __forceinline__ int64_t lower_row(const uint32_t *rps, int64_t rows, uint32_t target) {
@@ -84,7 +94,7 @@ template <typename T, int TILE, int NOPS, bool GEN>
 __device__ __forceinline__ void stage_stream(const uint32_t *__restrict__ rps, int64_t rows,
                                              const uint2 *__restrict__ rec, const T *__restrict__ U,
                                              const T *__restrict__ xis, const T *__restrict__ ws, int64_t n,
-                                             T *__restrict__ out) {
+                                             T *__restrict__ out, int signs, uint32_t negmask, T mag) {
     constexpr int G = 32 / TILE, NG = kWarps * G;
     constexpr int M = TILE >= 8 ? 4 : 8;          // records per lane per chunk
     constexpr int CH = M * TILE;                  // records per group per chunk
@@ -106,7 +116,7 @@ __device__ __forceinline__ void stage_stream(const uint32_t *__restrict__ rps, i
     auto flush = [&]() {
 #pragma unroll
         for (int o = 0; o < NA; o++) {
-            out[((int64_t)o * (GEN ? 0 : n) + cur) * TILE + b] = acc[o];
+            out[((int64_t)o * (GEN ? 0 : n) + cur) * TILE + b] = signs ? acc[o] * mag : acc[o];
             acc[o] = T(0);
         }
         cur++;
@@ -137,11 +147,12 @@ __device__ __forceinline__ void stage_stream(const uint32_t *__restrict__ rps, i
                     q.x = __shfl_sync(gmask, v[0].x, s0 + s, TILE);
                     q.y = __shfl_sync(gmask, v[0].y, s0 + s, TILE);
                     const int64_t i = (int64_t)(q.x & kIdx) * TILE + b, j = (int64_t)q.y * TILE + b;
+                    const uint32_t code = q.x >> 24;
+                    const T src = GEN ? U[i] : xis[i];
+                    cf[s] = signs ? flip_if(src, (negmask >> (code & 31)) & 1u) : ws[code] * src;
                     if (GEN) {
-                        cf[s] = ws[q.x >> 24] * U[i];
                         uv[s][0] = U[j];
                     } else {
-                        cf[s] = ws[q.x >> 24] * xis[i];
 #pragma unroll
                         for (int o = 0; o < NA; o++) uv[s][o] = U[(int64_t)o * n * TILE + j];
                     }
@@ -174,9 +185,9 @@ template <typename T, int TILE, int NOPS>
 __device__ void rhs_tile(const Args &a, const uint32_t *__restrict__ rps0, const uint32_t *__restrict__ rps1,
                          const T *__restrict__ U, T *__restrict__ xis, const T *__restrict__ ws,
                          T *__restrict__ K) {
-    stage_stream<T, TILE, NOPS, true>(rps0, a.n_g, a.rec0, U, nullptr, ws, a.n, xis);
+    stage_stream<T, TILE, NOPS, true>(rps0, a.n_g, a.rec0, U, nullptr, ws, a.n, xis, a.signs, a.negmask, T(a.mag));
     __syncthreads();
-    stage_stream<T, TILE, NOPS, false>(rps1, a.n, a.rec1, U, xis, ws, a.n, K);
+    stage_stream<T, TILE, NOPS, false>(rps1, a.n, a.rec1, U, xis, ws, a.n, K, a.signs, a.negmask, T(a.mag));
 }
 
 template <typename T, int TILE, int NOPS>
@@ -203,6 +214,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_batched_kernel(Args a) {
     double *Y5 = Y + L * TILE;
     T *Kb = reinterpret_cast<T *>(Y5 + L * TILE);
     auto Kst = [&](int s) { return Kb + (int64_t)s * L * TILE; };
+    T *Yf = Kst(8);   // FP32 path: the state rounded to FP32 (stage inputs are formed in FP32)
     if (threadIdx.x < TILE) { inst[threadIdx.x] = -1; status[threadIdx.x] = 0; }
     if (threadIdx.x == 0) cta_attempts = 0;
     __syncthreads();
@@ -215,7 +227,9 @@ __global__ void __launch_bounds__(kThreads, 1) flow_batched_kernel(Args a) {
         if (threadIdx.x < TILE) {
             const int t = threadIdx.x;
             need_k1[t] = 0;
-            if (inst[t] == -1) {
+            if (inst[t] == -1 && t >= a.slots) {
+                inst[t] = -2;   // slot not used at this CTA count
+            } else if (inst[t] == -1) {
                 int b = atomicAdd(a.queue, 1);
                 if (b < a.B) {
                     inst[t] = b;
@@ -243,7 +257,9 @@ __global__ void __launch_bounds__(kThreads, 1) flow_batched_kernel(Args a) {
             if (!need_k1[b]) continue;
             const int64_t row = e / TILE, o = row / n, k = row % n;
             const int64_t i = inst[b];
-            Y[e] = o == 0 ? a.H[i * n + k] : a.X[(i * (NOPS - 1) + (o - 1)) * n + k];
+            const double y0 = o == 0 ? a.H[i * n + k] : a.X[(i * (NOPS - 1) + (o - 1)) * n + k];
+            Y[e] = y0;
+            if (sizeof(T) == 4) Yf[e] = T(y0);
         }
         __syncthreads();
         if (!any_active) break;
@@ -254,23 +270,35 @@ __global__ void __launch_bounds__(kThreads, 1) flow_batched_kernel(Args a) {
             const bool fsal_first = tb.adaptive && st == 0;
             if (fsal_first && !any_new) continue;       // K1 = f(Y) carried over (FSAL)
             // U = Y + ds sum_j a[st][j] K_j, rounded to T into shared memory.
-            // FP32 slopes: the stage sum is formed in FP32 (the slopes carry
-            // FP32 precision anyway) and added to the FP64 state with one FP64
-            // FMA; FP64 slopes: all in FP64.
+            // FP32 slopes: the stage inputs are formed in FP32 from the FP32
+            // copy of the state (they are rounded to FP32 anyway); only the
+            // candidate state Y5 (last DP45 stage) is formed in FP64, with one
+            // FP64 FMA.  FP64 slopes: all in FP64.
+            const double ds = ds_[mb];
+            const float dsf = (float)ds;
+            float af[7];
+#pragma unroll
+            for (int j = 0; j < 7; j++) af[j] = (float)tb.a[st][j];
+            const bool y5_stage = tb.adaptive && st == S - 1;
             for (int64_t e = threadIdx.x; e < L * TILE; e += kThreads) {
-                const double ds = ds_[mb];
                 double u;
                 if (sizeof(T) == 4) {
                     float inc = 0.0f;
-                    for (int j = 0; j < st; j++)
-                        if (tb.a[st][j] != 0.0) inc = fmaf((float)tb.a[st][j], (float)Kst(j)[e], inc);
+#pragma unroll
+                    for (int j = 0; j < 7; j++)
+                        if (j < st && af[j] != 0.0f) inc = fmaf(af[j], (float)Kst(j)[e], inc);
+                    if (!y5_stage) {
+                        U[e] = T(fmaf(dsf, inc, (float)Yf[e]));
+                        continue;
+                    }
                     u = fma(ds, (double)inc, Y[e]);
                 } else {
                     u = Y[e];
-                    for (int j = 0; j < st; j++)
-                        if (tb.a[st][j] != 0.0) u += (tb.a[st][j] * ds) * (double)Kst(j)[e];
+#pragma unroll
+                    for (int j = 0; j < 7; j++)
+                        if (j < st && tb.a[st][j] != 0.0) u += (tb.a[st][j] * ds) * (double)Kst(j)[e];
                 }
-                if (tb.adaptive && st == S - 1) Y5[e] = u;
+                if (y5_stage) Y5[e] = u;
                 U[e] = T(u);
             }
             __syncthreads();
@@ -292,30 +320,35 @@ __global__ void __launch_bounds__(kThreads, 1) flow_batched_kernel(Args a) {
                     double r;
                     if (sizeof(T) == 4) {   // error ratio in FP32 from FP32 slopes
                         float err = 0.0f;
-                        for (int j = 0; j < S; j++)
-                            if (tb.e[j] != 0.0) err = fmaf((float)tb.e[j], (float)Kst(j)[e], err);
-                        const float sc = (float)a.atol + (float)a.rtol * fmaxf(fabsf((float)Y[e]), fabsf((float)Y5[e]));
+#pragma unroll
+                        for (int j = 0; j < 7; j++)
+                            if (j < S && tb.e[j] != 0.0) err = fmaf((float)tb.e[j], (float)Kst(j)[e], err);
+                        // U holds the last stage input, FP32(Y5)
+                        const float sc = (float)a.atol + (float)a.rtol * fmaxf(fabsf((float)Yf[e]), fabsf((float)U[e]));
                         r = (double)(fabsf((float)ds * err) / sc);
                     } else {
                         double err = 0.0;
-                        for (int j = 0; j < S; j++)
-                            if (tb.e[j] != 0.0) err += (ds * tb.e[j]) * (double)Kst(j)[e];
+#pragma unroll
+                        for (int j = 0; j < 7; j++)
+                            if (j < S && tb.e[j] != 0.0) err += (ds * tb.e[j]) * (double)Kst(j)[e];
                         const double sc = a.atol + a.rtol * fmax(fabs(Y[e]), fabs(Y5[e]));
                         r = fabs(err) / sc;
                     }
-                    if (!(r == r) || !isfinite(Y5[e])) bad = true;
+                    if (!(r == r) || !isfinite(sizeof(T) == 4 ? (double)U[e] : Y5[e])) bad = true;
                     else m = fmax(m, r);
                 } else {
                     double y;
                     if (sizeof(T) == 4) {
                         float inc = 0.0f;
-                        for (int j = 0; j < S; j++)
-                            if (tb.b[j] != 0.0) inc = fmaf((float)tb.b[j], (float)Kst(j)[e], inc);
+#pragma unroll
+                        for (int j = 0; j < 7; j++)
+                            if (j < S && tb.b[j] != 0.0) inc = fmaf((float)tb.b[j], (float)Kst(j)[e], inc);
                         y = fma(ds, (double)inc, Y[e]);
                     } else {
                         y = Y[e];
-                        for (int j = 0; j < S; j++)
-                            if (tb.b[j] != 0.0) y += (tb.b[j] * ds) * (double)Kst(j)[e];
+#pragma unroll
+                        for (int j = 0; j < 7; j++)
+                            if (j < S && tb.b[j] != 0.0) y += (tb.b[j] * ds) * (double)Kst(j)[e];
                     }
                     Y5[e] = y;
                     if (!isfinite(y)) bad = true;
@@ -374,6 +407,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_batched_kernel(Args a) {
             const int b = (int)(e % TILE);
             if (acc_flag[b] & 1) {
                 Y[e] = Y5[e];
+                if (sizeof(T) == 4) Yf[e] = tb.adaptive ? U[e] : T(Y5[e]);
                 if (tb.adaptive) Kst(0)[e] = Kst(S - 1)[e];
             }
             if (acc_flag[b] & 2) {
@@ -400,6 +434,9 @@ struct BatchedGraphView {
     int64_t n, n_g;
     const unsigned char *sha;
     int64_t R0, R1;   // records of the two stages
+    int uniform;      // every factor is +-mag
+    double mag;
+    uint32_t negmask; // sign of each code (codes < 32)
 };
 
 template <typename T, int TILE, int NOPS>
@@ -411,7 +448,7 @@ static size_t smem_bytes(const BatchedGraphView &v) {
 template <typename T, int TILE, int NOPS>
 static size_t ws_bytes(const BatchedGraphView &v) {
     size_t L = (size_t)NOPS * v.n * TILE;
-    size_t b = L * (2 * sizeof(double) + 8 * sizeof(T));
+    size_t b = L * (2 * sizeof(double) + 9 * sizeof(T));   // Y, Y5, K[8], FP32 state copy
     return (b + 255) & ~size_t(255);
 }
 
@@ -428,7 +465,13 @@ static cudaError_t launch_tile(const BatchedGraphView &v, kb::Args args, int max
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kb::kThreads, sm);
     if (e != cudaSuccess) return e;
     if (per < 1) return cudaErrorInvalidConfiguration;
-    int ctas = std::min<int64_t>((args.B + TILE - 1) / TILE, (int64_t)nsm * per);
+    // slots per CTA: the fewest that still put the whole batch in flight on
+    // every resident CTA (1024 instances, 148 SMs, TILE 8 -> 7 slots x 147 CTAs)
+    const int64_t resident = (int64_t)nsm * per;
+    int slots = (int)std::min<int64_t>(TILE, (args.B + resident - 1) / resident);
+    if (slots < 1) slots = 1;
+    args.slots = slots;
+    int ctas = (int)std::min<int64_t>((args.B + slots - 1) / slots, resident);
     if (max_ctas > 0) ctas = std::min(ctas, max_ctas);
     size_t need = ws_bytes<T, TILE, NOPS>(v) * ctas;
     if (need > *ws_cap) {
@@ -439,7 +482,7 @@ static cudaError_t launch_tile(const BatchedGraphView &v, kb::Args args, int max
     }
     args.ws = (double *)*ws_base;
     args.ws_stride = (int64_t)ws_bytes<T, TILE, NOPS>(v);
-    if (ctas_out) *ctas_out = ctas;
+    if (ctas_out) *ctas_out = (int)std::min<int64_t>(args.B, (int64_t)ctas * slots);   // instances in flight
     kern<<<ctas, kb::kThreads, sm, s>>>(args);
     return cudaGetLastError();
 }
@@ -541,6 +584,9 @@ cut_status flow_batched_impl(const BatchedGraphView &v, int device, int batch, d
     memset(&a, 0, sizeof(a));
     a.rp0 = v.rp0; a.rp1 = v.rp1; a.rec0 = v.rec0; a.rec1 = v.rec1;
     a.wtab = v.wtab; a.n_codes = v.n_codes; a.n = v.n; a.n_g = v.n_g;
+    a.signs = v.uniform && v.n_codes <= 32;
+    a.negmask = v.negmask;
+    a.mag = v.mag;
     a.nops = nops; a.B = batch;
     a.s0 = o->s0; a.s1 = o->s1; a.rtol = o->rtol; a.atol = o->atol;
     a.tb = make_tableau(o->method);
@@ -614,7 +660,7 @@ cut_status flow_batched_impl(const BatchedGraphView &v, int device, int batch, d
                 float ms = 0;
                 cudaEventElapsedTime(&ms, t0, t1);
                 // time per instance-attempt: every resident slot ran two attempts
-                const double inflight = std::min<double>(batch, (double)ctas * t);
+                const double inflight = (double)ctas;
                 const float norm = (float)(ms / inflight);
                 if (norm < best) { best = norm; tile = t; }
             }

@@ -52,6 +52,7 @@ struct cut_graph {
     unsigned long long *wsign = nullptr;  // sign bit per code
     double wmag = 1.0;             // common magnitude when all factors share it
     int wuniform = 0;
+    uint32_t wnegmask = 0;         // bit c set when factor c < 0 (codes < 32)
     int arith = CUT_ARITH_FP64;    // arithmetic of the commutator stage
     int64_t device_bytes = 0;
     std::mutex mu;
@@ -220,7 +221,15 @@ static void apply_L(const cut_graph *g, const double *xi, float2 *xi2, float2 *X
 }
 
 static size_t df_scratch_bytes(const cut_graph *g) {
-    return g->arith == CUT_ARITH_DF64 ? (size_t)(std::max<int64_t>(1, g->host.n_g()) + 4 * g->host.n()) * 8 : 0;
+    return g->arith == CUT_ARITH_DF64 ? (size_t)(std::max<int64_t>(1, g->host.n_g()) + 4 * g->host.n()) * 8 + 32 : 0;
+}
+
+// Double-float scratch: xi2[n_g] pairs, then X2[n][4] pairs starting on a
+// 32-byte boundary (the stage reads one index's block with a 256-bit load).
+static float2 *df_pairs_x(const cut_graph *g, void *df) {
+    if (!df) return nullptr;
+    const uintptr_t p = (uintptr_t)((float2 *)df + std::max<int64_t>(1, g->host.n_g()));
+    return (float2 *)((p + 31) & ~(uintptr_t)31);
 }
 
 // f(Y) for the stacked state Y[nops][n] into DY[nops][n].  df: scratch of
@@ -232,9 +241,7 @@ static void stacked_rhs(const cut_graph *g, const double *Y, double *DY, int nop
     const double *xs[64];
     double *dxs[64];
     for (int o = 0; o < nops; o++) { xs[o] = Y + o * n; dxs[o] = DY + o * n; }
-    float2 *xi2 = (float2 *)df;
-    float2 *X2 = df ? xi2 + std::max<int64_t>(1, g->host.n_g()) : nullptr;
-    apply_L(g, xi, xi2, X2, nops, xs, dxs, s, done);
+    apply_L(g, xi, (float2 *)df, df_pairs_x(g, df), nops, xs, dxs, s, done);
 }
 
 }  // namespace cut
@@ -282,6 +289,7 @@ cut_status cut_graph_load(const char *path, int device, unsigned flags, cut_grap
         w[c] = (double)g->host.num[c] / (double)g->host.den[c];
         w32[c] = (float)w[c];
         sg[c] = w[c] < 0 ? 0x8000000000000000ull : 0ull;
+        if (w[c] < 0 && c < 32) g->wnegmask |= 1u << c;
         if (std::fabs(w[c]) != std::fabs(w[0]) || w[c] == 0.0) g->wuniform = 0;
     }
     g->wmag = std::fabs(w[0]);
@@ -397,8 +405,7 @@ cut_status cut_rhs(const cut_graph *g, const double *h, int n_obs, const double 
     xs[0] = h;
     dxs[0] = dh;
     for (int o = 0; o < n_obs; o++) { xs[o + 1] = x + o * n; dxs[o + 1] = dx + o * n; }
-    float2 *xi2 = (float2 *)df;
-    apply_L(g, xi, xi2, df ? xi2 + std::max<int64_t>(1, g->host.n_g()) : nullptr, n_obs + 1, xs, dxs, s, nullptr);
+    apply_L(g, xi, (float2 *)df, df_pairs_x(g, df), n_obs + 1, xs, dxs, s, nullptr);
     CUDA_TRY(cudaGetLastError());
     if (!xi_out) CUDA_TRY(cudaFreeAsync(xi, s));
     if (df) CUDA_TRY(cudaFreeAsync(df, s));
@@ -426,8 +433,7 @@ cut_status cut_apply_L(const cut_graph *g, const double *xi, int n_ops, const do
     const double *xs[64];
     double *dxs[64];
     for (int o = 0; o < n_ops; o++) { xs[o] = x + o * n; dxs[o] = dx + o * n; }
-    float2 *xi2 = (float2 *)df;
-    apply_L(g, xi, xi2, df ? xi2 + std::max<int64_t>(1, g->host.n_g()) : nullptr, n_ops, xs, dxs, s, nullptr);
+    apply_L(g, xi, (float2 *)df, df_pairs_x(g, df), n_ops, xs, dxs, s, nullptr);
     CUDA_TRY(cudaGetLastError());
     if (df) CUDA_TRY(cudaFreeAsync(df, s));
     return set_ok();
@@ -1036,6 +1042,9 @@ struct BatchedGraphView {
     int64_t n, n_g;
     const unsigned char *sha;
     int64_t R0, R1;   // records of the two stages
+    int uniform;      // every factor is +-mag
+    double mag;
+    uint32_t negmask; // sign of each code (codes < 32)
 };
 cut_status flow_batched_impl(const BatchedGraphView &v, int device, int batch, double *h, int n_obs, double *x,
                              int precision, const cut_flow_opts *o, int tile, int *steps_out, int *status_out,
@@ -1055,7 +1064,7 @@ extern "C" cut_status cut_flow_batched(const cut_graph *g, int batch, double *h,
     DeviceGuard dg(g->device);
     BatchedGraphView v{g->st[0].rp, g->st[1].rp, g->st[0].rec, g->st[1].rec, g->wtab,
                        (int)g->host.num.size(), g->host.n(), g->host.n_g(), g->host.sha,
-                       g->st[0].R, g->st[1].R};
+                       g->st[0].R, g->st[1].R, g->wuniform, g->wmag, g->wnegmask};
     return flow_batched_impl(v, g->device, batch, h, n_obs, x, precision, o, tile, steps_out, status_out,
                              (cudaStream_t)stream, &g_last_tile);
 }

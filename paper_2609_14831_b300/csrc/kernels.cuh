@@ -188,6 +188,14 @@ __device__ __forceinline__ void df_madd(float ch, float cl, float xh, float xl, 
     s = t;
 }
 
+// The 32-byte operand pair block of one input index in one 256-bit load
+// (sm_100 and later): one L1 request per gathered record instead of two.
+__device__ __forceinline__ void ld_pairs32(const float4 *p, float4 &a, float4 &b) {
+    asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+                 : "l"(p));
+}
+
 template <int NOPS, int LANES>
 __global__ void __launch_bounds__(kBlock) comm_stage_df(const uint64_t *__restrict__ rp,
                                                         const uint2 *__restrict__ rec, Weights wt,
@@ -210,9 +218,10 @@ __global__ void __launch_bounds__(kBlock) comm_stage_df(const uint64_t *__restri
         if (r < rows) {
             const uint64_t e = rp[r + 1];
             uint64_t p = rp[r] + sl;
-            // eight records per lane per step, all loads ahead of the
-            // arithmetic (measured best on the 3.4e8-record graph)
-            constexpr int U = 8;
+            // four records per lane per step, all loads ahead of the
+            // arithmetic (measured best with 256-bit operand loads on the
+            // 3.4e8-record graph)
+            constexpr int U = 4;
             for (; p + (U - 1) * LANES < e; p += U * LANES) {
                 uint2 q[U];
 #pragma unroll
@@ -222,8 +231,7 @@ __global__ void __launch_bounds__(kBlock) comm_stage_df(const uint64_t *__restri
 #pragma unroll
                 for (int u = 0; u < U; u++) {
                     cf[u] = xi2[q[u].x & kIdx];
-                    a[u] = X2[2 * (int64_t)q[u].y];
-                    if (NOPS > 2) b[u] = X2[2 * (int64_t)q[u].y + 1];
+                    ld_pairs32(X2 + 2 * (int64_t)q[u].y, a[u], b[u]);
                 }
 #pragma unroll
                 for (int u = 0; u < U; u++) {
@@ -241,13 +249,11 @@ __global__ void __launch_bounds__(kBlock) comm_stage_df(const uint64_t *__restri
                 const unsigned int sb = (unsigned int)(sg[q.x >> 24] >> 32);
                 cf.x = __uint_as_float(__float_as_uint(cf.x) ^ sb);
                 cf.y = __uint_as_float(__float_as_uint(cf.y) ^ sb);
-                const float4 a = X2[2 * (int64_t)q.y];
+                float4 a, b;
+                ld_pairs32(X2 + 2 * (int64_t)q.y, a, b);
                 df_madd(cf.x, cf.y, a.x, a.y, s[0], c[0]);
                 if (NOPS > 1) df_madd(cf.x, cf.y, a.z, a.w, s[1], c[1]);
-                if (NOPS > 2) {
-                    const float4 b = X2[2 * (int64_t)q.y + 1];
-                    df_madd(cf.x, cf.y, b.x, b.y, s[2], c[2]);
-                }
+                if (NOPS > 2) df_madd(cf.x, cf.y, b.x, b.y, s[2], c[2]);
             }
         }
 #pragma unroll
