@@ -13,6 +13,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -41,52 +42,98 @@ __global__ void pack_input(const float *__restrict__ x, int batch, int n_in, int
 }
 
 // dZ = 2 (Y - t_hat) / (batch n_out) on valid entries, t_hat = (T - shift -
-// J x) / scale (J, x optional: the linear skip term); loss sum
-__global__ void mse_grad(const float *__restrict__ Y, int ldy, const float *__restrict__ T, int batch, int n_out,
-                         const float *__restrict__ scale, const float *__restrict__ shift, int Mp, int Np,
-                         bf16 *__restrict__ dz, bf16 *__restrict__ dzt, float *__restrict__ dz32,
-                         float *__restrict__ loss, const float *__restrict__ J, const float *__restrict__ x, int K) {
-    __shared__ float red[256];
-    float acc = 0.0f;
+// J x) / scale (J, x optional: the linear skip term); loss sum.  One 32 x 32
+// tile of (rows, columns) per block of 32 x 8 threads: J and x slices are
+// staged in shared memory, and the transposed copy of dZ is written through
+// a shared tile so that every global access is coalesced.
+__global__ void __launch_bounds__(256) mse_grad(const float *__restrict__ Y, int ldy, const float *__restrict__ T,
+                                                int batch, int n_out, const float *__restrict__ scale,
+                                                const float *__restrict__ shift, int Mp, int Np,
+                                                bf16 *__restrict__ dz, bf16 *__restrict__ dzt,
+                                                float *__restrict__ dz32, float *__restrict__ loss,
+                                                const float *__restrict__ J, const float *__restrict__ x, int K) {
+    __shared__ float Js[32][65], Xs[32][65], Gs[32][33], red[256];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+    const int c0 = blockIdx.x * 32, m0 = blockIdx.y * 32, c = c0 + tx;
     const float inv = 1.0f / ((float)batch * (float)n_out);
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)Mp * Np;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int m = (int)(e / Np), c = (int)(e % Np);
+    float lin[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (J) {
+        for (int k0 = 0; k0 < K; k0 += 64) {
+            const int kc = min(64, K - k0);
+            for (int i = tid; i < 32 * 64; i += 256) {
+                const int r = i / 64, k = i % 64;
+                Js[r][k] = (k < kc && c0 + r < n_out) ? J[(int64_t)(c0 + r) * K + k0 + k] : 0.0f;
+                Xs[r][k] = (k < kc && m0 + r < batch) ? x[(int64_t)(m0 + r) * K + k0 + k] : 0.0f;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+                for (int k = 0; k < kc; k++) lin[i] = fmaf(Js[tx][k], Xs[ty + 8 * i][k], lin[i]);
+            __syncthreads();
+        }
+    }
+    float acc = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const int rr = ty + 8 * i, m = m0 + rr;
         float g = 0.0f;
         if (m < batch && c < n_out) {
-            float lin = 0.0f;
-            if (J)
-                for (int k = 0; k < K; k++) lin = fmaf(J[(int64_t)c * K + k], x[(int64_t)m * K + k], lin);
-            const float t = (T[(int64_t)m * n_out + c] - shift[c] - lin) / scale[c];
+            const float t = (T[(int64_t)m * n_out + c] - shift[c] - lin[i]) / scale[c];
             const float r = Y[(int64_t)m * ldy + c] - t;
             acc += r * r;
             g = 2.0f * r * inv;
         }
+        const int64_t e = (int64_t)m * Np + c;
         dz[e] = __float2bfloat16(g);
-        dzt[(int64_t)c * Mp + m] = __float2bfloat16(g);
         dz32[e] = g;
+        Gs[rr][tx] = g;
     }
-    red[threadIdx.x] = acc;
+    red[tid] = acc;
     __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const int cc = ty + 8 * i;   // column within the tile; lanes run along rows
+        dzt[(int64_t)(c0 + cc) * Mp + m0 + tx] = __float2bfloat16(Gs[tx][cc]);
+    }
+    for (int s = 128; s > 0; s >>= 1) {
+        if (tid < s) red[tid] += red[tid + s];
         __syncthreads();
     }
-    if (threadIdx.x == 0 && loss) atomicAdd(loss, red[0] * inv);
+    if (tid == 0 && loss) atomicAdd(loss, red[0] * inv);
 }
 
-// db[c] = sum_m dz[m][c] (valid rows)
-__global__ void col_sum(const float *__restrict__ dz, int ld, int rows, int cols, float *__restrict__ db) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= cols) return;
+// db[c] = sum_m dz[m][c] (valid rows): 32 columns per block, 8 row groups
+// summed in a fixed order (coalesced rows, deterministic result)
+__global__ void __launch_bounds__(256) col_sum(const float *__restrict__ dz, int ld, int rows, int cols,
+                                               float *__restrict__ db) {
+    __shared__ float part[8][33];
+    const int tx = threadIdx.x, ty = threadIdx.y, c = blockIdx.x * 32 + tx;
     float s = 0.0f;
-    for (int m = 0; m < rows; m++) s += dz[(int64_t)m * ld + c];
-    db[c] = s;
+    if (c < cols) {
+#pragma unroll 4
+        for (int m = ty; m < rows; m += 8) s += dz[(int64_t)m * ld + c];
+    }
+    part[ty][tx] = s;
+    __syncthreads();
+    if (ty == 0 && c < cols) {
+        float t = 0.0f;
+        for (int g = 0; g < 8; g++) t += part[g][tx];
+        db[c] = t;
+    }
+}
+
+// Split-K partial products: out[e] = sum_z part[z][e] in z order.
+__global__ void sum_splits(const float *__restrict__ part, int splits, int64_t count, float *__restrict__ out) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+        float t = 0.0f;
+        for (int z = 0; z < splits; z++) t += part[(int64_t)z * count + e];
+        out[e] = t;
+    }
 }
 
 // AdamW (Loshchilov & Hutter): decoupled weight decay; refreshes the BF16
 // copies W and W^T.  Parameters are [out][in] (bias: in = 1, no transpose).
-// AdamW over every parameter segment of the network in one launch.
+// Every parameter segment of the network in one launch.
 struct AdamSeg {
     float *w, *g, *m, *v;
     bf16 *wb, *wt;      // BF16 copies (weights only)
@@ -169,29 +216,33 @@ static cut_status make_map(CUtensorMap *map, const void *ptr, int rows, int cols
     return CUT_OK;
 }
 
-// C[M][N] = A[M][K] B[N][K]^T, M % 128 == 0, N % 64 == 0, K % 64 == 0
-static cut_status gemm(const bf16 *A, const bf16 *B, int M, int N, int K, tc::Epi ep, cudaStream_t s) {
-    if (M % 128 || N % 64 || K % 64) return set_error(CUT_ERR_INVALID_ARG, "gemm: shape not padded");
+// C[M][N] = A[M][K] B[N][K]^T, M % 128 == 0, N % 64 == 0, K % (64 splits) == 0.
+// splits > 1: split k, partial products to ep.out_f32 + z ep.split_stride.
+static cut_status gemm(const bf16 *A, const bf16 *B, int M, int N, int K, tc::Epi ep, cudaStream_t s,
+                       int splits = 1) {
+    if (M % 128 || N % 64 || splits < 1 || K % (64 * splits)) return set_error(CUT_ERR_INVALID_ARG, "gemm: shape not padded");
     CUtensorMap ma, mb;
     const int bn = (N % 128 == 0) ? 128 : 64;
     cut_status st = make_map(&ma, A, M, K, 128);
     if (st != CUT_OK) return st;
     st = make_map(&mb, B, N, K, bn);
     if (st != CUT_OK) return st;
-    dim3 grid(M / 128, N / bn);
+    dim3 grid(M / 128, N / bn, splits);
     if (bn == 128) {
         auto k = tc::gemm_bf16_tn<128>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::gemm_smem_bytes<128>());
-        k<<<grid, tc::kThreads, tc::gemm_smem_bytes<128>(), s>>>(ma, mb, K, ep);
+        k<<<grid, tc::kThreads, tc::gemm_smem_bytes<128>(), s>>>(ma, mb, K / splits, ep);
     } else {
         auto k = tc::gemm_bf16_tn<64>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::gemm_smem_bytes<64>());
-        k<<<grid, tc::kThreads, tc::gemm_smem_bytes<64>(), s>>>(ma, mb, K, ep);
+        k<<<grid, tc::kThreads, tc::gemm_smem_bytes<64>(), s>>>(ma, mb, K / splits, ep);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(CUT_ERR_CUDA, std::string("gemm launch: ") + cudaGetErrorString(e));
     return CUT_OK;
 }
+
+constexpr int kMaxSplits = 16;   // split-k factor bound of the weight-gradient GEMMs
 
 static tc::Epi epi0(int M, int N, int *err) {
     tc::Epi e;
@@ -219,6 +270,7 @@ struct cut_mlp {
     Layer L[3];
     float *scale = nullptr, *shift = nullptr;   // output affine (targets standardised)
     float *J = nullptr;                         // linear skip [n_out][n_in] (FP32), or null
+    float *splitbuf = nullptr;                  // split-k partial weight gradients
     int *err = nullptr;
     long long t = 0;                            // Adam step
     // activations for the largest padded batch seen
@@ -373,8 +425,10 @@ cut_status cut_mlp_create(int n_in, int n_hidden, int n_out, uint64_t seed, int 
         cudaMemcpy(Ly.w, hw.data(), cnt * 4, cudaMemcpyHostToDevice);
         mlpk::to_bf16<<<grid_of(cnt), 256>>>(Ly.w, cnt, Ly.in_p, Ly.out_p, Ly.wb, Ly.wt);
     }
+    size_t wmax = 0;
+    for (int l = 0; l < 3; l++) wmax = std::max(wmax, (size_t)m->L[l].in_p * m->L[l].out_p);
     if (m->alloc(&m->scale, m->L[2].out_p) != cudaSuccess || m->alloc(&m->shift, m->L[2].out_p) != cudaSuccess ||
-        m->alloc(&m->err, 4) != cudaSuccess)
+        m->alloc(&m->err, 4) != cudaSuccess || m->alloc(&m->splitbuf, wmax * kMaxSplits) != cudaSuccess)
         return set_error(CUT_ERR_OUT_OF_MEMORY, "cut_mlp_create: buffers");
     std::vector<float> one(m->L[2].out_p, 1.0f);
     cudaMemcpy(m->scale, one.data(), one.size() * 4, cudaMemcpyHostToDevice);
@@ -483,21 +537,33 @@ static cut_status backward_body(cut_mlp *m, int batch, const float *x, const flo
     const int Mp = pad_to(batch, 128);
     Layer *L = m->L;
     // output layer
-    mlpk::mse_grad<<<grid_of((int64_t)Mp * L[2].out_p), 256, 0, s>>>(m->z[2], L[2].out_p, target, batch, m->n_out,
-                                                                       m->scale, m->shift, Mp, L[2].out_p, m->dzb,
-                                                                       m->dzt, m->dz32, loss, m->J, x, m->n_in);
+    mlpk::mse_grad<<<dim3(L[2].out_p / 32, Mp / 32), dim3(32, 8), 0, s>>>(
+        m->z[2], L[2].out_p, target, batch, m->n_out, m->scale, m->shift, Mp, L[2].out_p, m->dzb, m->dzt, m->dz32,
+        loss, m->J, x, m->n_in);
     bf16 *dzb = m->dzb, *dzt = m->dzt, *nb = m->dzb2, *nt = m->dzt2;
     float *dz32 = m->dz32, *n32 = m->dz32b;
     for (int l = 2; l >= 0; l--) {
         Layer &Ly = L[l];
         // dW_l[out][in] = dZ^T[out][M] * IN^T[in][M]^T
         const bf16 *inT = l == 0 ? m->xt : m->ht[l - 1];
+        // few output tiles and a long k (the batch): split k across CTAs so
+        // that about one wave of SMs works on it, then sum the partials in
+        // split order (deterministic)
+        const int bn = Ly.in_p % 128 == 0 ? 128 : 64;
+        const int tiles = (Ly.out_p / 128) * (Ly.in_p / bn);
+        int splits = 1;
+        while (splits < kMaxSplits && tiles * splits * 2 <= 148 && Mp % (64 * splits * 2) == 0 &&
+               Mp / (splits * 2) >= 256)
+            splits *= 2;
         tc::Epi e = epi0(Ly.out_p, Ly.in_p, m->err);
-        e.out_f32 = Ly.gw;
+        e.out_f32 = splits > 1 ? m->splitbuf : Ly.gw;
         e.ld_f32 = Ly.in_p;
-        st = gemm(dzt, inT, Ly.out_p, Ly.in_p, Mp, e, s);
+        e.split_stride = (int64_t)Ly.out_p * Ly.in_p;
+        st = gemm(dzt, inT, Ly.out_p, Ly.in_p, Mp, e, s, splits);
         if (st != CUT_OK) return st;
-        mlpk::col_sum<<<(Ly.out_p + 255) / 256, 256, 0, s>>>(dz32, Ly.out_p, batch, Ly.out_p, Ly.gb);
+        if (splits > 1)
+            mlpk::sum_splits<<<grid_of(e.split_stride), 256, 0, s>>>(m->splitbuf, splits, e.split_stride, Ly.gw);
+        mlpk::col_sum<<<(Ly.out_p + 31) / 32, dim3(32, 8), 0, s>>>(dz32, Ly.out_p, batch, Ly.out_p, Ly.gb);
         if (l == 0) break;
         // dZ_{l-1} = (dZ_l W_l) * GELU'(Z_{l-1})
         Layer &Lp = L[l - 1];

@@ -26,7 +26,7 @@ namespace tc {
 
 constexpr int BM = 128;
 constexpr int BK = 64;          // one 128-byte swizzle row of BF16
-constexpr int STAGES = 4;
+constexpr int STAGES = 3;          // 97 KB of ring at BN = 128: two CTAs per SM
 constexpr int kThreads = 128;
 constexpr long long kSpinLimit = 1ll << 26;
 
@@ -41,8 +41,9 @@ struct Epi {
     const float *lin_J;         // optional linear skip: + sum_k J[col][k] x[row][k] (FP32)
     const float *lin_x;
     int lin_k;
-    float *out_f32;             // [M][ld_f32] or null
+    float *out_f32;             // [M][ld_f32] or null (split k: [splits][M][ld_f32])
     int ld_f32;
+    int64_t split_stride;       // split k (gridDim.z > 1): floats between the partial products
     __nv_bfloat16 *out_bf16;    // [M][ld_bf16] or null
     int ld_bf16;
     __nv_bfloat16 *out_t;       // transposed [N][ld_t] or null
@@ -132,7 +133,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-    const int KT = K / BK;
+    const int KT = K / BK;                 // K columns per split; split z starts at z K
+    const int kbase = blockIdx.z * K;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; s++) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
@@ -157,8 +159,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int s = kt % STAGES;
             if (kt >= STAGES && !mbar_wait(&empty[s], ((kt / STAGES) - 1) & 1)) { failed = 1; break; }
             mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
-            tma_load_2d(sA + s * A_BYTES, &tmA, &full[s], kt * BK, m0);
-            tma_load_2d(sB + s * B_BYTES, &tmB, &full[s], kt * BK, n0);
+            tma_load_2d(sA + s * A_BYTES, &tmA, &full[s], kbase + kt * BK, m0);
+            tma_load_2d(sB + s * B_BYTES, &tmB, &full[s], kbase + kt * BK, n0);
             issued = kt + 1;
         }
     } else if (warp == 1 && lane == 0) {
@@ -207,6 +209,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         float *ltile = stile + 32 * 33;        // linear-skip terms, same layout
         const int rbase = m0 + warp * 32;
         const int myrow = rbase + lane;
+        float *const out_f32 = ep.out_f32 ? ep.out_f32 + (int64_t)blockIdx.z * ep.split_stride : nullptr;
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += 32) {
             uint32_t r[32];
@@ -255,7 +258,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (ep.post_scale) v = v * psc + psh;
                 if (ep.lin_J) v += ltile[rr * 33 + lane];
                 if (ep.dgelu_z) v *= dgelu(ep.dgelu_z[(int64_t)row * ep.ldz + col]);
-                if (ep.out_f32) ep.out_f32[(int64_t)row * ep.ld_f32 + col] = v;
+                if (out_f32) out_f32[(int64_t)row * ep.ld_f32 + col] = v;
                 const float a = ep.act ? gelu(v) : v;
                 if (ep.out_bf16) ep.out_bf16[(int64_t)row * ep.ld_bf16 + col] = __float2bfloat16(a);
                 stile[rr * 33 + lane] = a;
