@@ -27,7 +27,7 @@ namespace tc {
 constexpr int BM = 128;
 constexpr int BK = 64;          // one 128-byte swizzle row of BF16
 constexpr int STAGES = 3;          // 97 KB of ring at BN = 128: two CTAs per SM
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;          // 8 warps: two per TMEM lane quarter share the epilogue
 constexpr long long kSpinLimit = 1ll << 26;
 
 struct Epi {
@@ -119,7 +119,7 @@ __device__ __forceinline__ float dgelu(float x) {
 }
 
 template <int BN>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
     gemm_bf16_tn(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int K, Epi ep) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte aligned tile ring
@@ -203,17 +203,21 @@ __global__ void __launch_bounds__(kThreads, 1)
         // stores are coalesced; the transposed output is written back from
         // the row layout, where it is coalesced too.
         static_assert(BN % 32 == 0, "epilogue works on 32-column slices");
-        static_assert(4 * 2 * 32 * 33 * 4 <= STAGES * (A_BYTES + B_BYTES), "staging fits in the ring");
+        static_assert(kThreads / 32 * 2 * 32 * 33 * 4 <= STAGES * (A_BYTES + B_BYTES), "staging fits in the ring");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         float *stile = reinterpret_cast<float *>(base) + warp * (2 * 32 * 33);
         float *ltile = stile + 32 * 33;        // linear-skip terms, same layout
-        const int rbase = m0 + warp * 32;
+        // warp w reads TMEM lanes 32 (w % 4) .. +31 (its rows); the warps
+        // sharing a lane quarter take alternate 32-column slices
+        constexpr int kQuarterWarps = kThreads / 128;
+        const int quarter = warp & 3, part = warp >> 2;
+        const int rbase = m0 + quarter * 32;
         const int myrow = rbase + lane;
         float *const out_f32 = ep.out_f32 ? ep.out_f32 + (int64_t)blockIdx.z * ep.split_stride : nullptr;
 #pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 32) {
+        for (int c0 = part * 32; c0 < BN; c0 += 32 * kQuarterWarps) {
             uint32_t r[32];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
                 "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
@@ -227,22 +231,26 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int i = 0; i < 32; i++) stile[lane * 33 + i] = __uint_as_float(r[i]);
             if (ep.lin_J) {
-                // skip terms sum_k J[col][k] x[row][k] in the row layout (J broadcast)
-                float l[32];
+                // skip terms sum_k J[col][k] x[row][k] in the row layout (J
+                // broadcast), 16 columns per pass to bound the registers
+#pragma unroll 1
+                for (int h = 0; h < 32; h += 16) {
+                    float l[16];
 #pragma unroll
-                for (int i = 0; i < 32; i++) l[i] = 0.0f;
-                if (myrow < ep.M) {
-                    for (int k = 0; k < ep.lin_k; k++) {
-                        const float xv = ep.lin_x[(int64_t)myrow * ep.lin_k + k];
+                    for (int i = 0; i < 16; i++) l[i] = 0.0f;
+                    if (myrow < ep.M) {
+                        for (int k = 0; k < ep.lin_k; k++) {
+                            const float xv = ep.lin_x[(int64_t)myrow * ep.lin_k + k];
 #pragma unroll
-                        for (int i = 0; i < 32; i++) {
-                            const int col = n0 + c0 + i;
-                            if (col < ep.N) l[i] = fmaf(ep.lin_J[(int64_t)col * ep.lin_k + k], xv, l[i]);
+                            for (int i = 0; i < 16; i++) {
+                                const int col = n0 + c0 + h + i;
+                                if (col < ep.N) l[i] = fmaf(ep.lin_J[(int64_t)col * ep.lin_k + k], xv, l[i]);
+                            }
                         }
                     }
-                }
 #pragma unroll
-                for (int i = 0; i < 32; i++) ltile[lane * 33 + i] = l[i];
+                    for (int i = 0; i < 16; i++) ltile[lane * 33 + h + i] = l[i];
+                }
             }
             __syncwarp();
             const int col = n0 + c0 + lane;
@@ -250,14 +258,21 @@ __global__ void __launch_bounds__(kThreads, 1)
             const float bias = (ep.bias && colok) ? ep.bias[col] : 0.0f;
             const float psc = (ep.post_scale && colok) ? ep.post_scale[col] : 1.0f;
             const float psh = (ep.post_scale && colok) ? ep.post_shift[col] : 0.0f;
-#pragma unroll 4
+            // every row's GELU-derivative input in flight at once
+            float zr[32];
+            if (ep.dgelu_z) {
+#pragma unroll
+                for (int rr = 0; rr < 32; rr++)
+                    zr[rr] = (colok && rbase + rr < ep.M) ? ep.dgelu_z[(int64_t)(rbase + rr) * ep.ldz + col] : 0.0f;
+            }
+#pragma unroll
             for (int rr = 0; rr < 32; rr++) {
                 const int row = rbase + rr;
                 if (!colok || row >= ep.M) continue;
                 float v = stile[rr * 33 + lane] * ep.alpha + bias;
                 if (ep.post_scale) v = v * psc + psh;
                 if (ep.lin_J) v += ltile[rr * 33 + lane];
-                if (ep.dgelu_z) v *= dgelu(ep.dgelu_z[(int64_t)row * ep.ldz + col]);
+                if (ep.dgelu_z) v *= dgelu(zr[rr]);
                 if (out_f32) out_f32[(int64_t)row * ep.ld_f32 + col] = v;
                 const float a = ep.act ? gelu(v) : v;
                 if (ep.out_bf16) ep.out_bf16[(int64_t)row * ep.ld_bf16 + col] = __float2bfloat16(a);
