@@ -87,3 +87,58 @@ def test_batched_rejects_bad_arguments():
     G = graph_for("mol4", ALG_FERMION, 4, labels)
     with pytest.raises(cg.CutError):
         G.flow_batched(torch.tensor(H), torch.tensor(X), precision="fp64", method="rk4", s0=0.0, s1=0.1, ds=0.01, tile=3)
+
+
+def test_batched_refills_slots_and_matches_single_instance_flows():
+    """More instances than resident slots (1500 > 148 CTAs x 8 slots): slots
+    that finish are refilled from the queue inside the kernel.  Every
+    instance, first wave or refilled, equals its own single-instance FP64
+    flow; the FP32-record batch stays within its stated error."""
+    import torch
+    w = workload("molecular_8so")
+    B = 1500
+    H = batched_parameters(w.labels, 8, B, seed=35)
+    X = np.stack([np.stack(w.observables)] * B)
+    G = graph_for("mol8", w.alg, w.nmodes, w.labels)
+    kw = dict(method="rk4", s0=0.0, s1=0.02, ds=0.01, tile=8)
+    Hs, Xs, steps, status = G.flow_batched(torch.tensor(H), torch.tensor(X), precision="fp64", **kw)
+    assert np.all(status.cpu().numpy() == 0) and np.all(steps.cpu().numpy() == 2)
+    for b in (0, 1, 1035, 1183, 1184, 1499):
+        hs, xs, st, _ = G.flow(H[b], list(X[b]), method="rk4", s0=0.0, s1=0.02, ds=0.01)
+        assert st["steps"] == 2
+        assert_close(np64(Hs[b]), np64(hs), what=f"h[{b}]")
+        assert_close(np64(Xs[b, 1]), np64(xs[1]), what=f"D[{b}]")
+    H32, X32, _, status32 = G.flow_batched(torch.tensor(H), torch.tensor(X), precision="fp32", **kw)
+    assert np.all(status32.cpu().numpy() == 0)
+    err = np.max(np.abs(np64(H32) - np64(Hs)), axis=1) / np.max(np.abs(np64(Hs)), axis=1)
+    assert err.max() < 1e-5, err.max()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batched_single_instance(precision):
+    import torch
+    labels, H, X = _batch(4, 1, seed=36)
+    G = graph_for("mol4", ALG_FERMION, 4, labels)
+    tol = dict(rtol=1e-10, atol=1e-12) if precision == "fp64" else dict(rtol=1e-6, atol=1e-9)
+    Hs, Xs, steps, status = G.flow_batched(torch.tensor(H), torch.tensor(X), precision=precision, method="dp45",
+                                           s0=0.0, s1=1.0, ds=1e-2, **tol)
+    assert int(status[0]) == 0
+    hs, xs, st, _ = G.flow(H[0], list(X[0]), method="dp45", s0=0.0, s1=1.0, ds=1e-2, rtol=1e-10, atol=1e-12)
+    assert_close(np64(Hs[0]), np64(hs), rtol=1e-8 if precision == "fp64" else 1e-4, what="h")
+
+
+def test_batched_diagonal_only_registry_is_stationary():
+    """No generator and no commutator records: every instance keeps its
+    coefficients bit for bit (the empty stages write exact zeros)."""
+    import torch
+    labels = np.array([l for l in fermion_registry(4) if oracle.is_diagonal(ALG_FERMION, l)], dtype=np.uint64)
+    G = graph_for("diag4", ALG_FERMION, 4, labels)
+    rng = np.random.default_rng(37)
+    H = rng.normal(size=(9, len(labels)))
+    X = rng.normal(size=(9, 1, len(labels)))
+    for precision in ("fp64", "fp32"):
+        Hs, Xs, steps, status = G.flow_batched(torch.tensor(H), torch.tensor(X), precision=precision, method="rk4",
+                                               s0=0.0, s1=0.1, ds=0.05)
+        assert np.all(status.cpu().numpy() == 0)
+        np.testing.assert_array_equal(np64(Hs), H)
+        np.testing.assert_array_equal(np64(Xs), X)
