@@ -137,6 +137,9 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int kbase = blockIdx.z * K;
 
     if (threadIdx.x == 0) {
+        // start fetching both tensor maps while the barriers and TMEM are set up
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
         for (int s = 0; s < STAGES; s++) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
         mbar_init(&done, 1);
         failed = 0;
