@@ -69,6 +69,38 @@ __device__ __forceinline__ double flip_if(double v, uint32_t neg) {
     return __longlong_as_double(__double_as_longlong(v) ^ ((long long)neg << 63));
 }
 
+// Operand values of one (index, slot) pair are stored together,
+// [index][slot][P] with P >= NOPS: FP32 with three operands is padded to
+// four so that one 16-byte shared-memory load fetches them (one wavefront
+// per lane group, no bank conflicts inside a group).
+template <typename T, int NOPS>
+struct OpPad {
+    static constexpr int P = (sizeof(T) == 4 && NOPS == 3) ? 4 : NOPS;
+};
+
+template <int NOPS, int P>
+__device__ __forceinline__ void load_ops(const float *p, float (&v)[NOPS]) {
+    if constexpr (P == 4) {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        v[0] = t.x;
+        if constexpr (NOPS > 1) v[1] = t.y;
+        if constexpr (NOPS > 2) v[2] = t.z;
+        if constexpr (NOPS > 3) v[3] = t.w;
+    } else if constexpr (P == 2) {
+        const float2 t = *reinterpret_cast<const float2 *>(p);
+        v[0] = t.x;
+        if constexpr (NOPS > 1) v[1] = t.y;
+    } else {
+#pragma unroll
+        for (int o = 0; o < NOPS; o++) v[o] = p[o];
+    }
+}
+template <int NOPS, int P>
+__device__ __forceinline__ void load_ops(const double *p, double (&v)[NOPS]) {
+#pragma unroll
+    for (int o = 0; o < NOPS; o++) v[o] = p[o];
+}
+
 // first row index in [0, rows] whose offset is >= target (rps[rows] >= target)
 __device__ __forceinline__ int64_t lower_row(const uint32_t *rps, int64_t rows, uint32_t target) {
     int64_t lo = 0, hi = rows;
@@ -100,6 +132,7 @@ __device__ __forceinline__ void stage_stream(const uint32_t *__restrict__ rps, i
     constexpr int CH = M * TILE;                  // records per group per chunk
     constexpr int SB = TILE < 8 ? TILE : 8;       // records gathered before they are summed
     constexpr int NA = GEN ? 1 : NOPS;
+    constexpr int P = OpPad<T, NOPS>::P;
     const int lane = threadIdx.x & 31, b = lane % TILE, g = lane / TILE;
     const int gi = (threadIdx.x >> 5) * G + g;
     const unsigned gmask = TILE == 32 ? 0xffffffffu : (((1u << TILE) - 1u) << (g * TILE));
@@ -116,7 +149,8 @@ __device__ __forceinline__ void stage_stream(const uint32_t *__restrict__ rps, i
     auto flush = [&]() {
 #pragma unroll
         for (int o = 0; o < NA; o++) {
-            out[((int64_t)o * (GEN ? 0 : n) + cur) * TILE + b] = signs ? acc[o] * mag : acc[o];
+            // GEN: xi[row][slot]; else slopes [row][slot][P]
+            out[GEN ? cur * TILE + b : (cur * TILE + b) * P + o] = signs ? acc[o] * mag : acc[o];
             acc[o] = T(0);
         }
         cur++;
@@ -148,13 +182,12 @@ __device__ __forceinline__ void stage_stream(const uint32_t *__restrict__ rps, i
                     q.y = __shfl_sync(gmask, v[0].y, s0 + s, TILE);
                     const int64_t i = (int64_t)(q.x & kIdx) * TILE + b, j = (int64_t)q.y * TILE + b;
                     const uint32_t code = q.x >> 24;
-                    const T src = GEN ? U[i] : xis[i];
+                    const T src = GEN ? U[i * P] : xis[i];
                     cf[s] = signs ? flip_if(src, (negmask >> (code & 31)) & 1u) : ws[code] * src;
-                    if (GEN) {
-                        uv[s][0] = U[j];
+                    if constexpr (GEN) {
+                        uv[s][0] = U[j * P];
                     } else {
-#pragma unroll
-                        for (int o = 0; o < NA; o++) uv[s][o] = U[(int64_t)o * n * TILE + j];
+                        load_ops<NOPS, P>(U + j * P, uv[s]);
                     }
                 }
                 // sum them in record order, closing rows at their ends
@@ -180,7 +213,7 @@ __device__ __forceinline__ void stage_stream(const uint32_t *__restrict__ rps, i
     while (cur < rb) flush();   // the last row and any empty rows after it
 }
 
-// RHS of all TILE slots: U (smem, [nops][n][TILE]) -> K (global, [nops][n][TILE])
+// RHS of all TILE slots: U (smem, [n][TILE][P]) -> K (global, [n][TILE][P])
 template <typename T, int TILE, int NOPS>
 __device__ void rhs_tile(const Args &a, const uint32_t *__restrict__ rps0, const uint32_t *__restrict__ rps1,
                          const T *__restrict__ U, T *__restrict__ xis, const T *__restrict__ ws,
@@ -190,13 +223,22 @@ __device__ void rhs_tile(const Args &a, const uint32_t *__restrict__ rps0, const
     stage_stream<T, TILE, NOPS, false>(rps1, a.n, a.rec1, U, xis, ws, a.n, K, a.signs, a.negmask, T(a.mag));
 }
 
+// Every (row, slot, operand) element of the RK arrays once: a thread keeps
+// one slot (kThreads is a multiple of TILE) and walks its operands; the
+// padding entries (o >= NOPS) are never touched.
+#define FOR_ELEMENTS(e)                                                          \
+    for (int64_t kb_ = threadIdx.x; kb_ < n * TILE; kb_ += kThreads)             \
+        _Pragma("unroll") for (int o_ = 0; o_ < NOPS; o_++)                      \
+            if (const int64_t e = kb_ * P + o_; true)
+
 template <typename T, int TILE, int NOPS>
 __global__ void __launch_bounds__(kThreads, 1) flow_batched_kernel(Args a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int64_t n = a.n, L = (int64_t)NOPS * n;
+    constexpr int P = OpPad<T, NOPS>::P;
+    const int64_t n = a.n, LP = (int64_t)P * n * TILE;   // elements of one RK array
     double *red = reinterpret_cast<double *>(smem);     // [kThreads]
-    T *U = reinterpret_cast<T *>(red + kThreads);       // [NOPS][n][TILE]
-    T *xis = U + L * TILE;                              // [n_g][TILE]
+    T *U = reinterpret_cast<T *>(red + kThreads);       // [n][TILE][P]
+    T *xis = U + LP;                                    // [n_g][TILE]
     T *ws = xis + a.n_g * TILE;                         // [256]
     uint32_t *rps0 = reinterpret_cast<uint32_t *>(ws + 256);   // [n_g + 1] record offsets
     uint32_t *rps1 = rps0 + a.n_g + 1;                         // [n + 1]
@@ -211,9 +253,9 @@ __global__ void __launch_bounds__(kThreads, 1) flow_batched_kernel(Args a) {
     for (int64_t r = threadIdx.x; r <= a.n; r += kThreads) rps1[r] = (uint32_t)a.rp1[r];
     // workspace of this CTA: Y, Y5 (double) then K[7] (T), all [NOPS][n][TILE]
     double *Y = reinterpret_cast<double *>(reinterpret_cast<char *>(a.ws) + (int64_t)blockIdx.x * a.ws_stride);
-    double *Y5 = Y + L * TILE;
-    T *Kb = reinterpret_cast<T *>(Y5 + L * TILE);
-    auto Kst = [&](int s) { return Kb + (int64_t)s * L * TILE; };
+    double *Y5 = Y + LP;
+    T *Kb = reinterpret_cast<T *>(Y5 + LP);
+    auto Kst = [&](int s) { return Kb + (int64_t)s * LP; };
     T *Yf = Kst(8);   // FP32 path: the state rounded to FP32 (stage inputs are formed in FP32)
     if (threadIdx.x < TILE) { inst[threadIdx.x] = -1; status[threadIdx.x] = 0; }
     if (threadIdx.x == 0) cta_attempts = 0;
@@ -252,10 +294,10 @@ __global__ void __launch_bounds__(kThreads, 1) flow_batched_kernel(Args a) {
             any_new = nw;
         }
         // load the initial state of new instances
-        for (int64_t e = threadIdx.x; e < L * TILE; e += kThreads) {
-            const int b = (int)(e % TILE);
+        FOR_ELEMENTS(e) {
+            const int b = (int)(kb_ % TILE);
             if (!need_k1[b]) continue;
-            const int64_t row = e / TILE, o = row / n, k = row % n;
+            const int64_t o = o_, k = kb_ / TILE;
             const int64_t i = inst[b];
             const double y0 = o == 0 ? a.H[i * n + k] : a.X[(i * (NOPS - 1) + (o - 1)) * n + k];
             Y[e] = y0;
@@ -280,7 +322,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_batched_kernel(Args a) {
 #pragma unroll
             for (int j = 0; j < 7; j++) af[j] = (float)tb.a[st][j];
             const bool y5_stage = tb.adaptive && st == S - 1;
-            for (int64_t e = threadIdx.x; e < L * TILE; e += kThreads) {
+            FOR_ELEMENTS(e) {
                 double u;
                 if (sizeof(T) == 4) {
                     float inc = 0.0f;
@@ -305,8 +347,9 @@ __global__ void __launch_bounds__(kThreads, 1) flow_batched_kernel(Args a) {
             rhs_tile<T, TILE, NOPS>(a, rps0, rps1, U, xis, ws, fsal_first ? Kst(S) : Kst(st));
             __syncthreads();
             if (fsal_first) {   // only the new slots take the fresh K1
-                for (int64_t e = threadIdx.x; e < L * TILE; e += kThreads)
+                FOR_ELEMENTS(e) {
                     if (need_k1[mb]) Kst(0)[e] = Kst(S)[e];
+                }
                 __syncthreads();
             }
         }
@@ -314,7 +357,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_batched_kernel(Args a) {
         {
             double m = 0.0;
             bool bad = false;
-            for (int64_t e = threadIdx.x; e < L * TILE; e += kThreads) {
+            FOR_ELEMENTS(e) {
                 const double ds = ds_[mb];
                 if (tb.adaptive) {
                     double r;
@@ -403,15 +446,15 @@ __global__ void __launch_bounds__(kThreads, 1) flow_batched_kernel(Args a) {
         }
         __syncthreads();
         // ---- accept: Y <- Y5 (and K1 <- K7 under FSAL); write back finished slots
-        for (int64_t e = threadIdx.x; e < L * TILE; e += kThreads) {
-            const int b = (int)(e % TILE);
+        FOR_ELEMENTS(e) {
+            const int b = (int)(kb_ % TILE);
             if (acc_flag[b] & 1) {
                 Y[e] = Y5[e];
                 if (sizeof(T) == 4) Yf[e] = tb.adaptive ? U[e] : T(Y5[e]);
                 if (tb.adaptive) Kst(0)[e] = Kst(S - 1)[e];
             }
             if (acc_flag[b] & 2) {
-                const int64_t row = e / TILE, o = row / n, k = row % n;
+                const int64_t o = o_, k = kb_ / TILE;
                 const int64_t i = inst[b];
                 if (o == 0) a.H[i * n + k] = Y[e];
                 else a.X[(i * (NOPS - 1) + (o - 1)) * n + k] = Y[e];
@@ -422,6 +465,8 @@ __global__ void __launch_bounds__(kThreads, 1) flow_batched_kernel(Args a) {
         __syncthreads();
     }
 }
+
+#undef FOR_ELEMENTS
 
 }  // namespace kb
 
@@ -441,13 +486,13 @@ struct BatchedGraphView {
 
 template <typename T, int TILE, int NOPS>
 static size_t smem_bytes(const BatchedGraphView &v) {
-    return sizeof(T) * TILE * ((size_t)NOPS * v.n + v.n_g) + 256 * sizeof(T) + kb::kThreads * sizeof(double) +
-           4 * ((size_t)v.n + v.n_g + 2);
+    return sizeof(T) * TILE * ((size_t)kb::OpPad<T, NOPS>::P * v.n + v.n_g) + 256 * sizeof(T) +
+           kb::kThreads * sizeof(double) + 4 * ((size_t)v.n + v.n_g + 2);
 }
 
 template <typename T, int TILE, int NOPS>
 static size_t ws_bytes(const BatchedGraphView &v) {
-    size_t L = (size_t)NOPS * v.n * TILE;
+    size_t L = (size_t)kb::OpPad<T, NOPS>::P * v.n * TILE;
     size_t b = L * (2 * sizeof(double) + 9 * sizeof(T));   // Y, Y5, K[8], FP32 state copy
     return (b + 255) & ~size_t(255);
 }
@@ -522,7 +567,8 @@ static LaunchFn pick_any(bool fp32, int nops, int tile) {
 
 static size_t smem_for(bool fp32, int nops, int tile, const BatchedGraphView &v) {
     size_t e = fp32 ? 4 : 8;
-    return e * tile * ((size_t)nops * v.n + v.n_g) + 256 * e + kb::kThreads * 8 + 4 * ((size_t)v.n + v.n_g + 2);  // matches smem_bytes
+    const size_t P = (fp32 && nops == 3) ? 4 : (size_t)nops;   // kb::OpPad
+    return e * tile * (P * v.n + v.n_g) + 256 * e + kb::kThreads * 8 + 4 * ((size_t)v.n + v.n_g + 2);  // matches smem_bytes
 }
 
 static kb::Tableau make_tableau(int method) {
