@@ -190,17 +190,26 @@ __device__ __forceinline__ void stage_stream(const uint32_t *__restrict__ rps, i
                         load_ops<NOPS, P>(U + j * P, uv[s]);
                     }
                 }
-                // sum them in record order, closing rows at their ends
+                // sum them in record order, closing rows at their ends; most
+                // slices lie inside one row and take the branch-free path
+                const uint32_t t0 = c + m * TILE + s0;
+                if (t0 + SB - 1 < nb && t0 + SB - 1 < pe) {
 #pragma unroll
-                for (int s = 0; s < SB; s++) {
-                    const uint32_t t = c + m * TILE + s0 + s;
-                    if (t < pe) {
-                        while (t >= nb) {
-                            flush();
-                            nb = rps[cur + 1];
-                        }
+                    for (int s = 0; s < SB; s++)
 #pragma unroll
                         for (int o = 0; o < NA; o++) acc[o] += cf[s] * uv[s][o];
+                } else {
+#pragma unroll
+                    for (int s = 0; s < SB; s++) {
+                        const uint32_t t = t0 + s;
+                        if (t < pe) {
+                            while (t >= nb) {
+                                flush();
+                                nb = rps[cur + 1];
+                            }
+#pragma unroll
+                            for (int o = 0; o < NA; o++) acc[o] += cf[s] * uv[s][o];
+                        }
                     }
                 }
             }
