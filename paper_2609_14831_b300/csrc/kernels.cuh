@@ -190,10 +190,20 @@ __device__ __forceinline__ void df_madd(float ch, float cl, float xh, float xl, 
 
 // The 32-byte operand pair block of one input index in one 256-bit load
 // (sm_100 and later): one L1 request per gathered record instead of two.
+// The operand blocks are spread over the whole registry and rarely reused
+// from L1, so they bypass L1 allocation (no_allocate), which leaves L1 to
+// the generator pairs; those are reused by neighbouring records (rows are
+// sorted by generator index) and kept with evict_last.  Measured on the
+// 3.4e8-record stress graph: 1.77 -> 1.64 ms per launch.
 __device__ __forceinline__ void ld_pairs32(const float4 *p, float4 &a, float4 &b) {
-    asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+    asm volatile("ld.global.nc.L1::no_allocate.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
                  : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
                  : "l"(p));
+}
+__device__ __forceinline__ float2 ld_xi_pair(const float2 *p) {
+    float2 v;
+    asm volatile("ld.global.nc.L1::evict_last.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    return v;
 }
 
 template <int NOPS, int LANES>
@@ -230,7 +240,7 @@ __global__ void __launch_bounds__(kBlock) comm_stage_df(const uint64_t *__restri
                 float4 a[U], b[U];
 #pragma unroll
                 for (int u = 0; u < U; u++) {
-                    cf[u] = xi2[q[u].x & kIdx];
+                    cf[u] = ld_xi_pair(xi2 + (q[u].x & kIdx));
                     ld_pairs32(X2 + 2 * (int64_t)q[u].y, a[u], b[u]);
                 }
 #pragma unroll
@@ -245,7 +255,7 @@ __global__ void __launch_bounds__(kBlock) comm_stage_df(const uint64_t *__restri
             }
             for (; p < e; p += LANES) {
                 const uint2 q = __ldcs(rec + p);
-                float2 cf = xi2[q.x & kIdx];
+                float2 cf = ld_xi_pair(xi2 + (q.x & kIdx));
                 const unsigned int sb = (unsigned int)(sg[q.x >> 24] >> 32);
                 cf.x = __uint_as_float(__float_as_uint(cf.x) ^ sb);
                 cf.y = __uint_as_float(__float_as_uint(cf.y) ^ sb);
