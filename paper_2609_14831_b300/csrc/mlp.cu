@@ -219,7 +219,7 @@ static cut_status make_map(CUtensorMap *map, const void *ptr, int rows, int cols
 // C[M][N] = A[M][K] B[N][K]^T, M % 128 == 0, N % 64 == 0, K % (64 splits) == 0.
 // splits > 1: split k, partial products to ep.out_f32 + z ep.split_stride.
 static cut_status gemm(const bf16 *A, const bf16 *B, int M, int N, int K, tc::Epi ep, cudaStream_t s,
-                       int splits = 1) {
+                       int splits = 1, bool gelu = false) {
     if (M % 128 || N % 64 || splits < 1 || K % (64 * splits)) return set_error(CUT_ERR_INVALID_ARG, "gemm: shape not padded");
     CUtensorMap ma, mb;
     const int bn = (N % 128 == 0) ? 128 : 64;
@@ -228,14 +228,20 @@ static cut_status gemm(const bf16 *A, const bf16 *B, int M, int N, int K, tc::Ep
     st = make_map(&mb, B, N, K, bn);
     if (st != CUT_OK) return st;
     dim3 grid(M / 128, N / bn, splits);
+    const int act = ep.dgelu_z ? tc::kGeluGrad : (gelu ? tc::kGelu : tc::kLinear);
+    auto launch = [&](auto kern, size_t sm) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        kern<<<grid, tc::kThreads, sm, s>>>(ma, mb, K / splits, ep);
+    };
+    const size_t sm128 = tc::gemm_smem_bytes<128>(), sm64 = tc::gemm_smem_bytes<64>();
     if (bn == 128) {
-        auto k = tc::gemm_bf16_tn<128>;
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::gemm_smem_bytes<128>());
-        k<<<grid, tc::kThreads, tc::gemm_smem_bytes<128>(), s>>>(ma, mb, K / splits, ep);
+        if (act == tc::kGelu) launch(tc::gemm_bf16_tn<128, tc::kGelu>, sm128);
+        else if (act == tc::kGeluGrad) launch(tc::gemm_bf16_tn<128, tc::kGeluGrad>, sm128);
+        else launch(tc::gemm_bf16_tn<128, tc::kLinear>, sm128);
     } else {
-        auto k = tc::gemm_bf16_tn<64>;
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::gemm_smem_bytes<64>());
-        k<<<grid, tc::kThreads, tc::gemm_smem_bytes<64>(), s>>>(ma, mb, K / splits, ep);
+        if (act == tc::kGelu) launch(tc::gemm_bf16_tn<64, tc::kGelu>, sm64);
+        else if (act == tc::kGeluGrad) launch(tc::gemm_bf16_tn<64, tc::kGeluGrad>, sm64);
+        else launch(tc::gemm_bf16_tn<64, tc::kLinear>, sm64);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(CUT_ERR_CUDA, std::string("gemm launch: ") + cudaGetErrorString(e));
@@ -361,7 +367,6 @@ static cut_status forward(cut_mlp *m, int batch, const float *x, cudaStream_t s,
         e.out_f32 = m->z[l];
         e.ld_f32 = Ly.out_p;
         if (l < 2) {
-            e.act = 1;
             e.out_bf16 = m->hb[l];
             e.ld_bf16 = Ly.out_p;
             e.out_t = m->ht[l];
@@ -378,7 +383,7 @@ static cut_status forward(cut_mlp *m, int batch, const float *x, cudaStream_t s,
             e.out_f32 = y_out;
             e.ld_f32 = m->n_out;
         }
-        st = gemm(in, Ly.wb, Mp, Ly.out_p, Ly.in_p, e, s);
+        st = gemm(in, Ly.wb, Mp, Ly.out_p, Ly.in_p, e, s, 1, l < 2);   // GELU on the hidden layers
         if (st != CUT_OK) return st;
         if (l < 2) in = m->hb[l];
     }

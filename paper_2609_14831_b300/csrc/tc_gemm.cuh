@@ -32,9 +32,8 @@ constexpr long long kSpinLimit = 1ll << 26;
 
 struct Epi {
     const float *bias;          // [N] or null
-    const float *dgelu_z;       // backward: multiply by GELU'(z), z row-major [M][ldz]
+    const float *dgelu_z;       // ACT == kGeluGrad: multiply by GELU'(z), z row-major [M][ldz]
     int ldz;
-    int act;                    // 1 = GELU on the output
     float alpha;                // scale of the product
     const float *post_scale;    // optional per-column affine after bias: v * scale + shift
     const float *post_shift;
@@ -118,7 +117,12 @@ __device__ __forceinline__ float dgelu(float x) {
     return cdf + x * pdf;
 }
 
-template <int BN>
+// Epilogue activation, fixed at compile time so that the row loop carries
+// only the arithmetic it needs (a runtime choice let the compiler evaluate
+// the error function on every element).
+enum EpiAct { kLinear = 0, kGelu = 1, kGeluGrad = 2 };
+
+template <int BN, int ACT>
 __global__ void __launch_bounds__(kThreads, 2)
     gemm_bf16_tn(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int K, Epi ep) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -261,29 +265,37 @@ __global__ void __launch_bounds__(kThreads, 2)
             const float bias = (ep.bias && colok) ? ep.bias[col] : 0.0f;
             const float psc = (ep.post_scale && colok) ? ep.post_scale[col] : 1.0f;
             const float psh = (ep.post_scale && colok) ? ep.post_shift[col] : 0.0f;
-            // every row's GELU-derivative input in flight at once
-            float zr[32];
-            if (ep.dgelu_z) {
+            // every row's GELU-derivative input in flight at once, parked in
+            // the second tile (the skip term and the GELU derivative are
+            // never used by the same GEMM)
+            if constexpr (ACT == kGeluGrad) {
+                float zr[32];
 #pragma unroll
                 for (int rr = 0; rr < 32; rr++)
                     zr[rr] = (colok && rbase + rr < ep.M) ? ep.dgelu_z[(int64_t)(rbase + rr) * ep.ldz + col] : 0.0f;
-            }
 #pragma unroll
+                for (int rr = 0; rr < 32; rr++) ltile[rr * 33 + lane] = zr[rr];
+            }
+            // partly unrolled: a fully unrolled row loop with the GELU (or
+            // its derivative) overflows the instruction cache
+            constexpr int kRowUnroll = ACT == kLinear ? 8 : 2;
+#pragma unroll(kRowUnroll)
             for (int rr = 0; rr < 32; rr++) {
                 const int row = rbase + rr;
                 if (!colok || row >= ep.M) continue;
                 float v = stile[rr * 33 + lane] * ep.alpha + bias;
                 if (ep.post_scale) v = v * psc + psh;
                 if (ep.lin_J) v += ltile[rr * 33 + lane];
-                if (ep.dgelu_z) v *= dgelu(zr[rr]);
+                if constexpr (ACT == kGeluGrad) v *= dgelu(ltile[rr * 33 + lane]);
                 if (out_f32) out_f32[(int64_t)row * ep.ld_f32 + col] = v;
-                const float a = ep.act ? gelu(v) : v;
+                float a = v;
+                if constexpr (ACT == kGelu) a = gelu(v);
                 if (ep.out_bf16) ep.out_bf16[(int64_t)row * ep.ld_bf16 + col] = __float2bfloat16(a);
                 stile[rr * 33 + lane] = a;
             }
             __syncwarp();
             if (ep.out_t && myrow < ep.M) {
-#pragma unroll 4
+#pragma unroll 8
                 for (int i = 0; i < 32; i++) {
                     const int cc = n0 + c0 + i;
                     if (cc < ep.N) ep.out_t[(int64_t)cc * ep.ld_t + myrow] = __float2bfloat16(stile[lane * 33 + i]);
