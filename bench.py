@@ -585,7 +585,7 @@ def main():
                 "unit": "TFLOP/s", "frac": fp64_flop / (comm_ms * 1e-3) / 1e12 / fp64_peak, "traffic": traffic,
                 "peak_kind": "nominal B300 FP64 rate (profiling recipe table); the FP64 pipe is the "
                              "measured bound (ncu: sm__pipe_fp64_cycles_active > 90%)",
-                "kernel": f"comm_stage<{nops}> (FP64), one launch per operand block",
+                "kernel": f"comm_stage_x4<{nops}> (FP64, operands of one index in one 32-byte block)",
                 "launch_ms": comm_ms, "algorithmic_flop": fp64_flop,
                 "hbm_view": {"achieved": comm_bytes / (comm_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
                              "frac": comm_bytes / (comm_ms * 1e-3) / 1e9 / hbm_peak, "peak_kind": peak_kind,
@@ -661,7 +661,9 @@ def main():
                        "build_s": round(tbuild, 1), "build_peak_over_stored":
                            round(bstats["peak_rss_bytes"] / max(1, bstats["bytes_stored"]), 3),
                        "parallelism": f"{world} independent instance(s)"},
-            "gpu_launches": int(args.steps * 4 * (1 + (nops + 3) // 4) + args.steps * 4),
+            # per RK4 step: 4 right-hand sides (generator stage, then per block of
+            # four operands one pack and one commutator launch) and 4 combinations
+            "gpu_launches": int(args.steps * 4 * (1 + 2 * ((nops + 3) // 4)) + args.steps * 4),
             "roofline": roofline,
             "df64": df,
             "batched": batched,

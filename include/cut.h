@@ -145,7 +145,10 @@ cut_status cut_graph_records(const cut_graph *g, int stage, int64_t *row_ptr, in
 /* dh = P[eta(h), H], dx_o = P[eta(h), X_o] for o < n_obs.
  * device in : h[n], x[n_obs][n] (NULL if n_obs == 0)
  * device out: dh[n], dx[n_obs][n], xi_out[n_g] (optional, NULL = not kept)
- * Runs asynchronously on `stream`.  Errors: INVALID_ARG, CUDA. */
+ * Runs asynchronously on `stream`; takes its scratch (the packed operand
+ * blocks, n x 32 bytes, and the generator when xi_out is NULL) from the
+ * stream-ordered allocator and returns it on the same stream.
+ * Errors: INVALID_ARG, CUDA. */
 cut_status cut_rhs(const cut_graph *g, const double *h, int n_obs, const double *x, double *dh,
                    double *dx, double *xi_out, cut_stream_t stream);
 
@@ -205,13 +208,16 @@ cut_status cut_rhs_jvp(const cut_graph *g, const double *h, int n_obs, const dou
 /* Allocation-free variant of cut_rhs.  The paper has no counterpart; it
  * exists for callers that may not allocate device memory while they run
  * (for example a real-time or serving loop whose memory is fixed up front,
- * or code whose allocator is owned by someone else), since cut_rhs takes a
- * temporary generator buffer from the stream-ordered allocator when xi_out
- * is NULL.  Here that buffer is a fixed array of CUT_RHS_NOALLOC_MAX_NG
+ * or code whose allocator is owned by someone else), since cut_rhs takes
+ * temporary buffers from the stream-ordered allocator (the generator when
+ * xi_out is NULL, and a 32-byte block per coordinate into which the
+ * operands are packed).  Here the generator buffer is a fixed array of
+ * CUT_RHS_NOALLOC_MAX_NG
  * doubles (8 MiB) compiled into the library: every GPU that loads the
  * library holds it until the process exits.
  *   - Same inputs, outputs and results as cut_rhs with xi_out = NULL, always
- *     in FP64 arithmetic.
+ *     in FP64 arithmetic; the operands are gathered one by one instead of
+ *     from packed blocks, with the same sums in the same order (same bits).
  *   - Graphs with more than CUT_RHS_NOALLOC_MAX_NG generator coordinates are
  *     rejected with CUT_ERR_INVALID_ARG before anything is queued.
  *   - Makes no cudaMalloc, cudaFree or other allocating call.

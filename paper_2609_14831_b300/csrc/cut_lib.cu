@@ -143,11 +143,45 @@ static void comm_launch(const DevCSR &c, const k::Weights &w, const double *xi, 
         k::comm_stage<M, false, L><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, xi, ops, c.rows, done);
 }
 
+template <int M, int L>
+static void comm_launch_x4(const DevCSR &c, const k::Weights &w, const double *xi, const k::Ops<M> &ops,
+                           const double *X4, cudaStream_t s, const int *done) {
+    const int grid = grid_for_groups(c.rows, L);
+    if (w.uniform)
+        k::comm_stage_x4<M, true, L><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, xi, X4, ops, c.rows, done);
+    else
+        k::comm_stage_x4<M, false, L><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, xi, X4, ops, c.rows, done);
+}
+
+// X4: optional scratch of n x 32 bytes on a 32-byte boundary.  With it the
+// operands go in blocks of four through pack_x4 + comm_stage_x4 (one gather
+// per record); without it through comm_stage (one gather per operand).
+// Both give the same bits.
 static void launch_comm(const cut_graph *g, const double *xi, int nops, const double *const *xs,
-                        double *const *dxs, cudaStream_t s, const int *done, int stage = 1) {
+                        double *const *dxs, cudaStream_t s, const int *done, int stage = 1,
+                        double *X4 = nullptr) {
     const DevCSR &c = g->st[stage];
     const k::Weights w = weights_of(g);
     const int lanes = comm_lanes(c.rows);
+    if (X4) {
+        const int64_t n = g->host.n();
+        for (int o0 = 0; o0 < nops; o0 += 4) {
+            const int m = std::min(4, nops - o0);
+            switch (m) {
+#define CASE(M)                                                                                       \
+    case M: {                                                                                         \
+        k::Ops<M> ops;                                                                                \
+        for (int t = 0; t < M; t++) { ops.x[t] = xs[o0 + t]; ops.dx[t] = dxs[o0 + t]; }                 \
+        k::pack_x4<M><<<grid_for_len(n), 256, 0, s>>>(ops, n, X4, done);                               \
+        if (lanes == 8) comm_launch_x4<M, 8>(c, w, xi, ops, X4, s, done);                              \
+        else comm_launch_x4<M, 32>(c, w, xi, ops, X4, s, done);                                        \
+    } break;
+                CASE(1) CASE(2) CASE(3) CASE(4)
+#undef CASE
+            }
+        }
+        return;
+    }
     // up to eight operands share one pass over the records
     for (int o0 = 0; o0 < nops; o0 += 8) {
         int m = std::min(8, nops - o0);
@@ -215,17 +249,20 @@ static void launch_comm_df(const cut_graph *g, const double *xi, float2 *xi2, fl
 // L(h) x_o for given xi (either arithmetic); df buffers may be null for FP64
 static void apply_L(const cut_graph *g, const double *xi, float2 *xi2, float2 *X2, int nops,
                     const double *const *xs, double *const *dxs, cudaStream_t s, const int *done) {
-    // without double-float scratch (adjoint recomputation) the stage runs in FP64
+    // without scratch (adjoint recomputation) the stage runs in FP64 with one
+    // gather per operand
     if (g->arith == CUT_ARITH_DF64 && xi2 && X2) launch_comm_df(g, xi, xi2, X2, nops, xs, dxs, s, done);
-    else launch_comm(g, xi, nops, xs, dxs, s, done);
+    else launch_comm(g, xi, nops, xs, dxs, s, done, 1, reinterpret_cast<double *>(X2));
 }
 
 static size_t df_scratch_bytes(const cut_graph *g) {
-    return g->arith == CUT_ARITH_DF64 ? (size_t)(std::max<int64_t>(1, g->host.n_g()) + 4 * g->host.n()) * 8 + 32 : 0;
+    return (size_t)(std::max<int64_t>(1, g->host.n_g()) + 4 * g->host.n()) * 8 + 32;
 }
 
-// Double-float scratch: xi2[n_g] pairs, then X2[n][4] pairs starting on a
-// 32-byte boundary (the stage reads one index's block with a 256-bit load).
+// Operand scratch of the commutator stage: xi2[n_g] pairs (double-float
+// only), then a 32-byte block per input index on a 32-byte boundary: X2[n][4]
+// FP32 pairs in double-float arithmetic, X4[n][4] doubles in FP64 (the stage
+// reads one index's block with a 256-bit load).
 static float2 *df_pairs_x(const cut_graph *g, void *df) {
     if (!df) return nullptr;
     const uintptr_t p = (uintptr_t)((float2 *)df + std::max<int64_t>(1, g->host.n_g()));
@@ -233,7 +270,7 @@ static float2 *df_pairs_x(const cut_graph *g, void *df) {
 }
 
 // f(Y) for the stacked state Y[nops][n] into DY[nops][n].  df: scratch of
-// df_scratch_bytes(g) bytes (double-float arithmetic only).
+// df_scratch_bytes(g) bytes (operand scratch; null: operands gathered one by one).
 static void stacked_rhs(const cut_graph *g, const double *Y, double *DY, int nops, double *xi,
                         cudaStream_t s, const int *done, void *df = nullptr) {
     const int64_t n = g->host.n();

@@ -61,3 +61,20 @@ def test_noalloc_rejects_host_only_handles(tmp_path):
     cg.build_graph(0, 2, pauli_registry(2), p)
     H = cg.Graph(p, device=-1)
     assert cg.lib().cut_rhs_noalloc(H._h, None, 0, None, None, None, None) == 1
+
+
+def test_packed_and_unpacked_operand_gathers_give_the_same_bits():
+    """cut_rhs packs the operands of each index into one 32-byte block (one
+    gather per record); cut_rhs_noalloc, which may not allocate the packing
+    scratch, gathers each operand separately.  Per operand both sum the same
+    records in the same order with the same FMAs: the results are equal bit
+    for bit."""
+    w = workload("molecular_8so")
+    G = graph_for("mol8", w.alg, w.nmodes, w.labels)
+    rng = np.random.default_rng(62)
+    xs = list(w.observables) + [rng.normal(size=len(w.h)) for _ in range(3)]   # 6 operands: two blocks
+    want_dh, want_dx = G.rhs(w.h, xs)
+    dh, dx = _noalloc(G, w.h, xs)
+    np.testing.assert_array_equal(dh, np64(want_dh))
+    for a, b in zip(dx, want_dx):
+        np.testing.assert_array_equal(a, np64(b))
