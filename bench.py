@@ -661,9 +661,10 @@ def main():
                        "build_s": round(tbuild, 1), "build_peak_over_stored":
                            round(bstats["peak_rss_bytes"] / max(1, bstats["bytes_stored"]), 3),
                        "parallelism": f"{world} independent instance(s)"},
-            # per RK4 step: 4 right-hand sides (generator stage, then per block of
-            # four operands one pack and one commutator launch) and 4 combinations
-            "gpu_launches": int(args.steps * 4 * (1 + 2 * ((nops + 3) // 4)) + args.steps * 4),
+            # per RK4 step: 4 right-hand sides (generator stage, then one pack and
+            # one commutator launch for up to four operands, else one commutator
+            # launch per eight) and 4 combinations
+            "gpu_launches": int(args.steps * 4 * (1 + (2 if nops <= 4 else (nops + 7) // 8)) + args.steps * 4),
             "roofline": roofline,
             "df64": df,
             "batched": batched,

@@ -153,17 +153,18 @@ static void comm_launch_x4(const DevCSR &c, const k::Weights &w, const double *x
         k::comm_stage_x4<M, false, L><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, xi, X4, ops, c.rows, done);
 }
 
-// X4: optional scratch of n x 32 bytes on a 32-byte boundary.  With it the
-// operands go in blocks of four through pack_x4 + comm_stage_x4 (one gather
-// per record); without it through comm_stage (one gather per operand).
-// Both give the same bits.
+// X4: optional scratch of n x 32 bytes on a 32-byte boundary.  With it, and
+// at most four operands, they go through pack_x4 + comm_stage_x4 (one gather
+// per record); otherwise through comm_stage (one gather per operand, up to
+// eight operands per pass over the records, so five to eight operands still
+// read the records once).  Both give the same bits.
 static void launch_comm(const cut_graph *g, const double *xi, int nops, const double *const *xs,
                         double *const *dxs, cudaStream_t s, const int *done, int stage = 1,
                         double *X4 = nullptr) {
     const DevCSR &c = g->st[stage];
     const k::Weights w = weights_of(g);
     const int lanes = comm_lanes(c.rows);
-    if (X4) {
+    if (X4 && nops <= 4) {
         const int64_t n = g->host.n();
         for (int o0 = 0; o0 < nops; o0 += 4) {
             const int m = std::min(4, nops - o0);

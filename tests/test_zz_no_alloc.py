@@ -72,7 +72,7 @@ def test_packed_and_unpacked_operand_gathers_give_the_same_bits():
     w = workload("molecular_8so")
     G = graph_for("mol8", w.alg, w.nmodes, w.labels)
     rng = np.random.default_rng(62)
-    xs = list(w.observables) + [rng.normal(size=len(w.h)) for _ in range(3)]   # 6 operands: two blocks
+    xs = list(w.observables) + [rng.normal(size=len(w.h))]   # H and three observables: one packed block
     want_dh, want_dx = G.rhs(w.h, xs)
     dh, dx = _noalloc(G, w.h, xs)
     np.testing.assert_array_equal(dh, np64(want_dh))
