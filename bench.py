@@ -38,6 +38,7 @@ sys.path.insert(0, ROOT)
 
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6400.0
+METRIC = "graph records applied per second (stress graph RK4 flow, FP64)"
 FP64_NOMINAL_TFLOPS = 1.25   # B300 FP64 (non-tensor) rate, nominal
 
 
@@ -455,10 +456,12 @@ def run_reference(args):
     if rank != 0:
         return
     cb = cpu_sample(seconds_budget=max(5.0, 60.0 / max(1, args.steps + args.warmup)))
-    line = {"impl": "reference", "metric": "graph records applied per second", "value": cb["value"],
+    # same metric, unit and workload name as the main line; the oracle runs a
+    # bounded sample of that recipe (stated in cpu_baseline.sample)
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"],
             "unit": "records/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "stress_16so (oracle on the 7-spin-orbital sample)"},
+            "data": "synthetic", "config": {"workload": args.workload, "sample": cb["sample"]},
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": "records/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -651,7 +654,7 @@ def main():
 
     if rank == 0:
         line = {
-            "metric": "graph records applied per second (stress graph RK4 flow, FP64)",
+            "metric": METRIC,
             "value": value, "unit": "records/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
