@@ -256,7 +256,7 @@ static void apply_L(const cut_graph *g, const double *xi, float2 *xi2, float2 *X
     else launch_comm(g, xi, nops, xs, dxs, s, done, 1, reinterpret_cast<double *>(X2));
 }
 
-static size_t df_scratch_bytes(const cut_graph *g) {
+static size_t operand_scratch_bytes(const cut_graph *g) {
     return (size_t)(std::max<int64_t>(1, g->host.n_g()) + 4 * g->host.n()) * 8 + 32;
 }
 
@@ -264,14 +264,14 @@ static size_t df_scratch_bytes(const cut_graph *g) {
 // only), then a 32-byte block per input index on a 32-byte boundary: X2[n][4]
 // FP32 pairs in double-float arithmetic, X4[n][4] doubles in FP64 (the stage
 // reads one index's block with a 256-bit load).
-static float2 *df_pairs_x(const cut_graph *g, void *df) {
+static float2 *operand_blocks(const cut_graph *g, void *df) {
     if (!df) return nullptr;
     const uintptr_t p = (uintptr_t)((float2 *)df + std::max<int64_t>(1, g->host.n_g()));
     return (float2 *)((p + 31) & ~(uintptr_t)31);
 }
 
 // f(Y) for the stacked state Y[nops][n] into DY[nops][n].  df: scratch of
-// df_scratch_bytes(g) bytes (operand scratch; null: operands gathered one by one).
+// operand_scratch_bytes(g) bytes (operand scratch; null: operands gathered one by one).
 static void stacked_rhs(const cut_graph *g, const double *Y, double *DY, int nops, double *xi,
                         cudaStream_t s, const int *done, void *df = nullptr) {
     const int64_t n = g->host.n();
@@ -279,7 +279,7 @@ static void stacked_rhs(const cut_graph *g, const double *Y, double *DY, int nop
     const double *xs[64];
     double *dxs[64];
     for (int o = 0; o < nops; o++) { xs[o] = Y + o * n; dxs[o] = DY + o * n; }
-    apply_L(g, xi, (float2 *)df, df_pairs_x(g, df), nops, xs, dxs, s, done);
+    apply_L(g, xi, (float2 *)df, operand_blocks(g, df), nops, xs, dxs, s, done);
 }
 
 }  // namespace cut
@@ -436,14 +436,14 @@ cut_status cut_rhs(const cut_graph *g, const double *h, int n_obs, const double 
     double *xi = xi_out;
     if (!xi) CUDA_TRY(cudaMallocAsync(&xi, std::max<int64_t>(1, g->host.n_g()) * 8, s));
     void *df = nullptr;
-    if (df_scratch_bytes(g)) CUDA_TRY(cudaMallocAsync(&df, df_scratch_bytes(g), s));
+    CUDA_TRY(cudaMallocAsync(&df, operand_scratch_bytes(g), s));
     launch_gen(g, h, xi, s, nullptr);
     const double *xs[64];
     double *dxs[64];
     xs[0] = h;
     dxs[0] = dh;
     for (int o = 0; o < n_obs; o++) { xs[o + 1] = x + o * n; dxs[o + 1] = dx + o * n; }
-    apply_L(g, xi, (float2 *)df, df_pairs_x(g, df), n_obs + 1, xs, dxs, s, nullptr);
+    apply_L(g, xi, (float2 *)df, operand_blocks(g, df), n_obs + 1, xs, dxs, s, nullptr);
     CUDA_TRY(cudaGetLastError());
     if (!xi_out) CUDA_TRY(cudaFreeAsync(xi, s));
     if (df) CUDA_TRY(cudaFreeAsync(df, s));
@@ -467,11 +467,11 @@ cut_status cut_apply_L(const cut_graph *g, const double *xi, int n_ops, const do
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = g->host.n();
     void *df = nullptr;
-    if (df_scratch_bytes(g)) CUDA_TRY(cudaMallocAsync(&df, df_scratch_bytes(g), s));
+    CUDA_TRY(cudaMallocAsync(&df, operand_scratch_bytes(g), s));
     const double *xs[64];
     double *dxs[64];
     for (int o = 0; o < n_ops; o++) { xs[o] = x + o * n; dxs[o] = dx + o * n; }
-    apply_L(g, xi, (float2 *)df, df_pairs_x(g, df), n_ops, xs, dxs, s, nullptr);
+    apply_L(g, xi, (float2 *)df, operand_blocks(g, df), n_ops, xs, dxs, s, nullptr);
     CUDA_TRY(cudaGetLastError());
     if (df) CUDA_TRY(cudaFreeAsync(df, s));
     return set_ok();
@@ -705,7 +705,7 @@ struct FlowWork {
     k::Control *ctl;
     double *replay, *record;
     int *flag;
-    void *df = nullptr;            // double-float scratch (or null)
+    void *df = nullptr;            // commutator operand scratch (or null)
     void *base = nullptr;
 };
 
@@ -858,7 +858,7 @@ extern "C" cut_status cut_flow(const cut_graph *g, double *h, int n_obs, double 
     const int64_t max_steps = o->max_steps > 0 ? o->max_steps : 1000000;
     const int64_t nrec = dp ? (replay ? o->n_replay : std::min<int64_t>(max_steps, 1 << 22)) : 1;
     FlowWork w;
-    st = alloc_work(w, L, ng, nrec, s, df_scratch_bytes(g));
+    st = alloc_work(w, L, ng, nrec, s, operand_scratch_bytes(g));
     if (st != CUT_OK) { end_work(sp); return st; }
     auto fail = [&](cut_status e) { cudaFreeAsync(w.base, s); end_work(sp); return e; };
     cudaMemcpyAsync(w.Y, h, n * 8, cudaMemcpyDeviceToDevice, s);
