@@ -47,6 +47,24 @@ def test_df64_rhs_matches_oracle(name):
         assert_close(np64(g_), w_, what="dx (df64)", atol=fl)
 
 
+@pytest.mark.parametrize("n_obs", [3, 5])
+def test_df64_rhs_with_operand_chunks(n_obs):
+    """Double-float arithmetic takes up to three operands per pass over the
+    records: four operands run as 3 + 1, six as 3 + 3."""
+    labels, h, _ = _mol5()
+    rng = np.random.default_rng(72 + n_obs)
+    xs = [rng.normal(size=len(labels)) for _ in range(n_obs)]
+    G = graph_for("mol5_3body_df", ALG_FERMION, 5, labels)
+    G.set_arithmetic("df64")
+    dh, dxs = G.rhs(h, xs)
+    want_dh, want_dxs = oracle.rhs(ALG_FERMION, 5, labels, h, xs)
+    fl = rhs_floor(h, xs)
+    assert_close(np64(dh), want_dh, what="dh (df64)", atol=fl)
+    assert len(dxs) == n_obs
+    for g_, w_ in zip(dxs, want_dxs):
+        assert_close(np64(g_), w_, what="dx (df64)", atol=fl)
+
+
 def test_df64_flows_match_oracle():
     from cut_inputs import fermion_registry
     norb = 4
