@@ -142,3 +142,27 @@ def test_batched_diagonal_only_registry_is_stationary():
         assert np.all(status.cpu().numpy() == 0)
         np.testing.assert_array_equal(np64(Hs), H)
         np.testing.assert_array_equal(np64(Xs), X)
+
+
+@pytest.mark.parametrize("n_obs", [0, 3])
+def test_batched_rk4_fp64_operand_counts(n_obs):
+    """No observable (H alone) and three observables (four operands, the
+    most a batch carries) against the oracle's RK4 flow."""
+    import torch
+    norb, B = 4, 11
+    labels = fermion_registry(norb)
+    H = batched_parameters(labels, norb, B, seed=38)
+    rng = np.random.default_rng(38)
+    obs = [number_operator(labels, norb), dipole_operator(labels, norb, seed=38), rng.normal(size=len(labels))]
+    X = np.stack([np.stack(obs[:n_obs])] * B) if n_obs else None
+    G = graph_for("mol4", ALG_FERMION, norb, labels)
+    Hs, Xs, steps, status = G.flow_batched(torch.tensor(H), None if X is None else torch.tensor(X),
+                                           precision="fp64", method="rk4", s0=0.0, s1=0.1, ds=0.02, tile=4)
+    assert np.all(status.cpu().numpy() == 0) and np.all(steps.cpu().numpy() == 5)
+    f = oracle.stacked_rhs(ALG_FERMION, norb, labels, n_obs)
+    n = len(labels)
+    for b in (0, 6, 10):
+        y = oracle.rk4_flow(f, np.concatenate([H[b]] + [X[b, o] for o in range(n_obs)]), 0.02, 5)
+        assert_close(np64(Hs[b]), y[:n], what=f"h[{b}]")
+        for o in range(n_obs):
+            assert_close(np64(Xs[b, o]), y[(o + 1) * n:(o + 2) * n], what=f"x{o}[{b}]")

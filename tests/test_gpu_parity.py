@@ -78,6 +78,20 @@ def test_rhs_is_bitwise_deterministic_and_n_obs_independent():
     assert np.all(np64(a[1][0]) == 0.0)
 
 
+def test_rhs_four_operands_one_packed_block():
+    """H and three observables: the largest set whose operands travel in one
+    packed 32-byte block per index."""
+    alg, nm, labels, h, xs = _case("mol5_3body")
+    xs = xs + [np.random.default_rng(27).normal(size=len(labels))]
+    G = graph_for("mol5_3body", alg, nm, labels)
+    dh, dxs = G.rhs(h, xs)
+    want_dh, want_dxs = oracle.rhs(alg, nm, labels, h, xs)
+    fl = rhs_floor(h, xs)
+    assert_close(np64(dh), want_dh, what="dh", atol=fl)
+    for g_, w_ in zip(dxs, want_dxs):
+        assert_close(np64(g_), w_, what="dx", atol=fl)
+
+
 def test_rhs_many_operands_in_chunks():
     """More than four operands run as several record passes."""
     alg, nm, labels, h, _ = _case("mol5_3body")
