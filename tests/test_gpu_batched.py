@@ -166,3 +166,25 @@ def test_batched_rk4_fp64_operand_counts(n_obs):
         assert_close(np64(Hs[b]), y[:n], what=f"h[{b}]")
         for o in range(n_obs):
             assert_close(np64(Xs[b, o]), y[(o + 1) * n:(o + 2) * n], what=f"x{o}[{b}]")
+
+
+@pytest.mark.parametrize("n_obs", [1, 3])
+def test_batched_fp32_operand_layouts(n_obs):
+    """FP32 records with two operands (pairs) and four (the padded block's
+    full width) against the FP64 batch of the same flows."""
+    import torch
+    norb, B = 4, 19
+    labels = fermion_registry(norb)
+    H = batched_parameters(labels, norb, B, seed=39)
+    rng = np.random.default_rng(39)
+    obs = [dipole_operator(labels, norb, seed=39), number_operator(labels, norb), rng.normal(size=len(labels))]
+    X = torch.tensor(np.stack([np.stack(obs[:n_obs])] * B))
+    G = graph_for("mol4", ALG_FERMION, norb, labels)
+    kw = dict(method="rk4", s0=0.0, s1=0.2, ds=0.02)
+    H64, X64, _, st64 = G.flow_batched(torch.tensor(H), X, precision="fp64", **kw)
+    H32, X32, _, st32 = G.flow_batched(torch.tensor(H), X, precision="fp32", **kw)
+    assert np.all(st64.cpu().numpy() == 0) and np.all(st32.cpu().numpy() == 0)
+    for a, b in ((H32, H64), (X32, X64)):
+        a, b = np64(a), np64(b)
+        err = np.max(np.abs(a - b)) / np.max(np.abs(b))
+        assert err < 1e-5, err
