@@ -665,9 +665,9 @@ def main():
                            round(bstats["peak_rss_bytes"] / max(1, bstats["bytes_stored"]), 3),
                        "parallelism": f"{world} independent instance(s)"},
             # per RK4 step: 4 right-hand sides (generator stage, then one pack and
-            # one commutator launch for up to four operands, else one commutator
+            # one commutator launch for up to eight operands, else one commutator
             # launch per eight) and 4 combinations
-            "gpu_launches": int(args.steps * 4 * (1 + (2 if nops <= 4 else (nops + 7) // 8)) + args.steps * 4),
+            "gpu_launches": int(args.steps * 4 * (1 + (2 if nops <= 8 else (nops + 7) // 8)) + args.steps * 4),
             "roofline": roofline,
             "df64": df,
             "batched": batched,

@@ -146,7 +146,7 @@ cut_status cut_graph_records(const cut_graph *g, int stage, int64_t *row_ptr, in
  * device in : h[n], x[n_obs][n] (NULL if n_obs == 0)
  * device out: dh[n], dx[n_obs][n], xi_out[n_g] (optional, NULL = not kept)
  * Runs asynchronously on `stream`; takes its scratch (the packed operand
- * blocks, n x 32 bytes, and the generator when xi_out is NULL) from the
+ * blocks, n x 64 bytes, and the generator when xi_out is NULL) from the
  * stream-ordered allocator and returns it on the same stream.
  * Errors: INVALID_ARG, CUDA. */
 cut_status cut_rhs(const cut_graph *g, const double *h, int n_obs, const double *x, double *dh,
@@ -210,7 +210,7 @@ cut_status cut_rhs_jvp(const cut_graph *g, const double *h, int n_obs, const dou
  * (for example a real-time or serving loop whose memory is fixed up front,
  * or code whose allocator is owned by someone else), since cut_rhs takes
  * temporary buffers from the stream-ordered allocator (the generator when
- * xi_out is NULL, and a 32-byte block per coordinate into which the
+ * xi_out is NULL, and up to 64 bytes per coordinate into which the
  * operands are packed).  Here the generator buffer is a fixed array of
  * CUT_RHS_NOALLOC_MAX_NG
  * doubles (8 MiB) compiled into the library: every GPU that loads the

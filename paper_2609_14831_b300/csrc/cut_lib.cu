@@ -153,21 +153,21 @@ static void comm_launch_x4(const DevCSR &c, const k::Weights &w, const double *x
         k::comm_stage_x4<M, false, L><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, xi, X4, ops, c.rows, done);
 }
 
-// X4: optional scratch of n x 32 bytes on a 32-byte boundary.  With it, and
-// at most four operands, they go through pack_x4 + comm_stage_x4 (one gather
-// per record); otherwise through comm_stage (one gather per operand, up to
-// eight operands per pass over the records, so five to eight operands still
-// read the records once).  Both give the same bits.
+// X4: optional scratch of n x 64 bytes on a 32-byte boundary.  With it, and
+// at most eight operands, they go through pack_x4 + comm_stage_x4 in one
+// pass over the records (one 256-bit gather per four operands and record);
+// otherwise through comm_stage (one gather per operand, eight operands per
+// pass).  Both give the same bits.
 static void launch_comm(const cut_graph *g, const double *xi, int nops, const double *const *xs,
                         double *const *dxs, cudaStream_t s, const int *done, int stage = 1,
                         double *X4 = nullptr) {
     const DevCSR &c = g->st[stage];
     const k::Weights w = weights_of(g);
     const int lanes = comm_lanes(c.rows);
-    if (X4 && nops <= 4) {
+    if (X4 && nops <= 8) {
         const int64_t n = g->host.n();
-        for (int o0 = 0; o0 < nops; o0 += 4) {
-            const int m = std::min(4, nops - o0);
+        for (int o0 = 0; o0 < nops; o0 += 8) {
+            const int m = std::min(8, nops - o0);
             switch (m) {
 #define CASE(M)                                                                                       \
     case M: {                                                                                         \
@@ -177,7 +177,7 @@ static void launch_comm(const cut_graph *g, const double *xi, int nops, const do
         if (lanes == 8) comm_launch_x4<M, 8>(c, w, xi, ops, X4, s, done);                              \
         else comm_launch_x4<M, 32>(c, w, xi, ops, X4, s, done);                                        \
     } break;
-                CASE(1) CASE(2) CASE(3) CASE(4)
+                CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
 #undef CASE
             }
         }
@@ -257,13 +257,14 @@ static void apply_L(const cut_graph *g, const double *xi, float2 *xi2, float2 *X
 }
 
 static size_t operand_scratch_bytes(const cut_graph *g) {
-    return (size_t)(std::max<int64_t>(1, g->host.n_g()) + 4 * g->host.n()) * 8 + 32;
+    return (size_t)(std::max<int64_t>(1, g->host.n_g()) + 8 * g->host.n()) * 8 + 32;
 }
 
 // Operand scratch of the commutator stage: xi2[n_g] pairs (double-float
-// only), then a 32-byte block per input index on a 32-byte boundary: X2[n][4]
-// FP32 pairs in double-float arithmetic, X4[n][4] doubles in FP64 (the stage
-// reads one index's block with a 256-bit load).
+// only), then, on a 32-byte boundary, up to 64 bytes per input index:
+// X2[n][4] FP32 pairs in double-float arithmetic, X4[n][4 NB] doubles in
+// FP64 (NB = 1 or 2 blocks of 32 bytes; the stages read a block with one
+// 256-bit load).
 static float2 *operand_blocks(const cut_graph *g, void *df) {
     if (!df) return nullptr;
     const uintptr_t p = (uintptr_t)((float2 *)df + std::max<int64_t>(1, g->host.n_g()));

@@ -169,10 +169,11 @@ __global__ void __launch_bounds__(kBlock) comm_stage(const uint64_t *__restrict_
     }
 }
 
-// The same stage with the (up to four) operands of one input index stored
-// together, X4[j][4] (32 bytes, one 256-bit load per record instead of one
-// load per operand).  Per lane and operand the records are summed in the
-// same order with the same FMAs as comm_stage, so both give the same bits.
+// The same stage with the (up to eight) operands of one input index stored
+// together in NB = ceil(NOPS / 4) blocks of 32 bytes, X4[j][4 NB] (one
+// 256-bit load per block and record instead of one load per operand).  Per
+// lane and operand the records are summed in the same order with the same
+// FMAs as comm_stage, so both give the same bits.
 __device__ __forceinline__ void ld_quad64(const double *p, double &a, double &b, double &c, double &d) {
     asm volatile("ld.global.nc.v4.f64 {%0, %1, %2, %3}, [%4];" : "=d"(a), "=d"(b), "=d"(c), "=d"(d) : "l"(p));
 }
@@ -183,7 +184,8 @@ __global__ void __launch_bounds__(kBlock) comm_stage_x4(const uint64_t *__restri
                                                         const double *__restrict__ xi,
                                                         const double *__restrict__ X4, Ops<NOPS> ops,
                                                         int64_t rows, const int *done) {
-    static_assert(NOPS <= 4, "four operands per packed block");
+    static_assert(NOPS <= 8, "at most two packed blocks");
+    constexpr int NB = (NOPS + 3) / 4;
     constexpr int RPW = 32 / LANES;
     __shared__ double ws[256];
     __shared__ unsigned long long sg[256];
@@ -200,16 +202,19 @@ __global__ void __launch_bounds__(kBlock) comm_stage_x4(const uint64_t *__restri
             const uint64_t e = rp[r + 1];
 #define COEF(q) (UNIFORM ? signed_by(xi[(q).x & kIdx], sg[(q).x >> 24]) : ws[(q).x >> 24] * xi[(q).x & kIdx])
             uint64_t p = rp[r] + sl;
-            constexpr int U = 4;   // as comm_stage
+            constexpr int U = NOPS <= 4 ? 4 : 2;   // as comm_stage
             for (; p + (U - 1) * LANES < e; p += U * LANES) {
                 uint2 q[U];
 #pragma unroll
                 for (int u = 0; u < U; u++) q[u] = __ldcs(rec + p + u * LANES);
-                double c[U], xv[U][4];
+                double c[U], xv[U][4 * NB];
 #pragma unroll
                 for (int u = 0; u < U; u++) {
                     c[u] = COEF(q[u]);
-                    ld_quad64(X4 + 4 * (int64_t)q[u].y, xv[u][0], xv[u][1], xv[u][2], xv[u][3]);
+#pragma unroll
+                    for (int b = 0; b < NB; b++)
+                        ld_quad64(X4 + 4 * NB * (int64_t)q[u].y + 4 * b, xv[u][4 * b], xv[u][4 * b + 1],
+                                  xv[u][4 * b + 2], xv[u][4 * b + 3]);
                 }
 #pragma unroll
                 for (int u = 0; u < U; u++)
@@ -219,8 +224,11 @@ __global__ void __launch_bounds__(kBlock) comm_stage_x4(const uint64_t *__restri
             for (; p < e; p += LANES) {
                 const uint2 q = __ldcs(rec + p);
                 const double c = COEF(q);
-                double xv[4];
-                ld_quad64(X4 + 4 * (int64_t)q.y, xv[0], xv[1], xv[2], xv[3]);
+                double xv[4 * NB];
+#pragma unroll
+                for (int b = 0; b < NB; b++)
+                    ld_quad64(X4 + 4 * NB * (int64_t)q.y + 4 * b, xv[4 * b], xv[4 * b + 1], xv[4 * b + 2],
+                              xv[4 * b + 3]);
 #pragma unroll
                 for (int o = 0; o < NOPS; o++) acc[o] += c * xv[o];
             }
@@ -234,13 +242,15 @@ __global__ void __launch_bounds__(kBlock) comm_stage_x4(const uint64_t *__restri
     }
 }
 
-// X4[j][o] = x_o[j] for o < NOPS (the remaining slots are never used)
+// X4[j][o] = x_o[j] for o < NOPS, blocks of 4 NB doubles per index (the
+// remaining slots are never used)
 template <int NOPS>
 __global__ void pack_x4(Ops<NOPS> ops, int64_t n, double *__restrict__ X4, const int *done) {
+    constexpr int NB = (NOPS + 3) / 4;
     if (skip(done)) return;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
-        for (int o = 0; o < NOPS; o++) X4[4 * j + o] = ops.x[o][j];
+        for (int o = 0; o < NOPS; o++) X4[4 * NB * j + o] = ops.x[o][j];
     }
 }
 

@@ -63,16 +63,17 @@ def test_noalloc_rejects_host_only_handles(tmp_path):
     assert cg.lib().cut_rhs_noalloc(H._h, None, 0, None, None, None, None) == 1
 
 
-def test_packed_and_unpacked_operand_gathers_give_the_same_bits():
-    """cut_rhs packs the operands of each index into one 32-byte block (one
-    gather per record); cut_rhs_noalloc, which may not allocate the packing
-    scratch, gathers each operand separately.  Per operand both sum the same
-    records in the same order with the same FMAs: the results are equal bit
-    for bit."""
+@pytest.mark.parametrize("n_obs", [3, 7])
+def test_packed_and_unpacked_operand_gathers_give_the_same_bits(n_obs):
+    """cut_rhs packs the operands of each index into 32-byte blocks (one
+    gather per block and record; 4 operands fill one block, 8 two);
+    cut_rhs_noalloc, which may not allocate the packing scratch, gathers each
+    operand separately.  Per operand both sum the same records in the same
+    order with the same FMAs: the results are equal bit for bit."""
     w = workload("molecular_8so")
     G = graph_for("mol8", w.alg, w.nmodes, w.labels)
     rng = np.random.default_rng(62)
-    xs = list(w.observables) + [rng.normal(size=len(w.h))]   # H and three observables: one packed block
+    xs = list(w.observables) + [rng.normal(size=len(w.h)) for _ in range(n_obs - 2)]
     want_dh, want_dx = G.rhs(w.h, xs)
     dh, dx = _noalloc(G, w.h, xs)
     np.testing.assert_array_equal(dh, np64(want_dh))
