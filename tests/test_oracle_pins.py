@@ -352,3 +352,44 @@ def test_oracle_jvp_pairs_with_vjp():
     jh, (jx,) = oracle.rhs_jvp(ALG_FERMION, 3, labels, h, [x], dh, [dx])
     bh, (bx,) = oracle.rhs_vjp(ALG_FERMION, 3, labels, h, [x], wh, [wx])
     np.testing.assert_allclose(wh @ jh + wx @ jx, bh @ dh + bx @ dx, rtol=1e-12)
+
+
+def test_adamw_oracle_worked_example_and_special_cases():
+    """Pins the oracle's AdamW step (Loshchilov & Hutter, decoupled weight
+    decay) against a hand-worked two-step example and against special cases
+    that a plausible mistake breaks.
+
+    Worked example, p0 = 1, lr = 0.1, beta1 = 0.9, beta2 = 0.999,
+    eps = 1e-8, wd = 0.01, m0 = v0 = 0:
+      t = 1, g = 0.5:  m = 0.1 * 0.5 = 0.05;  v = 0.001 * 0.25 = 2.5e-4;
+        m_hat = 0.05 / (1 - 0.9) = 0.5;  v_hat = 2.5e-4 / (1 - 0.999) = 0.25;
+        p1 = 1 - 0.1 * (0.5 / (0.5 + 1e-8) + 0.01 * 1) = 0.899000002 (to 1e-16)
+      t = 2, g = -0.25:  m = 0.9 * 0.05 + 0.1 * (-0.25) = 0.02;
+        v = 0.999 * 2.5e-4 + 0.001 * 0.0625 = 3.1225e-4;
+        m_hat = 0.02 / (1 - 0.81) = 2/19;  v_hat = 3.1225e-4 / (1 - 0.998001);
+        p2 = p1 - 0.1 * (m_hat / (sqrt(v_hat) + 1e-8) + 0.01 * p1)
+           = 0.871467298705846163 (40-digit decimal arithmetic)
+    """
+    from oracle import mlp
+    p, m, v = mlp.adamw(np.array([1.0]), np.array([0.5]), 0.0, 0.0, 1, 0.1, 0.9, 0.999, 1e-8, 0.01)
+    np.testing.assert_allclose(m, [0.05], rtol=1e-15)
+    np.testing.assert_allclose(v, [2.5e-4], rtol=1e-14)
+    np.testing.assert_allclose(p, [0.8990000019999999600], rtol=1e-15)
+    p, m, v = mlp.adamw(p, np.array([-0.25]), m, v, 2, 0.1, 0.9, 0.999, 1e-8, 0.01)
+    np.testing.assert_allclose(m, [0.02], rtol=1e-14)
+    np.testing.assert_allclose(v, [3.1225e-4], rtol=1e-14)
+    np.testing.assert_allclose(p, [0.8714672987058461626], rtol=1e-15)
+
+    g = np.array([3.0, -1e-3, 40.0])
+    # bias correction: the first step from zero moments moves every
+    # parameter by lr * sign(g) (up to eps), whatever |g| is
+    p1, _, _ = mlp.adamw(np.zeros(3), g, 0.0, 0.0, 1, 0.01, 0.9, 0.999, 1e-12, 0.0)
+    np.testing.assert_allclose(p1, -0.01 * np.sign(g), rtol=1e-8)
+    # decoupled decay, scaled by lr: with no gradient p -> p (1 - lr wd),
+    # and the moments stay zero (an L2 penalty would have entered them)
+    p1, m1, v1 = mlp.adamw(np.array([2.0]), np.array([0.0]), 0.0, 0.0, 1, 0.1, 0.9, 0.999, 1e-8, 0.5)
+    np.testing.assert_allclose(p1, [2.0 * (1 - 0.1 * 0.5)], rtol=1e-15)
+    assert m1[0] == 0.0 and v1[0] == 0.0
+    # eps outside the square root: g = eps gives m_hat / (|g| + eps) = 1/2
+    p1, _, _ = mlp.adamw(np.array([0.0]), np.array([1e-8]), 0.0, 0.0, 1, 1.0, 0.9, 0.999, 1e-8, 0.0)
+    np.testing.assert_allclose(p1, [-0.5], rtol=1e-12)
