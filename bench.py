@@ -39,7 +39,6 @@ sys.path.insert(0, ROOT)
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6400.0
 METRIC = "graph records applied per second (stress graph RK4 flow, FP64)"
-FP64_NOMINAL_TFLOPS = 1.25   # B300 FP64 (non-tensor) rate, nominal
 
 
 def _peak_hbm():
@@ -575,7 +574,10 @@ def main():
     comm_bytes = 8 * G.R_L + 8 * (n + 1) + 8 * nops * n
     fp64_flop = 2 * nops * G.R_L                # one FMA per record and operand
     hbm_peak, peak_kind = _peak_hbm()
-    fp64_peak = FP64_NOMINAL_TFLOPS
+    # the FP64 roof of this GPU, measured in this process (independent FMA
+    # chains on every SM, CUDA events), and the FP32 one beside it
+    fp64_peak = cg.measure_fma_rate(local, fp64=True, seconds=0.5)
+    fp32_peak = cg.measure_fma_rate(local, fp64=False, seconds=0.5)
     traffic_table = {}
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tpath):
@@ -586,8 +588,9 @@ def main():
     traffic = traffic_table.get(f"{args.workload}:comm_stage_fp64")
     roofline = {"bound": "alu", "achieved": fp64_flop / (comm_ms * 1e-3) / 1e12, "peak": fp64_peak,
                 "unit": "TFLOP/s", "frac": fp64_flop / (comm_ms * 1e-3) / 1e12 / fp64_peak, "traffic": traffic,
-                "peak_kind": "nominal B300 FP64 rate (profiling recipe table); the FP64 pipe is the "
-                             "measured bound (ncu: sm__pipe_fp64_cycles_active > 90%)",
+                "peak_kind": "measured in this run: FP64 FMA throughput of independent chains on every SM "
+                             "(cut_measure_fma_rate, best of 3 launches, CUDA events)",
+                "fp32_fma_tflops_measured": fp32_peak,
                 "kernel": f"comm_stage_x4<{nops}> (FP64, operands of one index in one 32-byte block)",
                 "launch_ms": comm_ms, "algorithmic_flop": fp64_flop,
                 "hbm_view": {"achieved": comm_bytes / (comm_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",

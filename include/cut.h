@@ -122,6 +122,12 @@ typedef struct {
     int64_t device_bytes;    /* graph bytes resident on the device */
     int64_t record_bytes;    /* bytes of one stored record (both stages) */
     int64_t n_out, R_C;      /* outside-space labels and records (0 without diagnostics) */
+    int shard_rank, shard_world; /* shard handles (cut_graph_load_shard): its
+                                    rank and the number of shards; 0, 0 for a
+                                    whole graph.  R_g and R_L then count the
+                                    shard's own records. */
+    int64_t gen_lo, gen_hi;      /* generator rows held: [gen_lo, gen_hi) */
+    int64_t comm_lo, comm_hi;    /* commutator rows held: [comm_lo, comm_hi) */
 } cut_graph_desc;
 
 cut_status cut_graph_query(const cut_graph *g, cut_graph_desc *out);
@@ -223,7 +229,9 @@ cut_status cut_rhs_jvp(const cut_graph *g, const double *h, int n_obs, const dou
  *   - Makes no cudaMalloc, cudaFree or other allocating call.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     before any stream capture.  The address is kept per device and CUDA
+ *     context: after a device reset, or with another context current, the
+ *     next call looks it up again (again outside any capture).
  *   - All calls on a device share the one array and it keeps what the last
  *     call left there (every entry is rewritten before it is read, so nothing
  *     needs clearing): calls whose kernels overlap on the GPU (different
@@ -245,6 +253,56 @@ cut_status cut_rhs_adjoint(const cut_graph *g, const double *h, int n_obs, const
                            cut_stream_t stream);
 
 /* ------------------------------------------------------------------ */
+/* Target-range shards (Sec. 2.2: records grouped by output)            */
+/* ------------------------------------------------------------------ */
+/* Because every output's records are stored together, the outputs of each
+ * stage split into contiguous row ranges that hold about equal numbers of
+ * records.  A shard holds one range of the generator stage and one of the
+ * commutator stage; per right-hand side the shards of a group compute their
+ * pieces from full input vectors and exchange them (all-gather of xi, then
+ * of the outputs).  Each row is summed exactly as the whole graph sums it,
+ * so the assembled pieces equal cut_rhs bit for bit.
+ *
+ * Record-balanced bounds of stage 0 (generator rows) or 1 (commutator rows)
+ * split into `parts`: host out bounds[parts + 1]; part p holds rows
+ * [bounds[p], bounds[p+1]) and starts at the first row whose record offset
+ * reaches p * R / parts.  Needs a whole-graph handle (host-only works).
+ * Errors: INVALID_ARG. */
+cut_status cut_graph_partition(const cut_graph *g, int stage, int parts, int64_t *bounds);
+
+/* Load shard `rank` of `world` onto `device`: the records of generator rows
+ * [gen_lo, gen_hi) and commutator rows [comm_lo, comm_hi) of
+ * cut_graph_partition(.., world, ..) are resident (about 1/world of the
+ * graph); labels and factors are kept whole on the host.  The handle serves
+ * cut_shard_generator, cut_shard_commutator, the query and host-side calls;
+ * whole-graph traversals (cut_rhs, cut_flow, ...) return INVALID_ARG on it.
+ * Errors: as cut_graph_load, INVALID_ARG (rank, world, device). */
+cut_status cut_graph_load_shard(const char *path, int device, int rank, int world, unsigned flags,
+                                cut_graph **out);
+
+/* Generator stage of the shard's rows (Eq. graph-actions, line 1):
+ * device in h[n] (whole vector); device out xi_part[gen_hi - gen_lo], entry
+ * r - gen_lo = xi_r.  Errors: INVALID_ARG, CUDA. */
+cut_status cut_shard_generator(const cut_graph *g, const double *h, double *xi_part, cut_stream_t stream);
+
+/* Commutator stage of the shard's rows (Eq. graph-actions, line 2) for n_ops
+ * operands: device in xi[n_g] (all generator coordinates), x[n_ops][n];
+ * device out dx_part[n_ops][comm_hi - comm_lo].  Takes the operand-packing
+ * scratch (n x 64 bytes) from the stream-ordered allocator like cut_rhs.
+ * Errors: INVALID_ARG, CUDA. */
+cut_status cut_shard_commutator(const cut_graph *g, const double *xi, int n_ops, const double *x, double *dx_part,
+                                cut_stream_t stream);
+
+/* Runge-Kutta combination out[i] = base[i] + sum_s (c[s] ds) K[s][i] for
+ * len entries (terms with c[s] == 0 skipped), the same kernel and rounding
+ * as the stage inputs and updates of cut_flow, so a flow driven step by step
+ * through the shard calls reproduces cut_flow's RK4 bit for bit.  host in:
+ * K[nk] (device pointers), c[nk]; nk <= 7; device in/out: base, out (may be
+ * the same).  Uses the current device.  Errors: INVALID_ARG, CUDA. */
+cut_status cut_combine(int64_t len, const double *base, int nk, const double *const *K, const double *c, double ds,
+                       double *out, cut_stream_t stream);
+
+/* ------------------------------------------------------------------ */
 /* Flows                                                                */
 /* ------------------------------------------------------------------ */
 typedef struct {
@@ -257,7 +315,12 @@ typedef struct {
                                    these n_replay steps, all accepted */
     int64_t n_replay;
     double *record_steps;    /* host, optional: accepted step sizes out */
-    int64_t record_cap;      /* capacity of record_steps */
+    int64_t record_cap;      /* capacity of record_steps (cut_flow), or per
+                                instance of batch_record_steps (cut_flow_batched) */
+    double *batch_record_steps; /* device, cut_flow_batched only, optional:
+                                   [batch][record_cap], row b receives the
+                                   accepted step sizes of instance b in order
+                                   (entries past its step count are untouched) */
 } cut_flow_opts;
 
 typedef struct {
@@ -298,13 +361,26 @@ cut_status cut_flow_vjp(const cut_graph *g, const double *h0, int n_obs, const d
  * the error estimate; the RK state and its updates Y + ds * (stage sum), the
  * flow coordinate and the step size stay FP64).
  * Each instance has its own adaptive step sequence (DP45) and stops at s1.
- * device out: steps_out[batch] accepted steps, status_out[batch] cut_status.
- * host in: opts (replay/record fields ignored).  `tile` chooses the instance
+ * device out: steps_out[batch] accepted steps, status_out[batch] cut_status,
+ * and, when opts->batch_record_steps is set, each instance's accepted step
+ * sizes (so that a reference can replay that instance's path).
+ * host in: opts (replay_steps and the host record_steps are ignored).  `tile` chooses the instance
  * tile width (0 = autotuned).  Synchronises `stream` before returning.
  * Errors: INVALID_ARG, CUDA, OUT_OF_MEMORY. */
 cut_status cut_flow_batched(const cut_graph *g, int batch, double *h, int n_obs, double *x,
                             int precision, const cut_flow_opts *opts, int tile, int *steps_out,
                             int *status_out, cut_stream_t stream);
+
+/* ------------------------------------------------------------------ */
+/* Measured roofs                                                       */
+/* ------------------------------------------------------------------ */
+/* Fused multiply-add throughput of CUDA device `device` in TFLOP/s (2 flops
+ * per FMA), FP64 (fp64 != 0) or FP32: independent FMA chains in every thread
+ * of 8 CTAs x 256 threads per SM; the loop length grows until one launch
+ * takes about seconds / 4, then the best of three timed launches (CUDA
+ * events) is reported.  The FP64 graph traversal on B300 is bound by this
+ * rate, not by HBM.  host out: tflops.  Errors: INVALID_ARG, CUDA. */
+cut_status cut_measure_fma_rate(int device, int fp64, double seconds, double *tflops);
 
 /* ------------------------------------------------------------------ */
 /* Learned surrogate of the flow map (the paper has no counterpart: a   */
@@ -347,8 +423,16 @@ cut_status cut_mlp_backward(cut_mlp *m, int batch, const float *x, const float *
  * backward's gradients. */
 cut_status cut_mlp_adamw_step(cut_mlp *m, float lr, float beta1, float beta2, float eps, float weight_decay,
                               cut_stream_t stream);
-/* Synchronises; TIMEOUT if a tensor-core pipeline wait gave up. */
+/* Synchronises; TIMEOUT if a tensor-core pipeline wait gave up since the
+ * last call (each wait gives up after about one second; the kernel then
+ * writes nothing, waits for its own copies, frees its tensor memory and
+ * returns, so the context stays usable).  The flag is cleared once reported. */
 cut_status cut_mlp_status(cut_mlp *m);
+/* Failure injection for tests (no fault, no hang): while `on` is nonzero
+ * every GEMM of m issues no operand copies, so its pipeline wait runs out
+ * after about a second and cut_mlp_status reports TIMEOUT; outputs of those
+ * calls are undefined.  Synchronises the device.  Errors: INVALID_ARG, CUDA. */
+cut_status cut_mlp_inject_stall(cut_mlp *m, int on);
 
 #ifdef __cplusplus
 }

@@ -48,7 +48,10 @@ class GraphDesc(ctypes.Structure):
                 ("n_codes", ctypes.c_int), ("n", ctypes.c_int64), ("n_g", ctypes.c_int64),
                 ("R_g", ctypes.c_int64), ("R_L", ctypes.c_int64), ("sha256", ctypes.c_uint8 * 32),
                 ("device_bytes", ctypes.c_int64), ("record_bytes", ctypes.c_int64),
-                ("n_out", ctypes.c_int64), ("R_C", ctypes.c_int64)]
+                ("n_out", ctypes.c_int64), ("R_C", ctypes.c_int64),
+                ("shard_rank", ctypes.c_int), ("shard_world", ctypes.c_int),
+                ("gen_lo", ctypes.c_int64), ("gen_hi", ctypes.c_int64),
+                ("comm_lo", ctypes.c_int64), ("comm_hi", ctypes.c_int64)]
 
 
 class FlowOpts(ctypes.Structure):
@@ -56,7 +59,7 @@ class FlowOpts(ctypes.Structure):
                 ("ds", ctypes.c_double), ("rtol", ctypes.c_double), ("atol", ctypes.c_double),
                 ("max_steps", ctypes.c_int64), ("replay_steps", ctypes.POINTER(ctypes.c_double)),
                 ("n_replay", ctypes.c_int64), ("record_steps", ctypes.POINTER(ctypes.c_double)),
-                ("record_cap", ctypes.c_int64)]
+                ("record_cap", ctypes.c_int64), ("batch_record_steps", ctypes.c_void_p)]
 
 
 class FlowStats(ctypes.Structure):
@@ -99,6 +102,12 @@ def lib():
         "cut_flow": (st, [VP, VP, i, VP, ctypes.POINTER(FlowOpts), ctypes.POINTER(FlowStats), VP]),
         "cut_flow_vjp": (st, [VP, VP, i, VP, ctypes.POINTER(FlowOpts), i, VP, VP, VP, VP, VP]),
         "cut_flow_batched": (st, [VP, i, VP, i, VP, i, ctypes.POINTER(FlowOpts), i, VP, VP, VP]),
+        "cut_graph_partition": (st, [VP, i, i, VP]),
+        "cut_graph_load_shard": (st, [ctypes.c_char_p, i, i, i, ctypes.c_uint, ctypes.POINTER(VP)]),
+        "cut_shard_generator": (st, [VP, VP, VP, VP]),
+        "cut_shard_commutator": (st, [VP, VP, i, VP, VP, VP]),
+        "cut_combine": (st, [i64, VP, i, VP, VP, ctypes.c_double, VP, VP]),
+        "cut_measure_fma_rate": (st, [i, i, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
         "cut_mlp_create": (st, [i, i, i, ctypes.c_uint64, i, ctypes.POINTER(VP)]),
         "cut_mlp_free": (st, [VP]),
         "cut_mlp_set_output_affine": (st, [VP, VP, VP]),
@@ -111,6 +120,7 @@ def lib():
         "cut_mlp_adamw_step": (st, [VP, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                     ctypes.c_float, VP]),
         "cut_mlp_status": (st, [VP]),
+        "cut_mlp_inject_stall": (st, [VP, i]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -123,6 +133,13 @@ def lib():
 def check(status):
     if status != 0:
         raise CutError(status, lib().cut_last_error().decode())
+
+
+def measure_fma_rate(device=0, fp64=True, seconds=0.5):
+    """Measured FMA throughput of a device in TFLOP/s (FP64 or FP32)."""
+    out = ctypes.c_double(0.0)
+    check(lib().cut_measure_fma_rate(int(device), 1 if fp64 else 0, float(seconds), ctypes.byref(out)))
+    return out.value
 
 
 def build_graph(algebra, nmodes, labels, path, max_rank=0, threads=0, diagnostics=False):
@@ -176,6 +193,7 @@ class Graph:
     def __init__(self, path, device=0):
         self._h = VP()
         check(lib().cut_graph_load(os.fsencode(path), int(device), 0, ctypes.byref(self._h)))
+        self.path = path
         self.device_index = int(device)
         d = GraphDesc()
         check(lib().cut_graph_query(self._h, ctypes.byref(d)))
@@ -350,8 +368,12 @@ class Graph:
         return gh, (list(gx) if n_obs else [])
 
     def flow_batched(self, H, Xs=None, precision="fp64", method="dp45", s0=0.0, s1=10.0, ds=1e-2,
-                     rtol=1e-10, atol=0.0, max_steps=0, tile=0, stream=None):
-        """Flows of many coefficient sets through one graph: H [B, n], Xs [B, n_obs, n]."""
+                     rtol=1e-10, atol=0.0, max_steps=0, tile=0, record_cap=0, stream=None):
+        """Flows of many coefficient sets through one graph: H [B, n], Xs [B, n_obs, n].
+
+        Returns (H, X, steps, status); with record_cap > 0 also a [B, record_cap]
+        FP64 device tensor whose row b holds instance b's accepted step sizes
+        (the first steps[b] entries, the rest zero)."""
         torch = _torch()
         H = _dev_f64(H, self.n, "H", self.device).clone()
         B = H.shape[0]
@@ -360,10 +382,15 @@ class Graph:
         steps = torch.zeros(B, dtype=torch.int32, device=self.device)
         status = torch.zeros(B, dtype=torch.int32, device=self.device)
         o, keep, _ = self._opts(method, s0, s1, ds, rtol, atol, max_steps, None, 0)
+        rec = None
+        if record_cap:
+            rec = torch.zeros(B, int(record_cap), dtype=torch.float64, device=self.device)
+            o.record_cap = int(record_cap)
+            o.batch_record_steps = rec.data_ptr()
         prec = FP64 if precision == "fp64" else FP32REC_FP64STATE
         check(lib().cut_flow_batched(self._h, B, _ptr(H), n_obs, _ptr(X), prec, ctypes.byref(o),
                                      int(tile), _ptr(steps), _ptr(status), _stream(stream)))
-        return H, X, steps, status
+        return (H, X, steps, status) if rec is None else (H, X, steps, status, rec)
 
 
 class MLP:
@@ -448,3 +475,7 @@ class MLP:
 
     def status(self):
         check(lib().cut_mlp_status(self._h))
+
+    def inject_stall(self, on):
+        """Test hook: make every GEMM's pipeline wait run out (see cut.h)."""
+        check(lib().cut_mlp_inject_stall(self._h, 1 if on else 0))

@@ -7,7 +7,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libcut.so")
-SOURCES = ["cut_lib.cu", "batched.cu", "mlp.cu", "builder.cpp", "bundle.cpp"]
+SOURCES = ["cut_lib.cu", "batched.cu", "mlp.cu", "calib.cu", "builder.cpp", "bundle.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

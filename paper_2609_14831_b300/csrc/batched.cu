@@ -60,6 +60,8 @@ struct Args {
     double s0, s1, ds0, rtol, atol;
     long long max_steps;        // attempts per instance
     long long probe_attempts;   // > 0: stop every CTA after that many attempts (autotuning)
+    double *record;             // [B][record_cap] accepted step sizes of each instance, or null
+    long long record_cap;
     Tableau tb;
 };
 
@@ -427,6 +429,7 @@ __global__ void __launch_bounds__(kThreads, 1) flow_batched_kernel(Args a) {
                     status[t] = CUT_ERR_NONFINITE;
                     done = 1;
                 } else if (!tb.adaptive) {
+                    if (a.record && steps_[t] < a.record_cap) a.record[inst[t] * a.record_cap + steps_[t]] = ds_[t];
                     acc_flag[t] = 1;
                     steps_[t]++;
                     s_[t] = a.s0 + (double)steps_[t] * ds_[t];
@@ -436,7 +439,12 @@ __global__ void __launch_bounds__(kThreads, 1) flow_batched_kernel(Args a) {
                     double fac;
                     if (accept) fac = r == 0.0 ? 5.0 : fmin(5.0, fmax(0.2, 0.9 * pow(r, -0.2)));
                     else fac = fmin(1.0, fmax(0.2, 0.9 * pow(r, -0.2)));
-                    if (accept) { s_[t] += ds_[t]; steps_[t]++; acc_flag[t] = 1; }
+                    if (accept) {
+                        if (a.record && steps_[t] < a.record_cap) a.record[inst[t] * a.record_cap + steps_[t]] = ds_[t];
+                        s_[t] += ds_[t];
+                        steps_[t]++;
+                        acc_flag[t] = 1;
+                    }
                     double ds = ds_[t] * fac;
                     if (!(s_[t] < a.s1)) done = 1;
                     else {
@@ -645,6 +653,10 @@ cut_status flow_batched_impl(const BatchedGraphView &v, int device, int batch, d
     a.nops = nops; a.B = batch;
     a.s0 = o->s0; a.s1 = o->s1; a.rtol = o->rtol; a.atol = o->atol;
     a.tb = make_tableau(o->method);
+    if (o->batch_record_steps && o->record_cap > 0) {
+        a.record = o->batch_record_steps;
+        a.record_cap = o->record_cap;
+    }
     if (o->method == CUT_RK4) {
         int64_t N = (int64_t)llround((o->s1 - o->s0) / o->ds);
         if (N < 1) N = 1;

@@ -25,18 +25,24 @@ cut_status set_error(cut_status s, const std::string &msg) {
 }
 cut_status set_ok() { return CUT_OK; }
 
+// On failure: report, and clear the runtime's record of a non-sticky error
+// (an allocation that did not fit) so that later calls start clean.
 #define CUDA_TRY(expr)                                                                          \
     do {                                                                                        \
         cudaError_t _e = (expr);                                                                \
-        if (_e != cudaSuccess)                                                                  \
+        if (_e != cudaSuccess) {                                                                \
+            (void)cudaGetLastError();                                                           \
             return set_error(_e == cudaErrorMemoryAllocation ? CUT_ERR_OUT_OF_MEMORY : CUT_ERR_CUDA, \
                              std::string(#expr) + ": " + cudaGetErrorString(_e));               \
+        }                                                                                       \
     } while (0)
 
 struct DevCSR {
     uint64_t *rp = nullptr;
     uint2 *rec = nullptr;
     int64_t rows = 0, R = 0;
+    int64_t lane_rows = 0;   // rows of the whole stage: picks the lanes per row, so
+                             // a shard sums each row exactly as the whole graph does
 };
 
 }  // namespace cut
@@ -54,6 +60,8 @@ struct cut_graph {
     int wuniform = 0;
     uint32_t wnegmask = 0;         // bit c set when factor c < 0 (codes < 32)
     int arith = CUT_ARITH_FP64;    // arithmetic of the commutator stage
+    int shard_rank = 0, shard_world = 0;   // world > 0: only rows [lo, hi) of stages 0, 1 resident
+    int64_t lo[2] = {0, 0}, hi[2] = {0, 0};
     int64_t device_bytes = 0;
     std::mutex mu;
     ~cut_graph() {
@@ -99,6 +107,7 @@ static int grid_for_len(int64_t len) {
 static cut_status upload_csr(DevCSR &d, const std::vector<uint64_t> &rp, const std::vector<uint32_t> &rec,
                              int64_t &bytes) {
     d.rows = (int64_t)rp.size() - 1;
+    d.lane_rows = d.rows;
     d.R = (int64_t)rec.size() / 2;
     CUDA_TRY(cudaMalloc(&d.rp, rp.size() * 8));
     CUDA_TRY(cudaMemcpy(d.rp, rp.data(), rp.size() * 8, cudaMemcpyHostToDevice));
@@ -108,6 +117,17 @@ static cut_status upload_csr(DevCSR &d, const std::vector<uint64_t> &rp, const s
     bytes += (int64_t)(rp.size() * 8 + rec.size() * 4);
     return CUT_OK;
 }
+
+static cut_status upload_weights(cut_graph *g);
+
+// Entry points that traverse the whole graph refuse a shard handle.
+static cut_status whole_graph(const cut_graph *g, const char *fn) {
+    if (g && g->shard_world > 0)
+        return set_error(CUT_ERR_INVALID_ARG, std::string(fn) + ": the handle holds one shard of the graph; use the "
+                                                                "cut_shard_* entry points");
+    return CUT_OK;
+}
+
 
 // ----------------------------------------------------------------- RHS core
 // dx_o (o < nops) for operands x_o, given xi; operands processed 4 at a time.
@@ -163,7 +183,7 @@ static void launch_comm(const cut_graph *g, const double *xi, int nops, const do
                         double *X4 = nullptr) {
     const DevCSR &c = g->st[stage];
     const k::Weights w = weights_of(g);
-    const int lanes = comm_lanes(c.rows);
+    const int lanes = comm_lanes(c.lane_rows);
     if (X4 && nops <= 8) {
         const int64_t n = g->host.n();
         for (int o0 = 0; o0 < nops; o0 += 8) {
@@ -213,7 +233,7 @@ static void gen_launch(const DevCSR &c, const k::Weights &w, const double *h, do
 static void launch_gen(const cut_graph *g, const double *h, double *xi, cudaStream_t s, const int *done) {
     const DevCSR &c = g->st[0];
     const k::Weights w = weights_of(g);
-    if (gen_lanes(c.rows) == 4) gen_launch<4>(c, w, h, xi, s, done);
+    if (gen_lanes(c.lane_rows) == 4) gen_launch<4>(c, w, h, xi, s, done);
     else gen_launch<8>(c, w, h, xi, s, done);
 }
 
@@ -224,7 +244,7 @@ static void launch_comm_df(const cut_graph *g, const double *xi, float2 *xi2, fl
     const DevCSR &c = g->st[1];
     const int64_t n = g->host.n(), ng = g->host.n_g();
     const k::Weights w = weights_of(g);
-    const int lanes = comm_lanes(c.rows);
+    const int lanes = comm_lanes(c.lane_rows);
     const int grid = grid_for_groups(c.rows, lanes);
     if (ng > 0) k::split_pairs<<<grid_for_len(ng), 256, 0, s>>>(xi, ng, xi2, 1, 0, done);
     for (int o0 = 0; o0 < nops; o0 += 3) {
@@ -320,6 +340,19 @@ cut_status cut_graph_load(const char *path, int device, unsigned flags, cut_grap
         cut_status st = upload_csr(g->st[s], g->host.rp[s], g->host.rec[s], bytes);
         if (st != CUT_OK) return st;
     }
+    cut_status st = upload_weights(g.get());
+    if (st != CUT_OK) return st;
+    g->device_bytes += bytes;
+    *out = g.release();
+    return set_ok();
+}
+
+}  // extern "C"
+
+namespace cut {
+// The exact factors as doubles, FP32 and sign bits on the graph's device
+// (current device), and the uniform-magnitude flags.
+static cut_status upload_weights(cut_graph *g) {
     std::vector<double> w(g->host.num.size());
     std::vector<float> w32(w.size());
     std::vector<unsigned long long> sg(w.size());
@@ -338,10 +371,12 @@ cut_status cut_graph_load(const char *path, int device, unsigned flags, cut_grap
     CUDA_TRY(cudaMemcpy(g->wtab, w.data(), w.size() * 8, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMalloc(&g->wtab32, w.size() * 4));
     CUDA_TRY(cudaMemcpy(g->wtab32, w32.data(), w.size() * 4, cudaMemcpyHostToDevice));
-    g->device_bytes = bytes + (int64_t)w.size() * 12;
-    *out = g.release();
-    return set_ok();
+    g->device_bytes += (int64_t)w.size() * 20;
+    return CUT_OK;
 }
+}  // namespace cut
+
+extern "C" {
 
 cut_status cut_graph_free(cut_graph *g) {
     delete g;
@@ -364,6 +399,12 @@ cut_status cut_graph_query(const cut_graph *g, cut_graph_desc *out) {
     out->record_bytes = 8;
     out->n_out = g->host.n_out();
     out->R_C = g->st[2].R;
+    out->shard_rank = g->shard_rank;
+    out->shard_world = g->shard_world;
+    out->gen_lo = g->shard_world ? g->lo[0] : 0;
+    out->gen_hi = g->shard_world ? g->hi[0] : g->host.n_g();
+    out->comm_lo = g->shard_world ? g->lo[1] : 0;
+    out->comm_hi = g->shard_world ? g->hi[1] : g->host.n();
     return set_ok();
 }
 
@@ -375,6 +416,7 @@ cut_status cut_graph_outside_labels(const cut_graph *g, uint64_t *out) {
 
 cut_status cut_rhs_outside(const cut_graph *g, const double *h, int n_obs, const double *x, double *c,
                            cut_stream_t stream) {
+    if (whole_graph(g, "cut_rhs_outside") != CUT_OK) return CUT_ERR_INVALID_ARG;
     if (!g || g->device < 0 || !h || !c || n_obs < 0 || n_obs > 63 || (n_obs > 0 && !x))
         return set_error(CUT_ERR_INVALID_ARG, "cut_rhs_outside: bad argument");
     if (g->host.n_out() == 0)
@@ -429,6 +471,7 @@ cut_status cut_graph_records(const cut_graph *g, int stage, int64_t *row_ptr, in
 
 cut_status cut_rhs(const cut_graph *g, const double *h, int n_obs, const double *x, double *dh, double *dx,
                    double *xi_out, cut_stream_t stream) {
+    if (whole_graph(g, "cut_rhs") != CUT_OK) return CUT_ERR_INVALID_ARG;
     if (!g || g->device < 0 || !h || !dh || n_obs < 0 || n_obs > 63 || (n_obs > 0 && (!x || !dx)))
         return set_error(CUT_ERR_INVALID_ARG, "cut_rhs: bad argument");
     DeviceGuard dg(g->device);
@@ -462,6 +505,7 @@ cut_status cut_graph_set_arithmetic(cut_graph *g, int arith) {
 
 cut_status cut_apply_L(const cut_graph *g, const double *xi, int n_ops, const double *x, double *dx,
                        cut_stream_t stream) {
+    if (whole_graph(g, "cut_apply_L") != CUT_OK) return CUT_ERR_INVALID_ARG;
     if (!g || g->device < 0 || !xi || n_ops < 1 || n_ops > 64 || !x || !dx)
         return set_error(CUT_ERR_INVALID_ARG, "cut_apply_L: bad argument");
     DeviceGuard dg(g->device);
@@ -498,6 +542,7 @@ extern "C" cut_status cut_assemble(int n_src, int64_t n, const double *X, int n_
 // ----------------------------------------------------------------- tangent
 extern "C" cut_status cut_rhs_jvp(const cut_graph *g, const double *h, int n_obs, const double *x, const double *dh,
                                   const double *dx, double *out_h, double *out_x, cut_stream_t stream) {
+    if (whole_graph(g, "cut_rhs_jvp") != CUT_OK) return CUT_ERR_INVALID_ARG;
     if (!g || g->device < 0 || !h || !dh || !out_h || n_obs < 0 || n_obs > 63 ||
         (n_obs > 0 && (!x || !dx || !out_x)))
         return set_error(CUT_ERR_INVALID_ARG, "cut_rhs_jvp: bad argument");
@@ -658,6 +703,7 @@ static void stacked_vjp(const cut_graph *g, const double *Y, const double *W, do
 extern "C" cut_status cut_rhs_adjoint(const cut_graph *g, const double *h, int n_obs, const double *x,
                                       const double *w_h, const double *w_x, double *h_bar, double *x_bar,
                                       cut_stream_t stream) {
+    if (whole_graph(g, "cut_rhs_adjoint") != CUT_OK) return CUT_ERR_INVALID_ARG;
     if (!g || g->device < 0 || !h || !w_h || !h_bar || n_obs < 0 || n_obs > 63 || (n_obs > 0 && (!x || !w_x || !x_bar)))
         return set_error(CUT_ERR_INVALID_ARG, "cut_rhs_adjoint: bad argument");
     DeviceGuard dg(g->device);
@@ -843,6 +889,7 @@ static int64_t rk4_nsteps(const cut_flow_opts *o, double *ds_eff) {
 
 extern "C" cut_status cut_flow(const cut_graph *g, double *h, int n_obs, double *x, const cut_flow_opts *o,
                                cut_flow_stats *stats, cut_stream_t stream) {
+    if (whole_graph(g, "cut_flow") != CUT_OK) return CUT_ERR_INVALID_ARG;
     if (!g || g->device < 0 || !h || n_obs < 0 || n_obs > 63 || (n_obs > 0 && !x)) return set_error(CUT_ERR_INVALID_ARG, "cut_flow: bad argument");
     cut_status st = check_opts(o);
     if (st != CUT_OK) return st;
@@ -949,6 +996,7 @@ extern "C" cut_status cut_flow(const cut_graph *g, double *h, int n_obs, double 
 extern "C" cut_status cut_flow_vjp(const cut_graph *g, const double *h0, int n_obs, const double *x0,
                                    const cut_flow_opts *o, int checkpoint_every, const double *yb_h,
                                    const double *yb_x, double *gh, double *gx, cut_stream_t stream) {
+    if (whole_graph(g, "cut_flow_vjp") != CUT_OK) return CUT_ERR_INVALID_ARG;
     if (!g || g->device < 0 || !h0 || !yb_h || !gh || n_obs < 0 || n_obs > 63 || (n_obs > 0 && (!x0 || !yb_x || !gx)) ||
         checkpoint_every < 1)
         return set_error(CUT_ERR_INVALID_ARG, "cut_flow_vjp: bad argument");
@@ -995,7 +1043,12 @@ extern "C" cut_status cut_flow_vjp(const cut_graph *g, const double *h0, int n_o
     double *buf = nullptr;
     size_t tot = (size_t)(ncp + (C + 1) + 3 * S + 3) * L + 2 * ng + n;
     cudaError_t e = cudaMallocAsync(&buf, tot * 8, s);
-    if (e != cudaSuccess) { end_work(sp); return set_error(CUT_ERR_OUT_OF_MEMORY, "cut_flow_vjp: workspace"); }
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        end_work(sp);
+        return set_error(CUT_ERR_OUT_OF_MEMORY, "cut_flow_vjp: workspace of " + std::to_string(tot * 8) +
+                                                    " bytes: " + cudaGetErrorString(e));
+    }
     double *cp = buf, *seg = cp + ncp * L, *U = seg + (C + 1) * L, *K = U + S * L, *KB = K + S * L;
     double *yb = KB + S * L, *ub = yb + L, *ybn = ub + L, *xi = ybn + L, *xib = xi + ng, *xb0 = xib + ng;
     cudaMemcpyAsync(cp, h0, n * 8, cudaMemcpyDeviceToDevice, s);
@@ -1094,6 +1147,7 @@ static thread_local int g_last_tile = 0;
 extern "C" cut_status cut_flow_batched(const cut_graph *g, int batch, double *h, int n_obs, double *x, int precision,
                                        const cut_flow_opts *o, int tile, int *steps_out, int *status_out,
                                        cut_stream_t stream) {
+    if (whole_graph(g, "cut_flow_batched") != CUT_OK) return CUT_ERR_INVALID_ARG;
     if (!g || g->device < 0 || batch < 1 || !h || n_obs < 0 || n_obs > 3 || (n_obs > 0 && !x) || !steps_out ||
         !status_out || (precision != CUT_FP64 && precision != CUT_FP32REC_FP64STATE) || tile < 0)
         return set_error(CUT_ERR_INVALID_ARG, "cut_flow_batched: bad argument (n_obs <= 3)");
@@ -1118,18 +1172,40 @@ static __device__ __align__(256) double g_noalloc_xi[kNoAllocMaxGen];
 
 static std::mutex g_noalloc_mu;
 static double *g_noalloc_ptr[256] = {nullptr};
+static void *g_noalloc_ctx[256] = {nullptr};   // context the address belongs to
 
-// Device address of the scratch array on the current device, looked up once
-// per device (the host-side name of the array is not a device address).
+// The calling thread's current CUDA context (driver entry point reached
+// through the runtime, so the library does not link libcuda directly).
+static void *current_context() {
+    typedef int (*CtxGetCurrent)(void **);
+    static CtxGetCurrent fn = []() -> CtxGetCurrent {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return (CtxGetCurrent)f;
+    }();
+    void *ctx = nullptr;
+    if (fn) fn(&ctx);
+    return ctx;
+}
+
+// Device address of the scratch array in the current device's context,
+// looked up once per device and context (the host-side name of the array is
+// not a device address; a device reset or another context makes a new
+// lookup).
 static cut_status noalloc_scratch(int device, double **out) {
     if (device < 0 || device >= 256) return set_error(CUT_ERR_INVALID_ARG, "cut_rhs_noalloc: device index out of range");
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[device]) {
+    void *ctx = current_context();
+    if (!g_noalloc_ptr[device] || !ctx || ctx != g_noalloc_ctx[device]) {
         void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_xi);
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_xi);   // creates the context if needed
         if (e != cudaSuccess || !p)
             return set_error(CUT_ERR_CUDA, std::string("cut_rhs_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
         g_noalloc_ptr[device] = (double *)p;
+        g_noalloc_ctx[device] = current_context();
     }
     *out = g_noalloc_ptr[device];
     return CUT_OK;
@@ -1139,6 +1215,7 @@ static cut_status noalloc_scratch(int device, double **out) {
 
 extern "C" cut_status cut_rhs_noalloc(const cut_graph *g, const double *h, int n_obs, const double *x, double *dh,
                                       double *dx, cut_stream_t stream) {
+    if (whole_graph(g, "cut_rhs_noalloc") != CUT_OK) return CUT_ERR_INVALID_ARG;
     if (!g || g->device < 0 || !h || !dh || n_obs < 0 || n_obs > 63 || (n_obs > 0 && (!x || !dx)))
         return set_error(CUT_ERR_INVALID_ARG, "cut_rhs_noalloc: bad argument");
     if (g->host.n_g() > kNoAllocMaxGen)
@@ -1160,6 +1237,132 @@ extern "C" cut_status cut_rhs_noalloc(const cut_graph *g, const double *h, int n
     dxs[0] = dh;
     for (int o = 0; o < n_obs; o++) { xs[o + 1] = x + o * n; dxs[o + 1] = dx + o * n; }
     launch_comm(g, xi, n_obs + 1, xs, dxs, s, nullptr);
+    CUDA_TRY(cudaGetLastError());
+    return set_ok();
+}
+
+// ----------------------------------------------------------------- target-range shards
+// Sec. 2.2: records are grouped by output, so the outputs of each stage can
+// be split into contiguous ranges that hold about equal numbers of records;
+// a rank holding one range of each stage computes its generator
+// coordinates and its outputs from full input vectors, and the ranks
+// exchange those pieces (an all-gather of xi, then of the right-hand side).
+namespace cut {
+
+// bounds[0..parts]: row r of the stage goes to part p when
+// bounds[p] <= r < bounds[p+1]; part p starts at the first row whose record
+// offset reaches p R / parts (deterministic, independent of the caller).
+static void partition_rows(const std::vector<uint64_t> &rp, int parts, int64_t *bounds) {
+    const int64_t rows = (int64_t)rp.size() - 1;
+    const uint64_t R = rows > 0 ? rp[rows] : 0;
+    bounds[0] = 0;
+    for (int p = 1; p < parts; p++) {
+        const uint64_t target = (uint64_t)(((unsigned __int128)R * (unsigned)p) / (unsigned)parts);
+        int64_t b = (int64_t)(std::lower_bound(rp.begin(), rp.end(), target) - rp.begin());
+        b = std::min(b, rows);
+        bounds[p] = std::max(b, bounds[p - 1]);
+    }
+    bounds[parts] = std::max<int64_t>(rows, 0);
+}
+
+// the rows [lo, hi) of a stage, row pointers rebased to start at 0
+static cut_status upload_rows(DevCSR &d, const std::vector<uint64_t> &rp, const std::vector<uint32_t> &rec,
+                              int64_t lo, int64_t hi, int64_t &bytes) {
+    std::vector<uint64_t> lrp(hi - lo + 1);
+    for (int64_t r = lo; r <= hi; r++) lrp[r - lo] = rp[r] - rp[lo];
+    std::vector<uint32_t> lrec(rec.begin() + 2 * rp[lo], rec.begin() + 2 * rp[hi]);
+    cut_status st = upload_csr(d, lrp, lrec, bytes);
+    d.lane_rows = (int64_t)rp.size() - 1;
+    return st;
+}
+
+}  // namespace cut
+
+extern "C" cut_status cut_graph_partition(const cut_graph *g, int stage, int parts, int64_t *bounds) {
+    if (!g || stage < 0 || stage > 1 || parts < 1 || parts > 65536 || !bounds)
+        return set_error(CUT_ERR_INVALID_ARG, "cut_graph_partition: bad argument");
+    if (g->shard_world > 0 || g->host.rp[stage].empty())
+        return set_error(CUT_ERR_INVALID_ARG, "cut_graph_partition: needs a handle of the whole graph");
+    partition_rows(g->host.rp[stage], parts, bounds);
+    return set_ok();
+}
+
+extern "C" cut_status cut_graph_load_shard(const char *path, int device, int rank, int world, unsigned flags,
+                                           cut_graph **out) {
+    if (!path || !out || device < 0 || world < 1 || world > 65536 || rank < 0 || rank >= world || flags != 0)
+        return set_error(CUT_ERR_INVALID_ARG, "cut_graph_load_shard: bad argument");
+    *out = nullptr;
+    int ndev = 0;
+    CUDA_TRY(cudaGetDeviceCount(&ndev));
+    if (device >= ndev) return set_error(CUT_ERR_INVALID_ARG, "cut_graph_load_shard: bad device");
+    std::unique_ptr<cut_graph> g(new cut_graph());
+    g->device = device;
+    std::string err;
+    int rc = read_bundle(path, g->host, &err);
+    if (rc != 0) return set_error((cut_status)rc, "cut_graph_load_shard: " + err);
+    DeviceGuard dg(device);
+    int64_t bytes = 0;
+    std::vector<int64_t> b(world + 1);
+    for (int s = 0; s < 2; s++) {
+        partition_rows(g->host.rp[s], world, b.data());
+        g->lo[s] = b[rank];
+        g->hi[s] = b[rank + 1];
+        cut_status st = upload_rows(g->st[s], g->host.rp[s], g->host.rec[s], g->lo[s], g->hi[s], bytes);
+        if (st != CUT_OK) return st;
+    }
+    cut_status st = upload_weights(g.get());
+    if (st != CUT_OK) return st;
+    g->device_bytes += bytes;
+    g->shard_rank = rank;
+    g->shard_world = world;
+    *out = g.release();
+    return set_ok();
+}
+
+extern "C" cut_status cut_shard_generator(const cut_graph *g, const double *h, double *xi_part, cut_stream_t stream) {
+    if (!g || g->device < 0 || g->shard_world < 1 || !h || (!xi_part && g->hi[0] > g->lo[0]))
+        return set_error(CUT_ERR_INVALID_ARG, "cut_shard_generator: bad argument (needs a shard handle)");
+    if (g->hi[0] == g->lo[0]) return set_ok();
+    DeviceGuard dg(g->device);
+    launch_gen(g, h, xi_part, (cudaStream_t)stream, nullptr);
+    CUDA_TRY(cudaGetLastError());
+    return set_ok();
+}
+
+extern "C" cut_status cut_shard_commutator(const cut_graph *g, const double *xi, int n_ops, const double *x,
+                                           double *dx_part, cut_stream_t stream) {
+    if (!g || g->device < 0 || g->shard_world < 1 || !xi || n_ops < 1 || n_ops > 64 || !x ||
+        (!dx_part && g->hi[1] > g->lo[1]))
+        return set_error(CUT_ERR_INVALID_ARG, "cut_shard_commutator: bad argument (needs a shard handle)");
+    const int64_t rows = g->hi[1] - g->lo[1];
+    if (rows == 0) return set_ok();
+    DeviceGuard dg(g->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = g->host.n();
+    void *df = nullptr;
+    CUDA_TRY(cudaMallocAsync(&df, operand_scratch_bytes(g), s));
+    const double *xs[64];
+    double *dxs[64];
+    for (int o = 0; o < n_ops; o++) { xs[o] = x + o * n; dxs[o] = dx_part + o * rows; }
+    apply_L(g, xi, (float2 *)df, operand_blocks(g, df), n_ops, xs, dxs, s, nullptr);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaFreeAsync(df, s));
+    return set_ok();
+}
+
+extern "C" cut_status cut_combine(int64_t len, const double *base, int nk, const double *const *K, const double *c,
+                                  double ds, double *out, cut_stream_t stream) {
+    if (len < 0 || !base || !out || nk < 0 || nk > 7 || (nk > 0 && (!K || !c)))
+        return set_error(CUT_ERR_INVALID_ARG, "cut_combine: bad argument (nk <= 7)");
+    if (len == 0) return set_ok();
+    k::Combine cb;
+    cb.base = base;
+    cb.nk = 0;
+    for (int s = 0; s < nk; s++) {
+        if (!K[s]) return set_error(CUT_ERR_INVALID_ARG, "cut_combine: null slope");
+        if (c[s] != 0.0) { cb.K[cb.nk] = K[s]; cb.c[cb.nk] = c[s]; cb.nk++; }
+    }
+    k::rk_combine<<<grid_for_len(len), 256, 0, (cudaStream_t)stream>>>(cb, out, len, nullptr, ds, nullptr);
     CUDA_TRY(cudaGetLastError());
     return set_ok();
 }

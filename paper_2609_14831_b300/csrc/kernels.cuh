@@ -1,8 +1,8 @@
 // kernels.cuh -- sm_103a kernels of the graph traversals (paper Eq.
 // graph-actions and Sec. 2.4).
 //
-// Records of one output form a contiguous CSR segment (Sec. 2.2: "records
-// that contribute to the same output are stored together").  One warp owns a
+// Records of one output form a contiguous CSR segment (Sec. 2.2, records
+// grouped by output).  One warp (or a fixed group of its lanes) owns a
 // segment: its lanes stream the packed 8-byte records with coalesced loads,
 // multiply the exact factor by the gathered coefficients, and the partial
 // sums meet in a warp-shuffle reduction.  Nothing is scattered and nothing

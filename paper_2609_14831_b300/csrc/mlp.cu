@@ -257,6 +257,7 @@ static tc::Epi epi0(int M, int N, int *err) {
     e.M = M;
     e.N = N;
     e.err = err;
+    e.stall = err + 1;   // err[1]: the injection flag of cut_mlp_inject_stall
     return e;
 }
 
@@ -669,7 +670,21 @@ cut_status cut_mlp_status(cut_mlp *m) {
     int h = 0;
     cudaError_t e = cudaMemcpy(&h, m->err, 4, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return set_error(CUT_ERR_CUDA, std::string("cut_mlp_status: ") + cudaGetErrorString(e));
-    if (h) return set_error(CUT_ERR_TIMEOUT, "cut_mlp: a tensor-core pipeline wait timed out");
+    if (h) {
+        const int zero = 0;   // reported once: later calls start clean
+        cudaMemcpy(m->err, &zero, 4, cudaMemcpyHostToDevice);
+        return set_error(CUT_ERR_TIMEOUT, "cut_mlp: a tensor-core pipeline wait timed out");
+    }
+    return set_ok();
+}
+
+cut_status cut_mlp_inject_stall(cut_mlp *m, int on) {
+    if (!m) return set_error(CUT_ERR_INVALID_ARG, "cut_mlp_inject_stall: null");
+    cudaSetDevice(m->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    const int v = on ? 1 : 0;
+    if (e == cudaSuccess) e = cudaMemcpy(m->err + 1, &v, 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return set_error(CUT_ERR_CUDA, std::string("cut_mlp_inject_stall: ") + cudaGetErrorString(e));
     return set_ok();
 }
 

@@ -29,6 +29,7 @@ constexpr int BK = 64;          // one 128-byte swizzle row of BF16
 constexpr int STAGES = 3;          // 97 KB of ring at BN = 128: two CTAs per SM
 constexpr int kThreads = 256;          // 8 warps: two per TMEM lane quarter share the epilogue
 constexpr long long kSpinLimit = 1ll << 26;
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;   // a pipeline wait gives up after 1 s
 
 struct Epi {
     const float *bias;          // [N] or null
@@ -49,6 +50,9 @@ struct Epi {
     int ld_t;
     int M, N;                   // valid extent (rows, columns) written
     int *err;                   // set to 1 when a wait timed out
+    const int *stall;           // failure injection for tests: while *stall != 0 the
+                                // producer issues no operand copies, so the MMA
+                                // issuer's wait runs out (no fault, no hang)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -64,9 +68,17 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
                  : "memory");
 }
 
-// Bounded wait on the phase with the given parity; false on timeout.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait on the phase with the given parity; false once it has waited
+// kWaitLimitNs (or kSpinLimit polls), whichever comes first.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
     const uint32_t a = smem_u32(bar);
+    unsigned long long t0 = 0;
     for (long long it = 0; it < kSpinLimit; it++) {
         uint32_t ok;
         asm volatile(
@@ -77,6 +89,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
             : "r"(a), "r"(parity)
             : "memory");
         if (ok) return true;
+        if ((it & 255) == 0) {
+            const unsigned long long t = global_ns();
+            if (it == 0) t0 = t;
+            else if (t - t0 > kWaitLimitNs) return false;
+        }
     }
     return false;
 }
@@ -162,7 +179,8 @@ __global__ void __launch_bounds__(kThreads, 2)
     int issued = 0;
     if (warp == 0 && lane == 0) {
         // producer
-        for (int kt = 0; kt < KT && !failed; kt++) {
+        const bool stall = ep.stall && *ep.stall;
+        for (int kt = 0; kt < KT && !failed && !stall; kt++) {
             const int s = kt % STAGES;
             if (kt >= STAGES && !mbar_wait(&empty[s], ((kt / STAGES) - 1) & 1)) { failed = 1; break; }
             mbar_expect_tx(&full[s], A_BYTES + B_BYTES);

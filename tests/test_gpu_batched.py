@@ -188,3 +188,80 @@ def test_batched_fp32_operand_layouts(n_obs):
         a, b = np64(a), np64(b)
         err = np.max(np.abs(a - b)) / np.max(np.abs(b))
         assert err < 1e-5, err
+
+
+def _sector_replay(labels, h0, D0, steps, N):
+    """Dense Wegner flow of the N-particle block of (H, D) along the given
+    accepted Dormand-Prince steps (the oracle's tableau).  Rank-3 terms
+    annihilate every state with at most two particles, so the projected
+    flow of the <=2-body registry is this flow exactly (pinned on CPU by
+    test_oracle_pins.test_fermion_flow_matches_sector_wegner_flows)."""
+    import dense
+    A, B = oracle.DP_A[:6], oracle.DP_B[:6]
+
+    def f(Y):
+        dB, eta = dense.wegner_rhs(Y[0])
+        return np.stack([dB, eta @ Y[1] - Y[1] @ eta])
+    Y = np.stack([dense.sector_matrix(labels, h0, 8, N), dense.sector_matrix(labels, D0, 8, N)])
+    for ds in steps:
+        Y = dense.rk_dense(f, Y, ds, A, B)
+    return Y
+
+
+def test_batched_full_size_dp45_matches_oracle_replay():
+    """The benchmarked batch itself: 8 spin-orbitals, 1024 parameter sets,
+    H + N + D, DP45 rtol 1e-10 to s = 10, FP64.  Four instances spread over
+    the batch replay their own recorded accepted steps in the oracle's
+    Dormand-Prince tableau on the dense N=1 and N=2 blocks, and must agree
+    element by element at 1e-10 of the block's largest entry.  Over a short
+    span one instance of the same batch is also replayed through the
+    string-algebra oracle itself.  The FP32-record batch (rtol 1e-6) is then compared with
+    this FP64 batch instance by instance; its error is stated per result."""
+    import torch
+    import dense
+    w = workload("molecular_8so")
+    B = 1024
+    H = batched_parameters(w.labels, 8, B, seed=3)
+    X = np.stack([np.stack(w.observables)] * B)
+    G = graph_for("mol8", w.alg, w.nmodes, w.labels)
+    H64, X64, st64, status, rec = G.flow_batched(torch.tensor(H), torch.tensor(X), precision="fp64",
+                                                 method="dp45", s0=0.0, s1=10.0, ds=1e-2, rtol=1e-10,
+                                                 atol=w.atol, record_cap=4096)
+    st64, rec = st64.cpu().numpy(), np64(rec)
+    assert np.all(status.cpu().numpy() == 0)
+    assert st64.max() < 4096 and len(set(st64.tolist())) > 1
+    for b in (0, 341, 682, 1023):
+        steps = rec[b, :st64[b]]
+        assert np.all(steps > 0) and np.all(rec[b, st64[b]:] == 0)
+        assert abs(steps.sum() - 10.0) < 1e-9, steps.sum()
+        np.testing.assert_array_equal(np64(X64[b, 0]), w.observables[0])     # N is carried unchanged
+        for N in (1, 2):
+            Y = _sector_replay(w.labels, H[b], w.observables[1], steps, N)
+            assert_close(dense.sector_matrix(w.labels, np64(H64[b]), 8, N), Y[0], rtol=1e-10,
+                         what=f"instance {b} H block N={N}")
+            assert_close(dense.sector_matrix(w.labels, np64(X64[b, 1]), 8, N), Y[1], rtol=1e-10,
+                         what=f"instance {b} D block N={N}")
+    # the string-algebra oracle itself, along the steps that instance 682 of
+    # the same 1024-instance batch takes over a short span (s in [0, 0.01])
+    b = 682
+    Hs, Xs, sts, status2, recs = G.flow_batched(torch.tensor(H), torch.tensor(X), precision="fp64",
+                                                method="dp45", s0=0.0, s1=0.01, ds=5e-3, rtol=1e-10,
+                                                atol=w.atol, record_cap=16)
+    assert np.all(status2.cpu().numpy() == 0)
+    steps = list(np64(recs)[b, :int(sts[b])])
+    assert 1 <= len(steps) <= 6 and abs(sum(steps) - 0.01) < 1e-15
+    f = oracle.stacked_rhs(w.alg, w.nmodes, w.labels, 2)
+    y, _, _ = oracle.dp45_flow(f, np.concatenate([H[b], X[b, 0], X[b, 1]]), 0.0, 0.01, 5e-3, 1e-10, w.atol,
+                               replay=steps)
+    n = len(w.labels)
+    assert_close(np64(Hs[b]), y[:n], what="batched h vs oracle replay")
+    assert_close(np64(Xs[b, 1]), y[2 * n:], what="batched D vs oracle replay")
+    # FP32 records against the FP64 batch, per instance
+    H32, X32, st32, status32 = G.flow_batched(torch.tensor(H), torch.tensor(X), precision="fp32", method="dp45",
+                                              s0=0.0, s1=10.0, ds=1e-2, rtol=1e-6, atol=1e-9)
+    assert np.all(status32.cpu().numpy() == 0)
+    a, r = np64(H32), np64(H64)
+    err = np.max(np.abs(a - r), axis=1) / np.max(np.abs(r), axis=1)
+    print(f"FP32-record batch vs oracle-checked FP64 batch, per instance (1024): median {np.median(err):.2e}, "
+          f"p99 {np.percentile(err, 99):.2e}, max {err.max():.2e}")
+    assert err.max() < 1e-4

@@ -63,10 +63,11 @@ def test_noalloc_rejects_host_only_handles(tmp_path):
     assert cg.lib().cut_rhs_noalloc(H._h, None, 0, None, None, None, None) == 1
 
 
-@pytest.mark.parametrize("n_obs", [3, 7])
+@pytest.mark.parametrize("n_obs", [3, 4, 7])
 def test_packed_and_unpacked_operand_gathers_give_the_same_bits(n_obs):
     """cut_rhs packs the operands of each index into 32-byte blocks (one
-    gather per block and record; 4 operands fill one block, 8 two);
+    gather per block and record; 4 operands fill one block, 5 fill one and a
+    part of a second, 8 fill two);
     cut_rhs_noalloc, which may not allocate the packing scratch, gathers each
     operand separately.  Per operand both sum the same records in the same
     order with the same FMAs: the results are equal bit for bit."""
