@@ -148,28 +148,74 @@ def _build(workload_name, seed, tmpdir, rank):
     return w, path, stats, time.time() - t0
 
 
-def cpu_sample(seconds_budget=20.0):
-    """Oracle RHS on the 7-spin-orbital stress recipe; records/s of its graph."""
+# Records of the CPU-sample graphs as cut_build compiles them (R_g + R_L);
+# tests/test_bench_host.py rebuilds both and checks these numbers, so the
+# reference arm can state its throughput in records/s without loading the
+# product library.
+SAMPLE_RECORDS = {"stress_7so": 436248, "molecular_8so": 87192}
+
+
+def _oracle_piece(args):
+    """One piece of an oracle right-hand side: P[eta, X_chunk] (real part)."""
+    alg, nm, labels, eta, chunk = args
     import oracle
-    import paper_2609_14831_b300 as cg
+    return oracle.project(oracle.commutator(alg, nm, eta, chunk), labels).real
+
+
+def oracle_rhs_parallel(pool, parts, alg, nm, labels, h, xs):
+    """The oracle's right-hand side spread over a process pool: eta = [H_d, H_od]
+    once, then [eta, X_o] split by the labels of X_o (the commutator is linear
+    in X), pieces summed in a fixed order."""
+    import oracle
+    eta = oracle.generator(alg, nm, labels, h)
+    tasks, owner = [], []
+    for o, v in enumerate([h] + list(xs)):
+        nz = [(int(l), complex(c)) for l, c in zip(labels, v) if c != 0]
+        step = max(1, -(-len(nz) // parts))
+        for c0 in range(0, max(1, len(nz)), step):
+            tasks.append((alg, nm, labels, eta, dict(nz[c0:c0 + step])))
+            owner.append(o)
+    out = [np.zeros(len(labels)) for _ in range(1 + len(xs))]
+    for o, piece in zip(owner, pool.map(_oracle_piece, tasks)):
+        out[o] += piece
+    return out
+
+
+def cpu_sample(seconds_budget=20.0, cores=None, gpu_flow_rhs_calls=None):
+    """The oracle on the host cores (process pool, spawn): right-hand sides of
+    the 7-spin-orbital stress recipe (records/s of its graph) and of the
+    8-spin-orbital molecular model (seconds per RHS, and the DP45 flow it
+    implies).  No product library is loaded here."""
+    import multiprocessing as mp
     from cut_inputs import workload
-    w = workload("stress_7so", seed=2)
-    with tempfile.TemporaryDirectory() as d:
-        p = os.path.join(d, "s8.cutg")
-        st = cg.build_graph(w.alg, w.nmodes, w.labels, p)
-    rec = st["R_g"] + st["R_L"]
-    t0 = time.time()
-    calls = 0
-    while True:
-        oracle.rhs(w.alg, w.nmodes, w.labels, w.h, w.observables)
-        calls += 1
-        if time.time() - t0 > seconds_budget or calls >= 3:
-            break
-    dt = (time.time() - t0) / calls
-    return {"value": rec / dt, "unit": "records/s", "cores": 1, "kind": "oracle",
-            "sample": f"oracle right-hand side (H, N, D) of the same recipe on 7 spin-orbitals "
-                      f"(n={len(w.labels)}, {rec} graph records), {calls} call(s), {dt:.2f} s each; "
-                      f"value = graph records / oracle time"}
+    cores = cores or os.cpu_count() or 1
+    ws = workload("stress_7so", seed=2)
+    wm = workload("molecular_8so")
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_piece, [(ws.alg, ws.nmodes, ws.labels[:1], {}, {})] * cores)   # start the workers
+        t0 = time.time()
+        calls = 0
+        while True:
+            oracle_rhs_parallel(pool, cores, ws.alg, ws.nmodes, ws.labels, ws.h, ws.observables)
+            calls += 1
+            if time.time() - t0 > seconds_budget / 2 or calls >= 3:
+                break
+        dt = (time.time() - t0) / calls
+        t0 = time.time()
+        oracle_rhs_parallel(pool, cores, wm.alg, wm.nmodes, wm.labels, wm.h, wm.observables)
+        dt8 = time.time() - t0
+    rec = SAMPLE_RECORDS["stress_7so"]
+    out = {"value": rec / dt, "unit": "records/s", "cores": cores, "kind": "oracle",
+           "sample": f"oracle right-hand side (H, N, D) of the stress recipe on 7 spin-orbitals (n={len(ws.labels)}, "
+                     f"{rec} graph records), {calls} call(s), {dt:.2f} s each on {cores} processes; value = graph "
+                     f"records / oracle time",
+           "molecular_8so_rhs_s": dt8,
+           "molecular_8so_records_per_s": SAMPLE_RECORDS["molecular_8so"] / dt8}
+    if gpu_flow_rhs_calls:
+        out["molecular_8so_dp45_flow_s_estimate"] = dt8 * gpu_flow_rhs_calls
+        out["molecular_8so_dp45_rhs_calls"] = int(gpu_flow_rhs_calls)
+    return out
 
 
 def batched_vs_plain(cg, torch, dev, local, batch=1024, plain_sample=8):
@@ -285,7 +331,8 @@ def gradient_vs_fd(cg, torch, dev, local):
     gn = g.cpu().numpy()
     G.close()
     return {"workload": "8-orbital model, d(flowed n_0)/d(32 parameters), DP45 to s = 10",
-            "accepted_steps": int(st["steps"]), "adjoint_s": t_adj, "fd_64_flows_s": t_fd,
+            "accepted_steps": int(st["steps"]), "rhs_calls": int(st["rhs_calls"]), "adjoint_s": t_adj,
+            "fd_64_flows_s": t_fd,
             "speedup": t_fd / t_adj, "max_rel_diff_vs_fd": float(np.max(np.abs(gn - fd)) / np.max(np.abs(fd)))}
 
 
@@ -455,6 +502,7 @@ def run_reference(args):
     if rank != 0:
         return
     cb = cpu_sample(seconds_budget=max(5.0, 60.0 / max(1, args.steps + args.warmup)))
+    cb["molecular_8so_dp45_flow_note"] = "GPU flow not run in this arm; a DP45 flow takes 1 + 6 x attempts RHS"
     # same metric, unit and workload name as the main line; the oracle runs a
     # bounded sample of that recipe (stated in cpu_baseline.sample)
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"],
@@ -653,7 +701,7 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        cpu = cpu_sample()
+        cpu = cpu_sample(gpu_flow_rhs_calls=gradient["rhs_calls"] if gradient else None)
 
     if rank == 0:
         line = {

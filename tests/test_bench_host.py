@@ -39,3 +39,33 @@ def test_job_throughput_is_weak_scaling_sum():
     assert bench.job_throughput(1000, 2.0, 1) == 500000.0
     assert bench.job_throughput(1000, 2.0, 4) == 2000000.0
     assert bench.max_over_ranks(3.5, 1) == 3.5
+
+
+def test_sample_record_counts_match_fresh_builds(tmp_path):
+    """The record counts the CPU baseline divides by are those of the graphs
+    cut_build compiles for the two sample workloads."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import paper_2609_14831_b300 as cg
+    from cut_inputs import workload
+    for name, seed in (("stress_7so", 2), ("molecular_8so", 1)):
+        w = workload(name, seed=seed)
+        st = cg.build_graph(w.alg, w.nmodes, w.labels, str(tmp_path / f"{name}.cutg"))
+        assert st["R_g"] + st["R_L"] == bench.SAMPLE_RECORDS[name], name
+
+
+def test_parallel_oracle_rhs_equals_the_oracle():
+    """The process-pool split of the oracle's right-hand side (by the labels
+    of each operand; the commutator is linear in X) gives the oracle's RHS."""
+    import multiprocessing as mp
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    from cut_inputs import workload
+    w = workload("molecular_4so")
+    with mp.get_context("spawn").Pool(2) as pool:
+        got = bench.oracle_rhs_parallel(pool, 3, w.alg, w.nmodes, w.labels, w.h, w.observables)
+    dh, dxs = oracle.rhs(w.alg, w.nmodes, w.labels, w.h, w.observables)
+    for g, want in zip(got, [dh] + list(dxs)):
+        np.testing.assert_allclose(g, want, rtol=0, atol=1e-13 * max(1.0, np.max(np.abs(want))))
