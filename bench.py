@@ -527,6 +527,7 @@ def main():
     ap.add_argument("--surrogate", action="store_true", help="run the surrogate workload instead")
     ap.add_argument("--no-paper", action="store_true", help="skip the paper's Pauli-boson workload")
     ap.add_argument("--no-gradient", action="store_true", help="skip the adjoint-gradient measurement")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the stress-graph adjoint measurement")
     ap.add_argument("--paper-diagnostics", action="store_true",
                     help="also time the 352M-record diagnostic action (builds a 2.8 GB graph)")
     ap.add_argument("--surrogate-train", type=int, default=50000)
@@ -559,7 +560,9 @@ def main():
         os.replace(path, shared)
     barrier()
     w = workload(args.workload, seed=2 + rank)
-    G = cg.Graph(shared, device=local)
+    t_adj_load = time.perf_counter()
+    G = cg.Graph(shared, device=local, adjoint=not args.no_adjoint)
+    t_adj_load = time.perf_counter() - t_adj_load
     barrier()
     if rank == 0:
         os.remove(shared)
@@ -645,6 +648,52 @@ def main():
                              "frac": comm_bytes / (comm_ms * 1e-3) / 1e9 / hbm_peak, "peak_kind": peak_kind,
                              "algorithmic_bytes": comm_bytes}}
 
+    # ---- one reverse traversal (vector-Jacobian product of the RHS) on the
+    #      stress graph: generator stage, the operand transpose, the generator
+    #      adjoint and the input adjoint of the generator stage
+    adjoint = None
+    if not args.no_adjoint:
+        import ctypes
+        W = torch.randn(nops, n, dtype=torch.float64, device=dev, generator=torch.Generator(device=dev).manual_seed(7))
+        HB = torch.empty_like(X)
+        P = lambda t: ctypes.c_void_p(t.data_ptr())
+        aargs = (G._h, P(X[0]), nops - 1, P(X[1:]), P(W[0]), P(W[1:]), P(HB[0]), P(HB[1:]),
+                 ctypes.c_void_p(stream.cuda_stream))
+        cg.check(cg.lib().cut_rhs_adjoint(*aargs))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(10):
+            cg.lib().cut_rhs_adjoint(*aargs)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        adj_ms = e0.elapsed_time(e1) / 10
+        # forward RHS on the same stream for the ratio
+        DXf = torch.empty_like(X)
+        fargs = (G._h, P(X[0]), nops - 1, P(X[1:]), P(DXf[0]), P(DXf[1:]), None, ctypes.c_void_p(stream.cuda_stream))
+        cg.check(cg.lib().cut_rhs(*fargs))
+        e0.record(stream)
+        for _ in range(10):
+            cg.lib().cut_rhs(*fargs)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fwd_ms = e0.elapsed_time(e1) / 10
+        # records streamed: generator stage (R_g), rows-by-input (R_L), rows
+        # by generator (R_L), both inputs of each generator record (2 R_g)
+        adj_records = 2 * G.R_L + 3 * G.R_g
+        adj_bytes = 8 * adj_records + 8 * nops * n * 4
+        adj_flop = 2 * nops * 2 * G.R_L + 2 * 3 * G.R_g
+        adjoint = {"kernels": "gen_stage, comm_stage_x4 over the transposed records, commT_xi_x4, genT_lanes",
+                   "ms": adj_ms, "forward_rhs_ms": fwd_ms, "adjoint_over_forward": adj_ms / fwd_ms,
+                   "records_streamed": int(adj_records), "records_over_forward": adj_records / R,
+                   "transposes_built_at_load_s": round(t_adj_load, 1),
+                   "roofline": {"bound": "alu", "achieved": adj_flop / (adj_ms * 1e-3) / 1e12, "peak": fp64_peak,
+                                "unit": "TFLOP/s", "frac": adj_flop / (adj_ms * 1e-3) / 1e12 / fp64_peak,
+                                "peak_kind": "measured FP64 FMA rate (this run)", "algorithmic_flop": int(adj_flop),
+                                "hbm_view": {"achieved": adj_bytes / (adj_ms * 1e-3) / 1e9, "peak": hbm_peak,
+                                             "unit": "GB/s", "frac": adj_bytes / (adj_ms * 1e-3) / 1e9 / hbm_peak,
+                                             "algorithmic_bytes": int(adj_bytes)}}}
+
     # ---- the same flow and kernel in double-float arithmetic (FP32 pairs)
     df = None
     if not args.no_df64 and rank == 0:
@@ -724,6 +773,7 @@ def main():
             "batched": batched,
             "paper_workload": paper,
             "gradient": gradient,
+            "adjoint": adjoint,
             "clocks": ck,
             "e2e": {"value": e2e_val, "unit": "records/s",
                     "h2d_bytes_per_step": int(8 * n * nops), "d2h_bytes_per_step": int(8 * n * nops)},

@@ -109,9 +109,13 @@ cut_status cut_build(const cut_build_opts *opts, int64_t n, const uint64_t *labe
 /* Read `path`, verify its SHA-256 and structure, upload to CUDA device
  * `device`.  device == -1 gives a host-only handle (no CUDA call is made):
  * query, labels, weights and records work, every traversal returns
- * INVALID_ARG.  flags: reserved, pass 0.  Errors: IO, FORMAT (bad header or
+ * INVALID_ARG.  flags: 0, or CUT_LOAD_ADJOINT to build the transposed record
+ * orders of the reverse traversal (Sec. 2.4) now, on the host threads, and
+ * upload them (about twice the graph's device memory more); without it they
+ * are built at the first adjoint call.  Errors: IO, FORMAT (bad header or
  * inconsistent arrays), CHECKSUM (payload digest mismatch), CUDA,
- * OUT_OF_MEMORY. */
+ * OUT_OF_MEMORY, INVALID_ARG (unknown flag). */
+enum { CUT_LOAD_ADJOINT = 1 };
 cut_status cut_graph_load(const char *path, int device, unsigned flags, cut_graph **out);
 cut_status cut_graph_free(cut_graph *g);
 
@@ -245,9 +249,11 @@ cut_status cut_rhs_noalloc(const cut_graph *g, const double *h, int n_obs, const
  *   h_bar = dL/dh (through eta and through X_0 = H),  x_bar[o] = dL/dx_o.
  * device in : h[n], x[n_obs][n], w_h[n], w_x[n_obs][n]
  * device out: h_bar[n], x_bar[n_obs][n]
- * The transposed record orders are built on the host at the first call
- * (synchronous), then kept with the graph.  Errors: INVALID_ARG, CUDA,
- * OUT_OF_MEMORY. */
+ * The transposed record orders come from cut_graph_load(.., CUT_LOAD_ADJOINT)
+ * or are built on the host at the first call (synchronous), then kept with
+ * the graph.  With at most eight operands the transposed passes gather the
+ * operands as packed 32-byte blocks (scratch n x 128 bytes from the
+ * stream-ordered allocator).  Errors: INVALID_ARG, CUDA, OUT_OF_MEMORY. */
 cut_status cut_rhs_adjoint(const cut_graph *g, const double *h, int n_obs, const double *x,
                            const double *w_h, const double *w_x, double *h_bar, double *x_bar,
                            cut_stream_t stream);
@@ -404,6 +410,17 @@ cut_status cut_mlp_set_output_affine(cut_mlp *m, const float *scale, const float
  * (t_hat = (t - shift - J x) / scale), so that the network learns only what
  * a linear model misses.  J = NULL removes it. */
 cut_status cut_mlp_set_linear(cut_mlp *m, const float *J);
+/* Fit the linear skip term and the output affine from training data on the
+ * device, in FP64: the least-squares affine map (1, x) -> t over the batch
+ * (normal equations, Cholesky with a 1e-12 relative ridge) gives shift =
+ * intercept and J = slopes; scale = the residual RMS of each output divided
+ * by sqrt(weight[o]) (host, optional, > 0: a larger weight makes that
+ * output's error count more in the loss).  The network then learns only
+ * what the affine map misses.  device in: x[batch][n_in] (FP32),
+ * t[batch][n_out] (FP64).  At most 63 inputs.  Errors: INVALID_ARG,
+ * UNSUPPORTED, OUT_OF_MEMORY, CUDA. */
+cut_status cut_mlp_fit_linear(cut_mlp *m, int batch, const float *x, const double *t, const float *weight,
+                              cut_stream_t stream);
 /* number of parameters in the flat layout W1, b1, W2, b2, W3, b3 (W [out][in]) */
 int64_t cut_mlp_param_count(const cut_mlp *m);
 /* host out: parameters (grads = 0) or the gradients of the last backward

@@ -121,6 +121,7 @@ def lib():
                                     ctypes.c_float, VP]),
         "cut_mlp_status": (st, [VP]),
         "cut_mlp_inject_stall": (st, [VP, i]),
+        "cut_mlp_fit_linear": (st, [VP, i, VP, VP, VP, VP]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -190,9 +191,12 @@ def assemble(X, C, stream=None):
 class Graph:
     """A loaded operation graph resident on one CUDA device."""
 
-    def __init__(self, path, device=0):
+    def __init__(self, path, device=0, adjoint=False):
+        """adjoint=True builds the transposed record orders of the reverse
+        traversal at load time (CUT_LOAD_ADJOINT) instead of at the first
+        adjoint call."""
         self._h = VP()
-        check(lib().cut_graph_load(os.fsencode(path), int(device), 0, ctypes.byref(self._h)))
+        check(lib().cut_graph_load(os.fsencode(path), int(device), 1 if adjoint else 0, ctypes.byref(self._h)))
         self.path = path
         self.device_index = int(device)
         d = GraphDesc()
@@ -431,6 +435,18 @@ class MLP:
         J = np.ascontiguousarray(J, dtype=np.float32)
         assert J.shape == (self.n_out, self.n_in)
         check(lib().cut_mlp_set_linear(self._h, J.ctypes.data))
+
+    def fit_linear(self, x, t, weight=None, stream=None):
+        """Least-squares affine part (shift, J) and residual scale from data
+        (x: [B, n_in], t: [B, n_out] FP64), fitted on the device."""
+        torch = _torch()
+        x = self._f32(x, self.n_in)
+        t = t if isinstance(t, torch.Tensor) else torch.as_tensor(np.asarray(t))
+        t = t.to(device=self.device, dtype=torch.float64).contiguous()
+        assert t.shape == (x.shape[0], self.n_out)
+        w = None if weight is None else np.ascontiguousarray(weight, dtype=np.float32)
+        check(lib().cut_mlp_fit_linear(self._h, x.shape[0], _ptr(x), _ptr(t),
+                                       None if w is None else w.ctypes.data, _stream(stream)))
 
     def params(self, grads=False):
         out = np.empty(lib().cut_mlp_param_count(self._h), dtype=np.float32)

@@ -8,6 +8,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "bundle.h"
@@ -119,6 +120,7 @@ static cut_status upload_csr(DevCSR &d, const std::vector<uint64_t> &rp, const s
 }
 
 static cut_status upload_weights(cut_graph *g);
+static cut_status ensure_transposes(cut_graph *g);
 
 // Entry points that traverse the whole graph refuse a shard handle.
 static cut_status whole_graph(const cut_graph *g, const char *fn) {
@@ -180,8 +182,8 @@ static void comm_launch_x4(const DevCSR &c, const k::Weights &w, const double *x
 // pass).  Both give the same bits.
 static void launch_comm(const cut_graph *g, const double *xi, int nops, const double *const *xs,
                         double *const *dxs, cudaStream_t s, const int *done, int stage = 1,
-                        double *X4 = nullptr) {
-    const DevCSR &c = g->st[stage];
+                        double *X4 = nullptr, const DevCSR *csr = nullptr) {
+    const DevCSR &c = csr ? *csr : g->st[stage];
     const k::Weights w = weights_of(g);
     const int lanes = comm_lanes(c.lane_rows);
     if (X4 && nops <= 8) {
@@ -314,7 +316,7 @@ const char *cut_version(void) { return "cutgraph-b300 0.1 (sm_103a)"; }
 
 cut_status cut_graph_load(const char *path, int device, unsigned flags, cut_graph **out) {
     if (!path || !out) return set_error(CUT_ERR_INVALID_ARG, "cut_graph_load: null argument");
-    if (flags != 0) return set_error(CUT_ERR_INVALID_ARG, "cut_graph_load: flags must be 0");
+    if (flags & ~(unsigned)CUT_LOAD_ADJOINT) return set_error(CUT_ERR_INVALID_ARG, "cut_graph_load: unknown flags");
     *out = nullptr;
     if (device < -1) return set_error(CUT_ERR_INVALID_ARG, "cut_graph_load: bad device");
     if (device >= 0) {
@@ -343,6 +345,10 @@ cut_status cut_graph_load(const char *path, int device, unsigned flags, cut_grap
     cut_status st = upload_weights(g.get());
     if (st != CUT_OK) return st;
     g->device_bytes += bytes;
+    if (flags & CUT_LOAD_ADJOINT) {
+        st = ensure_transposes(g.get());
+        if (st != CUT_OK) return st;
+    }
     *out = g.release();
     return set_ok();
 }
@@ -585,25 +591,57 @@ extern "C" cut_status cut_rhs_jvp(const cut_graph *g, const double *h, int n_obs
 namespace cut {
 
 // Counting sort of records into a new CSR keyed by `row_of(e)`, payload
-// (code | first(e), second(e)).
+// (code | first(e), second(e)).  The input rows are split into T contiguous
+// blocks, one host thread each: counts per (block, output row), then every
+// block writes its records after those of the blocks before it, so each
+// output row lists its records in input order, as a sequential pass would.
 template <class RowF, class AF, class BF>
 static void transpose(const std::vector<uint64_t> &rp, const std::vector<uint32_t> &rec, int64_t rows_out,
                       RowF row_of, AF first, BF second, std::vector<uint64_t> &orp,
                       std::vector<uint32_t> &orec) {
     const int64_t rows_in = (int64_t)rp.size() - 1;
+    const uint64_t R = rows_in > 0 ? rp[rows_in] : 0;
+    int T = (int)std::min<uint64_t>(std::max(1u, std::thread::hardware_concurrency()), 16);
+    if (R < (1u << 20)) T = 1;
+    std::vector<int64_t> blk(T + 1);
+    blk[0] = 0;
+    for (int t = 1; t < T; t++)
+        blk[t] = std::max(blk[t - 1], (int64_t)(std::lower_bound(rp.begin(), rp.end(), R * t / T) - rp.begin()));
+    blk[T] = rows_in;
+    std::vector<std::vector<uint64_t>> cnt(T, std::vector<uint64_t>(rows_out + 1, 0));
+    auto par = [&](auto fn) {
+        std::vector<std::thread> th;
+        for (int t = 0; t < T; t++) th.emplace_back(fn, t);
+        for (auto &x : th) x.join();
+    };
+    par([&](int t) {
+        auto &c = cnt[t];
+        for (int64_t r = blk[t]; r < std::min(blk[t + 1], rows_in); r++)
+            for (uint64_t e = rp[r]; e < rp[r + 1]; e++) c[row_of(r, rec[2 * e], rec[2 * e + 1])]++;
+    });
+    // offsets: output row major, block minor
     orp.assign(rows_out + 1, 0);
-    for (int64_t r = 0; r < rows_in; r++)
-        for (uint64_t e = rp[r]; e < rp[r + 1]; e++) orp[row_of(r, rec[2 * e], rec[2 * e + 1]) + 1]++;
-    for (int64_t r = 0; r < rows_out; r++) orp[r + 1] += orp[r];
-    std::vector<uint64_t> cur(orp.begin(), orp.end() - 1);
-    orec.assign(rec.size(), 0);
-    for (int64_t r = 0; r < rows_in; r++)
-        for (uint64_t e = rp[r]; e < rp[r + 1]; e++) {
-            uint32_t w0 = rec[2 * e], w1 = rec[2 * e + 1];
-            uint64_t p = cur[row_of(r, w0, w1)]++;
-            orec[2 * p] = ((w0 >> kIndexBits) << kIndexBits) | first(r, w0, w1);
-            orec[2 * p + 1] = second(r, w0, w1);
+    uint64_t acc = 0;
+    for (int64_t o = 0; o < rows_out; o++) {
+        orp[o] = acc;
+        for (int t = 0; t < T; t++) {
+            const uint64_t c = cnt[t][o];
+            cnt[t][o] = acc;
+            acc += c;
         }
+    }
+    orp[rows_out] = acc;
+    orec.assign(rec.size(), 0);
+    par([&](int t) {
+        auto &cur = cnt[t];
+        for (int64_t r = blk[t]; r < std::min(blk[t + 1], rows_in); r++)
+            for (uint64_t e = rp[r]; e < rp[r + 1]; e++) {
+                const uint32_t w0 = rec[2 * e], w1 = rec[2 * e + 1];
+                const uint64_t p = cur[row_of(r, w0, w1)]++;
+                orec[2 * p] = ((w0 >> kIndexBits) << kIndexBits) | first(r, w0, w1);
+                orec[2 * p + 1] = second(r, w0, w1);
+            }
+    });
 }
 
 static cut_status ensure_transposes(cut_graph *g) {
@@ -658,13 +696,68 @@ static cut_status ensure_transposes(cut_graph *g) {
     return CUT_OK;
 }
 
+// X4[j][4 NB] = Y[o][j] for the nops (<= 8) operands of a stacked vector
+static void pack_operands(const cut_graph *g, const double *Y, int nops, double *X4, cudaStream_t s) {
+    const int64_t n = g->host.n();
+    switch (nops) {
+#define CASE(M)                                                                       \
+    case M: {                                                                         \
+        k::Ops<M> ops;                                                                \
+        for (int t = 0; t < M; t++) { ops.x[t] = Y + t * n; ops.dx[t] = nullptr; }      \
+        k::pack_x4<M><<<grid_for_len(n), 256, 0, s>>>(ops, n, X4, nullptr);           \
+    } break;
+        CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+#undef CASE
+    }
+}
+
+// bytes of the packed adjoint scratch: two blocks of n x 64 bytes, 32-byte aligned
+static size_t adjoint_scratch_bytes(const cut_graph *g) { return (size_t)g->host.n() * 128 + 64; }
+
 // VJP of the stacked RHS at Y with cotangent W: YB = J(Y)^T W.  xi, xib:
-// scratch [n_g]; xbar0: scratch [n].
+// scratch [n_g]; xbar0: scratch [n]; pk: adjoint_scratch_bytes(g) of scratch
+// (null: the one-gather-per-operand kernels).
 static void stacked_vjp(const cut_graph *g, const double *Y, const double *W, double *YB, int nops, double *xi,
-                        double *xib, double *xbar0, cudaStream_t s) {
+                        double *xib, double *xbar0, cudaStream_t s, void *pk = nullptr) {
     const int64_t n = g->host.n(), ng = g->host.n_g();
     const int nc = (int)g->host.num.size();
     launch_gen(g, Y, xi, s, nullptr);
+    if (pk && nops <= 8) {
+        // operand transposes: x_bar_o[j] = sum beta xi[a] w_o[k] is the forward
+        // commutator's form over the rows-by-j records (W packed into W4)
+        double *W4 = reinterpret_cast<double *>(((uintptr_t)pk + 31) & ~(uintptr_t)31);
+        double *X4 = W4 + 8 * n;
+        const double *ws[8];
+        double *xb[8];
+        for (int o = 0; o < nops; o++) { ws[o] = W + o * n; xb[o] = o == 0 ? xbar0 : YB + o * n; }
+        launch_comm(g, xi, nops, ws, xb, s, nullptr, 1, W4, &g->tx);
+        pack_operands(g, Y, nops, X4, s);
+        const k::Weights w = weights_of(g);
+        const DevCSR &cx = g->txi, &ch = g->th;
+        const int lx = comm_lanes(cx.rows), lh = gen_lanes(ch.rows);
+        switch (nops) {
+#define CASE(M)                                                                                                 \
+    case M:                                                                                                     \
+        if (w.uniform) {                                                                                        \
+            if (lx == 8) k::commT_xi_x4<M, true, 8><<<grid_for_groups(cx.rows, 8), k::kBlock, 0, s>>>(cx.rp, cx.rec, w, W4, X4, xib, cx.rows); \
+            else k::commT_xi_x4<M, true, 32><<<grid_for_groups(cx.rows, 32), k::kBlock, 0, s>>>(cx.rp, cx.rec, w, W4, X4, xib, cx.rows); \
+        } else {                                                                                                \
+            if (lx == 8) k::commT_xi_x4<M, false, 8><<<grid_for_groups(cx.rows, 8), k::kBlock, 0, s>>>(cx.rp, cx.rec, w, W4, X4, xib, cx.rows); \
+            else k::commT_xi_x4<M, false, 32><<<grid_for_groups(cx.rows, 32), k::kBlock, 0, s>>>(cx.rp, cx.rec, w, W4, X4, xib, cx.rows); \
+        }                                                                                                       \
+        break;
+            CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+#undef CASE
+        }
+        if (w.uniform) {
+            if (lh == 4) k::genT_lanes<true, 4><<<grid_for_groups(ch.rows, 4), k::kBlock, 0, s>>>(ch.rp, ch.rec, w, xib, Y, xbar0, YB, ch.rows);
+            else k::genT_lanes<true, 8><<<grid_for_groups(ch.rows, 8), k::kBlock, 0, s>>>(ch.rp, ch.rec, w, xib, Y, xbar0, YB, ch.rows);
+        } else {
+            if (lh == 4) k::genT_lanes<false, 4><<<grid_for_groups(ch.rows, 4), k::kBlock, 0, s>>>(ch.rp, ch.rec, w, xib, Y, xbar0, YB, ch.rows);
+            else k::genT_lanes<false, 8><<<grid_for_groups(ch.rows, 8), k::kBlock, 0, s>>>(ch.rp, ch.rec, w, xib, Y, xbar0, YB, ch.rows);
+        }
+        return;
+    }
     // x_bar_o = L(h)^T w_o ; operand 0's goes to scratch, then into h_bar
     for (int o0 = 0; o0 < nops; o0 += 4) {
         int m = std::min(4, nops - o0);
@@ -715,13 +808,14 @@ extern "C" cut_status cut_rhs_adjoint(const cut_graph *g, const double *h, int n
     // stacked copies so that one code path serves single calls and flows
     double *buf = nullptr;
     const size_t L = (size_t)nops * n;
-    CUDA_TRY(cudaMallocAsync(&buf, (3 * L + 2 * ng + n) * 8, s));
+    CUDA_TRY(cudaMallocAsync(&buf, (3 * L + 2 * ng + n) * 8 + adjoint_scratch_bytes(g), s));
     double *Y = buf, *W = buf + L, *YB = buf + 2 * L, *xi = buf + 3 * L, *xib = xi + ng, *xb0 = xib + ng;
+    void *pk = xb0 + n;
     CUDA_TRY(cudaMemcpyAsync(Y, h, n * 8, cudaMemcpyDeviceToDevice, s));
     if (n_obs) CUDA_TRY(cudaMemcpyAsync(Y + n, x, (size_t)n_obs * n * 8, cudaMemcpyDeviceToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(W, w_h, n * 8, cudaMemcpyDeviceToDevice, s));
     if (n_obs) CUDA_TRY(cudaMemcpyAsync(W + n, w_x, (size_t)n_obs * n * 8, cudaMemcpyDeviceToDevice, s));
-    stacked_vjp(g, Y, W, YB, nops, xi, xib, xb0, s);
+    stacked_vjp(g, Y, W, YB, nops, xi, xib, xb0, s, pk);
     CUDA_TRY(cudaMemcpyAsync(h_bar, YB, n * 8, cudaMemcpyDeviceToDevice, s));
     if (n_obs) CUDA_TRY(cudaMemcpyAsync(x_bar, YB + n, (size_t)n_obs * n * 8, cudaMemcpyDeviceToDevice, s));
     CUDA_TRY(cudaGetLastError());
@@ -1039,9 +1133,11 @@ extern "C" cut_status cut_flow_vjp(const cut_graph *g, const double *h0, int n_o
     if (st != CUT_OK) return st;
     cudaStream_t s = sp.work;
     // memory: checkpoints [ncp][L], segment states [C+1][L], stages U[S][L],
-    // K[S][L], yb, ub, kb[S][L], xi, xib, xb0
+    // K[S][L], kb[S][L], yb, ub, ybn, the fixed step input/output Ycur, Ynext,
+    // xi, xib, xb0, the step sizes and the current one, packing scratch
+    const size_t dfb = operand_scratch_bytes(g) / 8 + 4, pkb = adjoint_scratch_bytes(g) / 8 + 4;
     double *buf = nullptr;
-    size_t tot = (size_t)(ncp + (C + 1) + 3 * S + 3) * L + 2 * ng + n;
+    size_t tot = (size_t)(ncp + (C + 1) + 3 * S + 5) * L + 2 * ng + n + N + 1 + dfb + pkb;
     cudaError_t e = cudaMallocAsync(&buf, tot * 8, s);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
@@ -1050,33 +1146,96 @@ extern "C" cut_status cut_flow_vjp(const cut_graph *g, const double *h0, int n_o
                                                     " bytes: " + cudaGetErrorString(e));
     }
     double *cp = buf, *seg = cp + ncp * L, *U = seg + (C + 1) * L, *K = U + S * L, *KB = K + S * L;
-    double *yb = KB + S * L, *ub = yb + L, *ybn = ub + L, *xi = ybn + L, *xib = xi + ng, *xb0 = xib + ng;
+    double *yb = KB + S * L, *ub = yb + L, *ybn = ub + L, *Ycur = ybn + L, *Ynext = Ycur + L;
+    double *xi = Ynext + L, *xib = xi + ng, *xb0 = xib + ng, *steps_d = xb0 + n, *dsd = steps_d + N;
+    void *df = dsd + 1, *pk = (double *)df + dfb;
     cudaMemcpyAsync(cp, h0, n * 8, cudaMemcpyDeviceToDevice, s);
     if (n_obs) cudaMemcpyAsync(cp + n, x0, (size_t)n_obs * n * 8, cudaMemcpyDeviceToDevice, s);
-    // generic explicit RK step with stage storage: y (in) -> out, stages in U/K
-    auto step = [&](const double *y, double *out, double ds) {
-        for (int i = 0; i < S; i++) {
-            k::Combine cb;
-            cb.base = y;
-            cb.nk = 0;
-            for (int j = 0; j < i; j++)
-                if (A[i][j] != 0.0) { cb.K[cb.nk] = K + j * L; cb.c[cb.nk] = A[i][j]; cb.nk++; }
-            k::rk_combine<<<grid_for_len(L), 256, 0, s>>>(cb, U + i * L, L, nullptr, ds, nullptr);
-            stacked_rhs(g, U + i * L, K + i * L, nops, xi, s, nullptr);
-        }
+    if (N) cudaMemcpyAsync(steps_d, steps.data(), N * 8, cudaMemcpyHostToDevice, s);
+    // out = base + sum c_j (ds K_j) with ds read from the device (*dsd) or given
+    auto combine = [&](double *out, const double *base, int nk, const double *const *Ks, const double *cs,
+                       const double *dsp, double dsc) {
         k::Combine cb;
-        cb.base = y;
+        cb.base = base;
         cb.nk = 0;
-        for (int j = 0; j < S; j++)
-            if (B[j] != 0.0) { cb.K[cb.nk] = K + j * L; cb.c[cb.nk] = B[j]; cb.nk++; }
-        k::rk_combine<<<grid_for_len(L), 256, 0, s>>>(cb, out, L, nullptr, ds, nullptr);
+        for (int j = 0; j < nk; j++)
+            if (cs[j] != 0.0) { cb.K[cb.nk] = Ks[j]; cb.c[cb.nk] = cs[j]; cb.nk++; }
+        k::rk_combine<<<grid_for_len(L), 256, 0, s>>>(cb, out, L, dsp, dsc, nullptr);
+    };
+    // one explicit RK step Ycur -> Ynext of size *dsd, stages kept in U/K
+    auto step = [&]() {
+        const double *Ks[7];
+        for (int j = 0; j < S; j++) Ks[j] = K + j * L;
+        for (int i = 0; i < S; i++) {
+            combine(U + i * L, Ycur, i, Ks, A[i], dsd, 0.0);
+            // FP64 whatever the graph's arithmetic setting: the adjoint is FP64
+            const double *xs[64];
+            double *dxs[64];
+            for (int o = 0; o < nops; o++) { xs[o] = U + i * L + o * n; dxs[o] = K + i * L + o * n; }
+            launch_gen(g, U + i * L, xi, s, nullptr);
+            launch_comm(g, xi, nops, xs, dxs, s, nullptr, 1, reinterpret_cast<double *>(operand_blocks(g, df)));
+        }
+        combine(Ynext, Ycur, S, Ks, B, dsd, 0.0);
+    };
+    // the reverse of one step: k_bar_i = ds b_i y_bar, then stage by stage
+    // u_bar_i = J(U_i)^T k_bar_i into y_bar and ds a_ij u_bar_i into k_bar_j
+    auto back = [&]() {
+        step();   // stage inputs U_i of this step
+        for (int i = 0; i < S; i++) {
+            cudaMemsetAsync(KB + i * L, 0, L * 8, s);
+            const double *v[1] = {yb};
+            const double c[1] = {B[i]};
+            if (B[i] != 0.0) combine(KB + i * L, KB + i * L, 1, v, c, dsd, 0.0);
+        }
+        cudaMemcpyAsync(ybn, yb, L * 8, cudaMemcpyDeviceToDevice, s);
+        for (int i = S - 1; i >= 0; i--) {
+            stacked_vjp(g, U + i * L, KB + i * L, ub, nops, xi, xib, xb0, s, pk);
+            const double *v[1] = {ub};
+            const double one[1] = {1.0};
+            combine(ybn, ybn, 1, v, one, nullptr, 1.0);
+            for (int j = 0; j < i; j++) {
+                const double c[1] = {A[i][j]};
+                if (A[i][j] != 0.0) combine(KB + j * L, KB + j * L, 1, v, c, dsd, 0.0);
+            }
+        }
+        cudaMemcpyAsync(yb, ybn, L * 8, cudaMemcpyDeviceToDevice, s);
+    };
+    // both bodies captured once as CUDA graphs; a step is then three
+    // launches: its size and its start state copied in, the graph replayed
+    cudaGraphExec_t gstep = nullptr, gback = nullptr;
+    auto capture = [&](auto body, cudaGraphExec_t *exec) -> cudaError_t {
+        cudaGraph_t graph;
+        cudaError_t ce = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (ce != cudaSuccess) return ce;
+        body();
+        ce = cudaStreamEndCapture(s, &graph);
+        if (ce != cudaSuccess) return ce;
+        ce = cudaGraphInstantiate(exec, graph, 0);
+        cudaGraphDestroy(graph);
+        return ce;
+    };
+    e = capture(step, &gstep);
+    if (e == cudaSuccess) e = capture(back, &gback);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        if (gstep) cudaGraphExecDestroy(gstep);
+        cudaFreeAsync(buf, s);
+        cudaStreamSynchronize(s);
+        end_work(sp);
+        return set_error(CUT_ERR_CUDA, std::string("cut_flow_vjp: graph capture: ") + cudaGetErrorString(e));
+    }
+    auto run_step = [&](int64_t t, const double *y, double *out) {
+        cudaMemcpyAsync(dsd, steps_d + t, 8, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(Ycur, y, L * 8, cudaMemcpyDeviceToDevice, s);
+        cudaGraphLaunch(gstep, s);
+        cudaMemcpyAsync(out, Ynext, L * 8, cudaMemcpyDeviceToDevice, s);
     };
     // forward: the state at step c*C is kept as checkpoint c
     {
         double *cur = seg, *nxt = seg + L;
         cudaMemcpyAsync(cur, cp, L * 8, cudaMemcpyDeviceToDevice, s);
         for (int64_t t = 0; t < N; t++) {
-            step(cur, nxt, steps[t]);
+            run_step(t, cur, nxt);
             std::swap(cur, nxt);
             if ((t + 1) % C == 0 && t + 1 < N) cudaMemcpyAsync(cp + ((t + 1) / C) * L, cur, L * 8, cudaMemcpyDeviceToDevice, s);
         }
@@ -1085,36 +1244,18 @@ extern "C" cut_status cut_flow_vjp(const cut_graph *g, const double *h0, int n_o
     // states from its checkpoint, then walk its steps in reverse
     cudaMemcpyAsync(yb, yb_h, n * 8, cudaMemcpyDeviceToDevice, s);
     if (n_obs) cudaMemcpyAsync(yb + n, yb_x, (size_t)n_obs * n * 8, cudaMemcpyDeviceToDevice, s);
-    auto axpy = [&](double *out, const double *base, const double *v, double c, double ds) {
-        k::Combine cb;
-        cb.base = base;
-        cb.nk = 1;
-        cb.K[0] = v;
-        cb.c[0] = c;
-        k::rk_combine<<<grid_for_len(L), 256, 0, s>>>(cb, out, L, nullptr, ds, nullptr);
-    };
     for (int64_t c0 = N > 0 ? ((N - 1) / C) * C : -1; c0 >= 0; c0 -= C) {
         const int64_t c1 = std::min(N, c0 + C);
         cudaMemcpyAsync(seg, cp + (c0 / C) * L, L * 8, cudaMemcpyDeviceToDevice, s);
-        for (int64_t t = c0; t < c1 - 1; t++) step(seg + (t - c0) * L, seg + (t - c0 + 1) * L, steps[t]);
+        for (int64_t t = c0; t < c1 - 1; t++) run_step(t, seg + (t - c0) * L, seg + (t - c0 + 1) * L);
         for (int64_t t = c1 - 1; t >= c0; t--) {
-            const double ds = steps[t];
-            step(seg + (t - c0) * L, ybn, ds);  // stage inputs U_i of step t
-            // k_bar_i = ds b_i y_bar, y_bar_new = y_bar
-            for (int i = 0; i < S; i++) {
-                cudaMemsetAsync(KB + i * L, 0, L * 8, s);
-                if (B[i] != 0.0) axpy(KB + i * L, KB + i * L, yb, B[i], ds);
-            }
-            cudaMemcpyAsync(ybn, yb, L * 8, cudaMemcpyDeviceToDevice, s);
-            for (int i = S - 1; i >= 0; i--) {
-                stacked_vjp(g, U + i * L, KB + i * L, ub, nops, xi, xib, xb0, s);  // u_bar_i
-                axpy(ybn, ybn, ub, 1.0, 1.0);
-                for (int j = 0; j < i; j++)
-                    if (A[i][j] != 0.0) axpy(KB + j * L, KB + j * L, ub, A[i][j], ds);
-            }
-            cudaMemcpyAsync(yb, ybn, L * 8, cudaMemcpyDeviceToDevice, s);
+            cudaMemcpyAsync(dsd, steps_d + t, 8, cudaMemcpyDeviceToDevice, s);
+            cudaMemcpyAsync(Ycur, seg + (t - c0) * L, L * 8, cudaMemcpyDeviceToDevice, s);
+            cudaGraphLaunch(gback, s);
         }
     }
+    cudaGraphExecDestroy(gstep);
+    cudaGraphExecDestroy(gback);
     cudaMemcpyAsync(gh, yb, n * 8, cudaMemcpyDeviceToDevice, s);
     if (n_obs) cudaMemcpyAsync(gx, yb + n, (size_t)n_obs * n * 8, cudaMemcpyDeviceToDevice, s);
     cudaFreeAsync(buf, s);

@@ -547,6 +547,87 @@ __global__ void __launch_bounds__(kBlock) genT(const uint64_t *__restrict__ rp,
     }
 }
 
+// ---------------------------------------------------------------- adjoint, packed
+// The transposed passes of the reverse traversal (Sec. 2.4) in the layout of
+// the forward stages: LANES lanes per row, records streamed with coalesced
+// loads, uniform factors applied as sign flips, operands gathered as packed
+// 32-byte blocks.  (The operand transpose x_bar_o[j] = sum beta xi[a] w_o[k]
+// has the forward commutator's form and runs in comm_stage_x4 itself.)
+//
+// Generator adjoint from the commutator stage, rows a, records (code|k, j):
+//   xi_bar[a] = sum_e beta_e sum_o W4[k][o] X4[j][o]
+template <int NOPS, bool UNIFORM, int LANES>
+__global__ void __launch_bounds__(kBlock) commT_xi_x4(const uint64_t *__restrict__ rp,
+                                                      const uint2 *__restrict__ rec, Weights wt,
+                                                      const double *__restrict__ W4,
+                                                      const double *__restrict__ X4,
+                                                      double *__restrict__ xi_bar, int64_t rows) {
+    static_assert(NOPS <= 8, "at most two packed blocks");
+    constexpr int NB = (NOPS + 3) / 4;
+    constexpr int RPW = 32 / LANES;
+    __shared__ double ws[256];
+    __shared__ unsigned long long sg[256];
+    load_weights(ws, sg, wt);
+    const int lane = threadIdx.x & 31, sub = lane / LANES, sl = lane % LANES;
+    const int64_t nw = (int64_t)gridDim.x * kWarpsPerBlock;
+    for (int64_t rg = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); rg * RPW < rows; rg += nw) {
+        const int64_t r = rg * RPW + sub;
+        double acc = 0.0;
+        if (r < rows) {
+            const uint64_t e = rp[r + 1];
+            for (uint64_t p = rp[r] + sl; p < e; p += LANES) {
+                const uint2 q = __ldcs(rec + p);
+                double wv[4 * NB], xv[4 * NB];
+#pragma unroll
+                for (int b = 0; b < NB; b++) {
+                    ld_quad64(W4 + 4 * NB * (int64_t)(q.x & kIdx) + 4 * b, wv[4 * b], wv[4 * b + 1], wv[4 * b + 2],
+                              wv[4 * b + 3]);
+                    ld_quad64(X4 + 4 * NB * (int64_t)q.y + 4 * b, xv[4 * b], xv[4 * b + 1], xv[4 * b + 2],
+                              xv[4 * b + 3]);
+                }
+                double d = wv[0] * xv[0];
+#pragma unroll
+                for (int o = 1; o < NOPS; o++) d = fma(wv[o], xv[o], d);
+                acc += UNIFORM ? signed_by(d, sg[q.x >> 24]) : ws[q.x >> 24] * d;
+            }
+        }
+        acc = group_sum<LANES>(acc);
+        if (sl == 0 && r < rows) xi_bar[r] = UNIFORM ? acc * wt.mag : acc;
+    }
+}
+
+// Input adjoint of the generator stage, rows = registry coordinates r,
+// records (code|a, partner) (both inputs of every generator record):
+//   h_bar[r] = x0_bar[r] + sum_e alpha_e xi_bar[a] h[partner]
+template <bool UNIFORM, int LANES>
+__global__ void __launch_bounds__(kBlock) genT_lanes(const uint64_t *__restrict__ rp,
+                                                     const uint2 *__restrict__ rec, Weights wt,
+                                                     const double *__restrict__ xi_bar,
+                                                     const double *__restrict__ h,
+                                                     const double *__restrict__ x0_bar,
+                                                     double *__restrict__ h_bar, int64_t rows) {
+    constexpr int RPW = 32 / LANES;
+    __shared__ double ws[256];
+    __shared__ unsigned long long sg[256];
+    load_weights(ws, sg, wt);
+    const int lane = threadIdx.x & 31, sub = lane / LANES, sl = lane % LANES;
+    const int64_t nw = (int64_t)gridDim.x * kWarpsPerBlock;
+    for (int64_t rg = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); rg * RPW < rows; rg += nw) {
+        const int64_t r = rg * RPW + sub;
+        double acc = 0.0;
+        if (r < rows) {
+            const uint64_t e = rp[r + 1];
+            for (uint64_t p = rp[r] + sl; p < e; p += LANES) {
+                const uint2 q = __ldcs(rec + p);
+                const double c = xi_bar[q.x & kIdx];
+                acc += UNIFORM ? signed_by(c, sg[q.x >> 24]) * h[q.y] : ws[q.x >> 24] * c * h[q.y];
+            }
+        }
+        acc = group_sum<LANES>(acc);
+        if (sl == 0 && r < rows) h_bar[r] = (x0_bar ? x0_bar[r] : 0.0) + (UNIFORM ? acc * wt.mag : acc);
+    }
+}
+
 // ---------------------------------------------------------------- RK algebra
 // out = base + sum_s coef_s * ds * K_s   (coefficients scaled by *ds_ptr
 // when ds_ptr is given, else by ds_const); vectors of length len.

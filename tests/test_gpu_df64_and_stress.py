@@ -185,3 +185,60 @@ def test_outside_space_diagnostics_match_oracle():
     fa = G.flow(h, xs, method="rk4", s0=0.0, s1=0.2, ds=0.02)
     fb = Gd.flow(h, xs, method="rk4", s0=0.0, s1=0.2, ds=0.02)
     assert_close(np64(fb[0]), np64(fa[0]), rtol=1e-13, what="retained flow")
+
+
+def test_stress_graph_full_size_adjoint(stress):
+    """The reverse traversal at full size (transposed record orders built at
+    load, packed operand gathers, 8 lanes per row): the forward tangent and
+    the vector-Jacobian product pair, <w, J v> = <J^T w, v>, and sampled
+    operand adjoints x_bar_o[j] = <w_o, P[eta, O_j]> match the oracle on
+    sparse inputs."""
+    import paper_2609_14831_b300 as cg
+    w, _ = stress
+    G = cg.Graph(graph_for("stress16", w.alg, w.nmodes, w.labels).path, device=0, adjoint=True)
+    rng = np.random.default_rng(75)
+    n = len(w.labels)
+    h, xs = w.h, list(w.observables)
+    v_h, v_x = rng.normal(size=n), [rng.normal(size=n) for _ in xs]
+    w_h, w_x = rng.normal(size=n), [rng.normal(size=n) for _ in xs]
+    jh, jx = G.rhs_jvp(h, xs, v_h, v_x)
+    bh, bx = G.rhs_adjoint(h, xs, w_h, w_x)
+    lhs = w_h @ np64(jh) + sum(a @ np64(b) for a, b in zip(w_x, jx))
+    rhs = np64(bh) @ v_h + sum(np64(a) @ b for a, b in zip(bx, v_x))
+    scale = np.abs(w_h) @ np.abs(np64(jh)) + sum(np.abs(a) @ np.abs(np64(b)) for a, b in zip(w_x, jx))
+    assert abs(lhs - rhs) <= 1e-12 * scale, (lhs, rhs, scale)
+    # sampled operand adjoints on sparse inputs against the oracle
+    hs = _sparse(w.h, 300, rng)
+    diag = np.nonzero([int(l) & 0xFFFFFFFF == int(l) >> 32 for l in w.labels])[0]
+    keep = rng.choice(diag, 40, replace=False)
+    hs[keep] = w.h[keep]
+    ws = [_sparse(rng.normal(size=n), 2000, rng) for _ in range(3)]
+    bh, bx = G.rhs_adjoint(hs, xs, ws[0], ws[1:])
+    eta = oracle.generator(w.alg, w.nmodes, w.labels, hs)
+    for j in rng.choice(n, 12, replace=False):
+        col = oracle.project(oracle.commutator(w.alg, w.nmodes, eta, {int(w.labels[j]): 1.0}), w.labels).real
+        for o, got in enumerate([None] + list(bx)):
+            if o == 0:
+                continue
+            want = col @ ws[o]
+            assert abs(np64(got)[j] - want) <= 1e-10 * (abs(want) + np.abs(col) @ np.abs(ws[o])) + 1e-300, (j, o)
+    G.close()
+
+
+@pytest.mark.parametrize("n_obs", [4, 7, 8])
+def test_packed_adjoint_operand_counts_match_oracle(n_obs):
+    """Five and eight operands (one and a part, and two full packed blocks) in
+    the packed transposed passes; nine operands take the unpacked kernels."""
+    from cut_inputs import fermion_registry
+    labels = fermion_registry(4)
+    h = molecular_hamiltonian(labels, 4, seed=76, scale=0.3)
+    rng = np.random.default_rng(76 + n_obs)
+    xs = [rng.normal(size=len(labels)) for _ in range(n_obs)]
+    G = graph_for("mol4", ALG_FERMION, 4, labels)
+    wh = rng.normal(size=len(labels))
+    wx = [rng.normal(size=len(labels)) for _ in xs]
+    hb, xb = G.rhs_adjoint(h, xs, wh, wx)
+    want_hb, want_xb = oracle.rhs_vjp(ALG_FERMION, 4, labels, h, xs, wh, wx)
+    assert_close(np64(hb), want_hb, what="h_bar")
+    for g_, w_ in zip(xb, want_xb):
+        assert_close(np64(g_), w_, what="x_bar")
