@@ -179,6 +179,126 @@ __global__ void to_bf16(const float *__restrict__ w, int64_t count, int in_p, in
     }
 }
 
+// ---- least-squares linear part of the surrogate (FP64, on the device)
+// Design matrix A[b] = (1, x[b][0..n_in)), P = n_in + 1 columns; the
+// "value" columns are A's own (for the Gram matrix A^T A) followed by the
+// targets (for A^T T).  partial[ch][p][c] = sum over the chunk's rows of
+// A[b][p] V[b][c]; chunks are summed in order afterwards (fixed sum order).
+constexpr int kFitP = 64;        // at most 63 inputs
+constexpr int kFitRows = 64;     // rows staged per shared-memory tile
+
+__device__ __forceinline__ double fit_a(const float *x, int n_in, int64_t b, int p) {
+    return p == 0 ? 1.0 : (double)x[b * n_in + (p - 1)];
+}
+
+__global__ void __launch_bounds__(128) fit_gram_partials(const float *__restrict__ x, const double *__restrict__ t,
+                                                         int64_t batch, int n_in, int n_out, int64_t rows_per_chunk,
+                                                         double *__restrict__ partial) {
+    const int P = n_in + 1, ncol = P + n_out;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t b0 = (int64_t)blockIdx.y * rows_per_chunk, b1 = min(batch, b0 + rows_per_chunk);
+    __shared__ double As[kFitRows][kFitP];
+    double acc[kFitP];
+#pragma unroll
+    for (int p = 0; p < kFitP; p++) acc[p] = 0.0;
+    for (int64_t r0 = b0; r0 < b1; r0 += kFitRows) {
+        const int nr = (int)(b1 - r0 < kFitRows ? b1 - r0 : kFitRows);
+        __syncthreads();
+        for (int e = threadIdx.x; e < nr * P; e += blockDim.x) As[e / P][e % P] = fit_a(x, n_in, r0 + e / P, e % P);
+        __syncthreads();
+        if (c < ncol) {
+            for (int r = 0; r < nr; r++) {
+                const double v = c < P ? As[r][c] : t[(r0 + r) * n_out + (c - P)];
+#pragma unroll
+                for (int p = 0; p < kFitP; p++)
+                    if (p < P) acc[p] = fma(As[r][p], v, acc[p]);
+            }
+        }
+    }
+    if (c < ncol)
+        for (int p = 0; p < P; p++) partial[((int64_t)blockIdx.y * P + p) * ncol + c] = acc[p];
+}
+
+// M[p][c] = sum_ch partial[ch][p][c] (chunk order)
+__global__ void fit_reduce(const double *__restrict__ partial, int chunks, int64_t len, double *__restrict__ M) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int ch = 0; ch < chunks; ch++) s += partial[ch * len + i];
+        M[i] = s;
+    }
+}
+
+// Cholesky of G = M[:, 0:P] + ridge I (thread 0), then each thread solves
+// G coef[:, o] = M[:, P + o] for its outputs; coef[P][n_out].
+__global__ void __launch_bounds__(256) fit_solve(const double *__restrict__ M, int n_in, int n_out, double ridge,
+                                                 double *__restrict__ coef, int *__restrict__ bad) {
+    const int P = n_in + 1, ncol = P + n_out;
+    __shared__ double Lm[kFitP][kFitP];
+    __shared__ int ok;
+    if (threadIdx.x == 0) {
+        ok = 1;
+        for (int i = 0; i < P; i++)
+            for (int j = 0; j <= i; j++) {
+                double v = M[i * ncol + j] + (i == j ? ridge : 0.0);
+                for (int k2 = 0; k2 < j; k2++) v -= Lm[i][k2] * Lm[j][k2];
+                if (i == j) {
+                    if (!(v > 0.0)) { ok = 0; v = 1.0; }
+                    Lm[i][i] = sqrt(v);
+                } else {
+                    Lm[i][j] = v / Lm[j][j];
+                }
+            }
+        if (!ok && bad) *bad = 1;
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < n_out; o += blockDim.x) {
+        double y[kFitP];
+        for (int i = 0; i < P; i++) {           // L y = rhs
+            double v = M[i * ncol + P + o];
+            for (int k2 = 0; k2 < i; k2++) v -= Lm[i][k2] * y[k2];
+            y[i] = v / Lm[i][i];
+        }
+        for (int i = P - 1; i >= 0; i--) {      // L^T z = y
+            double v = y[i];
+            for (int k2 = i + 1; k2 < P; k2++) v -= Lm[k2][i] * y[k2];
+            y[i] = v / Lm[i][i];
+        }
+        for (int i = 0; i < P; i++) coef[(int64_t)i * n_out + o] = y[i];
+    }
+}
+
+// partial[ch][o] = sum over the chunk of (t[b][o] - A[b] . coef[:, o])^2
+__global__ void __launch_bounds__(128) fit_resid_partials(const float *__restrict__ x, const double *__restrict__ t,
+                                                          const double *__restrict__ coef, int64_t batch, int n_in,
+                                                          int n_out, int64_t rows_per_chunk,
+                                                          double *__restrict__ partial) {
+    const int P = n_in + 1;
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t b0 = (int64_t)blockIdx.y * rows_per_chunk, b1 = min(batch, b0 + rows_per_chunk);
+    if (o >= n_out) return;
+    double cf[kFitP];
+    for (int p = 0; p < P; p++) cf[p] = coef[(int64_t)p * n_out + o];
+    double acc = 0.0;
+    for (int64_t b = b0; b < b1; b++) {
+        double r = t[b * n_out + o] - cf[0];
+        for (int p = 1; p < P; p++) r -= cf[p] * (double)x[b * n_in + (p - 1)];
+        acc = fma(r, r, acc);
+    }
+    partial[(int64_t)blockIdx.y * n_out + o] = acc;
+}
+
+// shift = intercept, J[o][i] = slope, scale = residual RMS / sqrt(weight)
+__global__ void fit_write(const double *__restrict__ coef, const double *__restrict__ ss, const float *__restrict__ w,
+                          int64_t batch, int n_in, int n_out, float *__restrict__ scale, float *__restrict__ shift,
+                          float *__restrict__ J) {
+    for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < n_out; o += gridDim.x * blockDim.x) {
+        shift[o] = (float)coef[o];
+        for (int i = 0; i < n_in; i++) J[(int64_t)o * n_in + i] = (float)coef[(int64_t)(1 + i) * n_out + o];
+        const double rms = sqrt(ss[o] / (double)(batch > 1 ? batch : 1));
+        scale[o] = (float)(fmax(rms, 1e-9) / sqrt((double)(w ? w[o] : 1.0f)));
+    }
+}
+
 }  // namespace mlpk
 
 static int pad_to(int v, int q) { return (v + q - 1) / q * q; }
@@ -474,6 +594,62 @@ cut_status cut_mlp_set_linear(cut_mlp *m, const float *J) {
         m->J = d;
     }
     cudaMemcpy(m->J, J, (size_t)m->n_out * m->n_in * 4, cudaMemcpyHostToDevice);
+    return set_ok();
+}
+
+cut_status cut_mlp_fit_linear(cut_mlp *m, int batch, const float *x, const double *t, const float *weight,
+                              cut_stream_t stream) {
+    if (!m || batch < 2 || !x || !t) return set_error(CUT_ERR_INVALID_ARG, "cut_mlp_fit_linear: bad argument");
+    if (m->n_in + 1 > mlpk::kFitP) return set_error(CUT_ERR_UNSUPPORTED, "cut_mlp_fit_linear: more than 63 inputs");
+    if (weight)
+        for (int o = 0; o < m->n_out; o++)
+            if (!(weight[o] > 0.0f) || !std::isfinite(weight[o]))
+                return set_error(CUT_ERR_INVALID_ARG, "cut_mlp_fit_linear: weights must be finite and > 0");
+    cudaSetDevice(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!m->J) {
+        float *d = nullptr;
+        if (m->alloc(&d, (size_t)m->n_out * m->n_in) != cudaSuccess)
+            return set_error(CUT_ERR_OUT_OF_MEMORY, "cut_mlp_fit_linear: J");
+        m->J = d;
+    }
+    const int P = m->n_in + 1, ncol = P + m->n_out;
+    const int chunks = (int)std::min<int64_t>(128, std::max<int64_t>(1, batch / 256));
+    const int64_t rpc = (batch + chunks - 1) / chunks;
+    const size_t np_ = (size_t)chunks * P * ncol, nres = (size_t)chunks * m->n_out;
+    double *buf = nullptr;
+    cudaError_t e = cudaMallocAsync(&buf, (np_ + (size_t)P * ncol + (size_t)P * m->n_out + nres + m->n_out) * 8 + 64, s);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return set_error(CUT_ERR_OUT_OF_MEMORY, "cut_mlp_fit_linear: scratch");
+    }
+    double *partial = buf, *M = partial + np_, *coef = M + (size_t)P * ncol, *rp = coef + (size_t)P * m->n_out,
+           *ss = rp + nres;
+    float *w = nullptr;
+    if (weight) {
+        e = cudaMallocAsync(&w, m->n_out * 4, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(w, weight, m->n_out * 4, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            cudaFreeAsync(buf, s);
+            return set_error(CUT_ERR_OUT_OF_MEMORY, "cut_mlp_fit_linear: weights");
+        }
+    }
+    mlpk::fit_gram_partials<<<dim3((ncol + 127) / 128, chunks), 128, 0, s>>>(x, t, batch, m->n_in, m->n_out, rpc,
+                                                                              partial);
+    mlpk::fit_reduce<<<grid_of((int64_t)P * ncol), 256, 0, s>>>(partial, chunks, (int64_t)P * ncol, M);
+    // a relative ridge of 1e-12 of the Gram matrix's scale keeps the solve
+    // defined when an input never varies
+    mlpk::fit_solve<<<1, 256, 0, s>>>(M, m->n_in, m->n_out, 1e-12 * (double)batch, coef, nullptr);
+    mlpk::fit_resid_partials<<<dim3((m->n_out + 127) / 128, chunks), 128, 0, s>>>(x, t, coef, batch, m->n_in,
+                                                                                   m->n_out, rpc, rp);
+    mlpk::fit_reduce<<<grid_of(m->n_out), 256, 0, s>>>(rp, chunks, m->n_out, ss);
+    mlpk::fit_write<<<grid_of(m->n_out), 256, 0, s>>>(coef, ss, w, batch, m->n_in, m->n_out, m->scale, m->shift,
+                                                      m->J);
+    e = cudaGetLastError();
+    cudaFreeAsync(buf, s);
+    if (w) cudaFreeAsync(w, s);
+    if (e != cudaSuccess) return set_error(CUT_ERR_CUDA, std::string("cut_mlp_fit_linear: ") + cudaGetErrorString(e));
     return set_ok();
 }
 
