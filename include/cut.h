@@ -421,6 +421,15 @@ cut_status cut_mlp_set_linear(cut_mlp *m, const float *J);
  * UNSUPPORTED, OUT_OF_MEMORY, CUDA. */
 cut_status cut_mlp_fit_linear(cut_mlp *m, int batch, const float *x, const double *t, const float *weight,
                               cut_stream_t stream);
+/* Statistics of an ensemble of K independently trained networks on the same
+ * queries, the error signal of the surrogate's gate: mean[b][o] = average
+ * of the K outputs (members summed in order; mean may be NULL) and
+ * spread[b] = max over the outputs with mask[o] != 0 of (max_k - min_k).
+ * host in: preds[K] (device pointers to [batch][n_out] FP32 outputs);
+ * device in: mask[n_out]; device out: mean, spread[batch].  1 <= K <= 16.
+ * Uses the current device.  Errors: INVALID_ARG, CUDA. */
+cut_status cut_mlp_ensemble_stats(int K, int batch, int n_out, const float *const *preds, const uint8_t *mask,
+                                  float *mean, float *spread, cut_stream_t stream);
 /* number of parameters in the flat layout W1, b1, W2, b2, W3, b3 (W [out][in]) */
 int64_t cut_mlp_param_count(const cut_mlp *m);
 /* host out: parameters (grads = 0) or the gradients of the last backward

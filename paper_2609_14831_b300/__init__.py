@@ -122,6 +122,7 @@ def lib():
         "cut_mlp_status": (st, [VP]),
         "cut_mlp_inject_stall": (st, [VP, i]),
         "cut_mlp_fit_linear": (st, [VP, i, VP, VP, VP, VP]),
+        "cut_mlp_ensemble_stats": (st, [i, i, i, VP, VP, VP, VP, VP]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -395,6 +396,21 @@ class Graph:
         check(lib().cut_flow_batched(self._h, B, _ptr(H), n_obs, _ptr(X), prec, ctypes.byref(o),
                                      int(tile), _ptr(steps), _ptr(status), _stream(stream)))
         return (H, X, steps, status) if rec is None else (H, X, steps, status, rec)
+
+
+def ensemble_stats(preds, mask, stream=None):
+    """(mean [B, n_out], spread [B]) of K member outputs preds[k] [B, n_out]
+    (FP32 device tensors); spread = max over masked outputs of max - min."""
+    torch = _torch()
+    K = len(preds)
+    B, n_out = preds[0].shape
+    ps = [p.contiguous() for p in preds]
+    arr = (ctypes.c_void_p * K)(*[p.data_ptr() for p in ps])
+    mask = torch.as_tensor(mask, dtype=torch.uint8, device=ps[0].device).contiguous()
+    mean = torch.empty(B, n_out, dtype=torch.float32, device=ps[0].device)
+    spread = torch.empty(B, dtype=torch.float32, device=ps[0].device)
+    check(lib().cut_mlp_ensemble_stats(K, B, n_out, arr, _ptr(mask), _ptr(mean), _ptr(spread), _stream(stream)))
+    return mean, spread
 
 
 class MLP:

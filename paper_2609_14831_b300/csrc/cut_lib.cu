@@ -42,6 +42,10 @@ struct DevCSR {
     uint64_t *rp = nullptr;
     uint2 *rec = nullptr;
     int64_t rows = 0, R = 0;
+    // long rows split into pieces (transposed orders only): rp then bounds
+    // the `rows` pieces, and pieces vr[r] .. vr[r+1]-1 make up row r
+    uint64_t *vr = nullptr;
+    int64_t real_rows = 0;
     int64_t lane_rows = 0;   // rows of the whole stage: picks the lanes per row, so
                              // a shard sums each row exactly as the whole graph does
 };
@@ -73,6 +77,7 @@ struct cut_graph {
         for (auto *c : {&st[0], &st[1], &st[2], &tx, &txi, &th}) {
             cudaFree(c->rp);
             cudaFree(c->rec);
+            cudaFree(c->vr);
         }
         cudaFree(wtab);
         cudaFree(wtab32);
@@ -644,6 +649,58 @@ static void transpose(const std::vector<uint64_t> &rp, const std::vector<uint32_
     });
 }
 
+// Rows much longer than the mean keep one lane group busy long after the
+// others finish.  Split every row of more than kSplitAbove records into
+// pieces of about kPiece records: the kernels sum pieces like rows, and
+// piece_reduce adds the pieces of each row in order (fixed sum order).
+constexpr uint64_t kSplitAbove = 2048, kPiece = 1024;
+
+static cut_status upload_split(DevCSR &d, const std::vector<uint64_t> &rp, const std::vector<uint32_t> &rc,
+                               int64_t &bytes) {
+    const int64_t rows = (int64_t)rp.size() - 1;
+    std::vector<uint64_t> vrp{0}, vr(rows + 1);
+    for (int64_t r = 0; r < rows; r++) {
+        vr[r] = vrp.size() - 1;
+        const uint64_t b = rp[r], len = rp[r + 1] - b;
+        const uint64_t np = len > kSplitAbove ? (len + kPiece - 1) / kPiece : 1;
+        for (uint64_t q = 1; q <= np; q++) vrp.push_back(b + len * q / np);
+    }
+    vr[rows] = vrp.size() - 1;
+    cut_status st = upload_csr(d, vrp, rc, bytes);
+    if (st != CUT_OK) return st;
+    d.real_rows = rows;
+    CUDA_TRY(cudaMalloc(&d.vr, vr.size() * 8));
+    CUDA_TRY(cudaMemcpy(d.vr, vr.data(), vr.size() * 8, cudaMemcpyHostToDevice));
+    bytes += (int64_t)vr.size() * 8;
+    return CUT_OK;
+}
+
+// Sort the records of every row by (first input, second input), rows split
+// over host threads (the order is fixed, so the sums stay reproducible).
+static void sort_rows_by_first(const std::vector<uint64_t> &rp, std::vector<uint32_t> &rc) {
+    const int64_t rows = (int64_t)rp.size() - 1;
+    const int T = (int)std::min<unsigned>(std::max(1u, std::thread::hardware_concurrency()), 16);
+    std::vector<std::thread> th;
+    for (int t = 0; t < T; t++)
+        th.emplace_back([&, t]() {
+            std::vector<uint64_t> key;
+            for (int64_t r = t; r < rows; r += T) {
+                const uint64_t b = rp[r], e = rp[r + 1];
+                key.resize(e - b);
+                for (uint64_t q = b; q < e; q++)
+                    key[q - b] = ((uint64_t)(rc[2 * q] & kIndexMask) << 32 | rc[2 * q + 1]) << 8 |
+                                 (rc[2 * q] >> kIndexBits);
+                std::sort(key.begin(), key.end());
+                for (uint64_t q = b; q < e; q++) {
+                    const uint64_t k2 = key[q - b];
+                    rc[2 * q] = (uint32_t)((k2 & 0xff) << kIndexBits) | (uint32_t)(k2 >> 40);
+                    rc[2 * q + 1] = (uint32_t)((k2 >> 8) & 0xffffffffu);
+                }
+            }
+        });
+    for (auto &x : th) x.join();
+}
+
 static cut_status ensure_transposes(cut_graph *g) {
     std::lock_guard<std::mutex> lk(g->mu);
     if (g->have_T) return CUT_OK;
@@ -652,17 +709,19 @@ static cut_status ensure_transposes(cut_graph *g) {
     std::vector<uint64_t> rp;
     std::vector<uint32_t> rc;
     int64_t bytes = 0;
-    // rows j, entries (code|a, k)
+    // rows j, entries (code|a, k), each row sorted by (a, k) like the forward
+    // rows, so that neighbouring lanes gather neighbouring generator entries
     transpose(H.rp[1], H.rec[1], n, [](int64_t, uint32_t, uint32_t w1) { return (int64_t)w1; },
               [](int64_t, uint32_t w0, uint32_t) { return w0 & kIndexMask; },
               [](int64_t k, uint32_t, uint32_t) { return (uint32_t)k; }, rp, rc);
-    cut_status st = upload_csr(g->tx, rp, rc, bytes);
+    sort_rows_by_first(rp, rc);
+    cut_status st = upload_split(g->tx, rp, rc, bytes);
     if (st != CUT_OK) return st;
     // rows a, entries (code|k, j)
     transpose(H.rp[1], H.rec[1], ng, [](int64_t, uint32_t w0, uint32_t) { return (int64_t)(w0 & kIndexMask); },
               [](int64_t k, uint32_t, uint32_t) { return (uint32_t)k; },
               [](int64_t, uint32_t, uint32_t w1) { return w1; }, rp, rc);
-    st = upload_csr(g->txi, rp, rc, bytes);
+    st = upload_split(g->txi, rp, rc, bytes);
     if (st != CUT_OK) return st;
     // rows r (both inputs of a generator record), entries (code|a, partner)
     {
@@ -688,7 +747,7 @@ static cut_status ensure_transposes(cut_graph *g) {
                 orc[2 * p] = (code << kIndexBits) | (uint32_t)a;
                 orc[2 * p + 1] = i;
             }
-        st = upload_csr(g->th, orp, orc, bytes);
+        st = upload_split(g->th, orp, orc, bytes);
         if (st != CUT_OK) return st;
     }
     g->device_bytes += bytes;
@@ -712,68 +771,102 @@ static void pack_operands(const cut_graph *g, const double *Y, int nops, double 
 }
 
 // bytes of the packed adjoint scratch: two blocks of n x 64 bytes, 32-byte aligned
-static size_t adjoint_scratch_bytes(const cut_graph *g) { return (size_t)g->host.n() * 128 + 64; }
+// operand blocks (two of n x 64 bytes) and the piece sums of the split
+// transposed passes (up to 8 operands)
+static size_t adjoint_scratch_bytes(const cut_graph *g) {
+    const int64_t pieces = std::max(std::max(g->tx.rows, g->txi.rows), g->th.rows);
+    return (size_t)g->host.n() * 128 + (size_t)pieces * 64 + 128;
+}
 
 // VJP of the stacked RHS at Y with cotangent W: YB = J(Y)^T W.  xi, xib:
 // scratch [n_g]; xbar0: scratch [n]; pk: adjoint_scratch_bytes(g) of scratch
-// (null: the one-gather-per-operand kernels).
+// (packed operand blocks and the piece sums of split rows).
 static void stacked_vjp(const cut_graph *g, const double *Y, const double *W, double *YB, int nops, double *xi,
-                        double *xib, double *xbar0, cudaStream_t s, void *pk = nullptr) {
+                        double *xib, double *xbar0, cudaStream_t s, void *pk) {
     const int64_t n = g->host.n(), ng = g->host.n_g();
     const int nc = (int)g->host.num.size();
     launch_gen(g, Y, xi, s, nullptr);
-    if (pk && nops <= 8) {
+    if (nops <= 8) {
         // operand transposes: x_bar_o[j] = sum beta xi[a] w_o[k] is the forward
         // commutator's form over the rows-by-j records (W packed into W4)
         double *W4 = reinterpret_cast<double *>(((uintptr_t)pk + 31) & ~(uintptr_t)31);
         double *X4 = W4 + 8 * n;
+        double *piece = X4 + 8 * n;   // piece sums [nops][pieces]
         const double *ws[8];
         double *xb[8];
-        for (int o = 0; o < nops; o++) { ws[o] = W + o * n; xb[o] = o == 0 ? xbar0 : YB + o * n; }
+        const int64_t ptx = g->tx.rows;
+        for (int o = 0; o < nops; o++) { ws[o] = W + o * n; xb[o] = piece + o * ptx; }
         launch_comm(g, xi, nops, ws, xb, s, nullptr, 1, W4, &g->tx);
+        {
+            k::Ops<8> red;
+            for (int o = 0; o < nops; o++) { red.x[o] = piece + o * ptx; red.dx[o] = o == 0 ? xbar0 : YB + o * n; }
+            k::piece_reduce<<<grid_for_len(n), 256, 0, s>>>(g->tx.vr, n, red, nops, nullptr);
+        }
         pack_operands(g, Y, nops, X4, s);
         const k::Weights w = weights_of(g);
         const DevCSR &cx = g->txi, &ch = g->th;
         const int lx = comm_lanes(cx.rows), lh = gen_lanes(ch.rows);
+        double *xpiece = piece, *hpiece = piece + std::max<int64_t>(cx.rows, 1);
         switch (nops) {
 #define CASE(M)                                                                                                 \
     case M:                                                                                                     \
         if (w.uniform) {                                                                                        \
-            if (lx == 8) k::commT_xi_x4<M, true, 8><<<grid_for_groups(cx.rows, 8), k::kBlock, 0, s>>>(cx.rp, cx.rec, w, W4, X4, xib, cx.rows); \
-            else k::commT_xi_x4<M, true, 32><<<grid_for_groups(cx.rows, 32), k::kBlock, 0, s>>>(cx.rp, cx.rec, w, W4, X4, xib, cx.rows); \
+            if (lx == 8) k::commT_xi_x4<M, true, 8><<<grid_for_groups(cx.rows, 8), k::kBlock, 0, s>>>(cx.rp, cx.rec, w, W4, X4, xpiece, cx.rows); \
+            else k::commT_xi_x4<M, true, 32><<<grid_for_groups(cx.rows, 32), k::kBlock, 0, s>>>(cx.rp, cx.rec, w, W4, X4, xpiece, cx.rows); \
         } else {                                                                                                \
-            if (lx == 8) k::commT_xi_x4<M, false, 8><<<grid_for_groups(cx.rows, 8), k::kBlock, 0, s>>>(cx.rp, cx.rec, w, W4, X4, xib, cx.rows); \
-            else k::commT_xi_x4<M, false, 32><<<grid_for_groups(cx.rows, 32), k::kBlock, 0, s>>>(cx.rp, cx.rec, w, W4, X4, xib, cx.rows); \
+            if (lx == 8) k::commT_xi_x4<M, false, 8><<<grid_for_groups(cx.rows, 8), k::kBlock, 0, s>>>(cx.rp, cx.rec, w, W4, X4, xpiece, cx.rows); \
+            else k::commT_xi_x4<M, false, 32><<<grid_for_groups(cx.rows, 32), k::kBlock, 0, s>>>(cx.rp, cx.rec, w, W4, X4, xpiece, cx.rows); \
         }                                                                                                       \
         break;
             CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
 #undef CASE
         }
+        {
+            k::Ops<8> red;
+            red.x[0] = xpiece;
+            red.dx[0] = xib;
+            k::piece_reduce<<<grid_for_len(ng), 256, 0, s>>>(cx.vr, ng, red, 1, nullptr);
+        }
+        // the rows of the diagonal coordinates hold most of the generator
+        // records (every generator record has one diagonal input) and are
+        // split into pieces like the other transposed orders
         if (w.uniform) {
-            if (lh == 4) k::genT_lanes<true, 4><<<grid_for_groups(ch.rows, 4), k::kBlock, 0, s>>>(ch.rp, ch.rec, w, xib, Y, xbar0, YB, ch.rows);
-            else k::genT_lanes<true, 8><<<grid_for_groups(ch.rows, 8), k::kBlock, 0, s>>>(ch.rp, ch.rec, w, xib, Y, xbar0, YB, ch.rows);
+            if (lh == 4) k::genT_lanes<true, 4><<<grid_for_groups(ch.rows, 4), k::kBlock, 0, s>>>(ch.rp, ch.rec, w, xib, Y, nullptr, hpiece, ch.rows);
+            else k::genT_lanes<true, 8><<<grid_for_groups(ch.rows, 8), k::kBlock, 0, s>>>(ch.rp, ch.rec, w, xib, Y, nullptr, hpiece, ch.rows);
         } else {
-            if (lh == 4) k::genT_lanes<false, 4><<<grid_for_groups(ch.rows, 4), k::kBlock, 0, s>>>(ch.rp, ch.rec, w, xib, Y, xbar0, YB, ch.rows);
-            else k::genT_lanes<false, 8><<<grid_for_groups(ch.rows, 8), k::kBlock, 0, s>>>(ch.rp, ch.rec, w, xib, Y, xbar0, YB, ch.rows);
+            if (lh == 4) k::genT_lanes<false, 4><<<grid_for_groups(ch.rows, 4), k::kBlock, 0, s>>>(ch.rp, ch.rec, w, xib, Y, nullptr, hpiece, ch.rows);
+            else k::genT_lanes<false, 8><<<grid_for_groups(ch.rows, 8), k::kBlock, 0, s>>>(ch.rp, ch.rec, w, xib, Y, nullptr, hpiece, ch.rows);
+        }
+        {
+            k::Ops<8> red;
+            red.x[0] = hpiece;
+            red.dx[0] = YB;
+            k::piece_reduce<<<grid_for_len(n), 256, 0, s>>>(ch.vr, n, red, 1, xbar0);
         }
         return;
     }
-    // x_bar_o = L(h)^T w_o ; operand 0's goes to scratch, then into h_bar
+    // more than eight operands: one gather per operand, four operands per
+    // pass, over the same pieces
+    double *piece = reinterpret_cast<double *>(((uintptr_t)pk + 31) & ~(uintptr_t)31) + 16 * n;
+    const int64_t ptx = g->tx.rows, pxi = g->txi.rows, pth = g->th.rows;
     for (int o0 = 0; o0 < nops; o0 += 4) {
         int m = std::min(4, nops - o0);
         switch (m) {
 #define CASE(M)                                                                              \
     case M: {                                                                                \
         k::Ops<M> ops;                                                                       \
-        for (int t = 0; t < M; t++) {                                                        \
-            ops.x[t] = W + (o0 + t) * n;                                                     \
-            ops.dx[t] = (o0 + t == 0) ? xbar0 : YB + (o0 + t) * n;                           \
-        }                                                                                    \
-        k::commT_x<M><<<grid_for_rows(n), k::kBlock, 0, s>>>(g->tx.rp, g->tx.rec, g->wtab, nc, xi, ops, n); \
+        for (int t = 0; t < M; t++) { ops.x[t] = W + (o0 + t) * n; ops.dx[t] = piece + t * ptx; } \
+        k::commT_x<M><<<grid_for_rows(ptx), k::kBlock, 0, s>>>(g->tx.rp, g->tx.rec, g->wtab, nc, xi, ops, ptx); \
     } break;
             CASE(1) CASE(2) CASE(3) CASE(4)
 #undef CASE
         }
+        k::Ops<8> red;
+        for (int t = 0; t < m; t++) {
+            red.x[t] = piece + t * ptx;
+            red.dx[t] = (o0 + t == 0) ? xbar0 : YB + (o0 + t) * n;
+        }
+        k::piece_reduce<<<grid_for_len(n), 256, 0, s>>>(g->tx.vr, n, red, m, nullptr);
     }
     for (int o0 = 0; o0 < nops; o0 += 4) {
         int m = std::min(4, nops - o0);
@@ -782,13 +875,25 @@ static void stacked_vjp(const cut_graph *g, const double *Y, const double *W, do
     case M: {                                                                                \
         k::Pairs<M> pr;                                                                      \
         for (int t = 0; t < M; t++) { pr.x[t] = Y + (o0 + t) * n; pr.w[t] = W + (o0 + t) * n; } \
-        k::commT_xi<M><<<grid_for_rows(ng), k::kBlock, 0, s>>>(g->txi.rp, g->txi.rec, g->wtab, nc, pr, xib, ng, o0 > 0); \
+        k::commT_xi<M><<<grid_for_rows(pxi), k::kBlock, 0, s>>>(g->txi.rp, g->txi.rec, g->wtab, nc, pr, piece, pxi, o0 > 0); \
     } break;
             CASE(1) CASE(2) CASE(3) CASE(4)
 #undef CASE
         }
     }
-    k::genT<<<grid_for_rows(n), k::kBlock, 0, s>>>(g->th.rp, g->th.rec, g->wtab, nc, xib, Y, xbar0, YB, n);
+    {
+        k::Ops<8> red;
+        red.x[0] = piece;
+        red.dx[0] = xib;
+        k::piece_reduce<<<grid_for_len(ng), 256, 0, s>>>(g->txi.vr, ng, red, 1, nullptr);
+    }
+    k::genT<<<grid_for_rows(pth), k::kBlock, 0, s>>>(g->th.rp, g->th.rec, g->wtab, nc, xib, Y, nullptr, piece, pth);
+    {
+        k::Ops<8> red;
+        red.x[0] = piece;
+        red.dx[0] = YB;
+        k::piece_reduce<<<grid_for_len(n), 256, 0, s>>>(g->th.vr, n, red, 1, xbar0);
+    }
 }
 
 }  // namespace cut

@@ -628,6 +628,20 @@ __global__ void __launch_bounds__(kBlock) genT_lanes(const uint64_t *__restrict_
     }
 }
 
+// Rows split into pieces: out_o[r] = add[r] (operand 0, if given) + the
+// piece sums in_o[v] for v = vr[r] .. vr[r+1]-1, added in piece order.
+__global__ void piece_reduce(const uint64_t *__restrict__ vr, int64_t rows, Ops<8> io, int nops,
+                             const double *__restrict__ add) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t v0 = vr[r], v1 = vr[r + 1];
+        for (int o = 0; o < nops; o++) {
+            double acc = io.x[o][v0];
+            for (uint64_t v = v0 + 1; v < v1; v++) acc += io.x[o][v];
+            io.dx[o][r] = (add && o == 0) ? add[r] + acc : acc;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- RK algebra
 // out = base + sum_s coef_s * ds * K_s   (coefficients scaled by *ds_ptr
 // when ds_ptr is given, else by ds_const); vectors of length len.

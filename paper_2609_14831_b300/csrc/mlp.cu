@@ -299,6 +299,38 @@ __global__ void fit_write(const double *__restrict__ coef, const double *__restr
     }
 }
 
+// ---- ensemble statistics of K surrogate networks (the gate's error signal)
+struct Members {
+    const float *p[16];
+};
+
+// One CTA per query row: mean[b][o] = (1/K) sum_k p_k[b][o] (members in
+// order) and spread[b] = max over the masked outputs of max_k - min_k.
+__global__ void __launch_bounds__(256) ensemble_stats(Members m, int K, int n_out, const uint8_t *__restrict__ mask,
+                                                      float *__restrict__ mean, float *__restrict__ spread) {
+    __shared__ float red[256];
+    const int64_t b = blockIdx.x;
+    float sp = 0.0f;
+    for (int o = threadIdx.x; o < n_out; o += blockDim.x) {
+        float sum = 0.0f, lo = 3.0e38f, hi = -3.0e38f;
+        for (int k = 0; k < K; k++) {
+            const float v = m.p[k][b * n_out + o];
+            sum += v;
+            lo = fminf(lo, v);
+            hi = fmaxf(hi, v);
+        }
+        if (mean) mean[b * n_out + o] = sum / (float)K;
+        if (mask[o]) sp = fmaxf(sp, hi - lo);
+    }
+    red[threadIdx.x] = sp;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + st]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) spread[b] = red[0];
+}
+
 }  // namespace mlpk
 
 static int pad_to(int v, int q) { return (v + q - 1) / q * q; }
@@ -650,6 +682,22 @@ cut_status cut_mlp_fit_linear(cut_mlp *m, int batch, const float *x, const doubl
     cudaFreeAsync(buf, s);
     if (w) cudaFreeAsync(w, s);
     if (e != cudaSuccess) return set_error(CUT_ERR_CUDA, std::string("cut_mlp_fit_linear: ") + cudaGetErrorString(e));
+    return set_ok();
+}
+
+cut_status cut_mlp_ensemble_stats(int K, int batch, int n_out, const float *const *preds, const uint8_t *mask,
+                                  float *mean, float *spread, cut_stream_t stream) {
+    if (K < 1 || K > 16 || batch < 0 || n_out < 1 || !preds || !mask || !spread)
+        return set_error(CUT_ERR_INVALID_ARG, "cut_mlp_ensemble_stats: bad argument (1 <= K <= 16)");
+    mlpk::Members mb;
+    for (int k = 0; k < K; k++) {
+        if (!preds[k]) return set_error(CUT_ERR_INVALID_ARG, "cut_mlp_ensemble_stats: null member output");
+        mb.p[k] = preds[k];
+    }
+    if (batch == 0) return set_ok();
+    mlpk::ensemble_stats<<<batch, 256, 0, (cudaStream_t)stream>>>(mb, K, n_out, mask, mean, spread);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(CUT_ERR_CUDA, std::string("cut_mlp_ensemble_stats: ") + cudaGetErrorString(e));
     return set_ok();
 }
 

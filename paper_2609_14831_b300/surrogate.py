@@ -1,16 +1,22 @@
 """Learned surrogate of the flow map theta -> flowed coefficients.
 
-Not in the paper: a warm start and screen in front of the graph flow, which
-stays the fallback and the judge of the surrogate's error.  Every numerical
-step runs in libcut.so: training data come from the batched flow kernel
-(FP32 records, FP64 state), the network is trained by the library's tcgen05
-forward/backward GEMMs and AdamW kernel, and rejected queries go through the
-FP64 batched flow.
+Not in the paper: a screen in front of the graph flow, which stays the
+fallback and the judge of the surrogate's error.  Every numerical step runs
+in libcut.so: training data come from the batched flow kernel (FP32 records,
+FP64 state); the linear part of the map is fitted on the device in FP64
+(cut_mlp_fit_linear) and each network learns what it misses with the
+library's tcgen05 forward/backward GEMMs and AdamW kernel; rejected queries go
+through the FP64 batched flow.
 
-Screening rule (a reading of "fallback when the error exceeds tol"): each
-query is flowed once with the loose FP32 batched flow; if the network's
-prediction of any screened coefficient differs from it by more than `tol`,
-the query falls back to the full FP64 flow, otherwise the prediction is used.
+The gate (a reading of "fallback when the error exceeds tol"; the error
+estimator is not stated): K networks trained from different initial weights
+and data orders answer every query; their spread on the screened
+coefficients (max over the coefficients of max - min over the members,
+cut_mlp_ensemble_stats) is the error signal, and no flow runs for a query
+the gate accepts.  The threshold tau on the spread is calibrated on
+validation queries with FP64 flows: the largest tau for which every
+validation query with spread <= tau has error <= tol.  The ensemble mean is
+the served answer; the other queries fall back to the FP64 flow.
 """
 import time
 
@@ -20,7 +26,7 @@ import paper_2609_14831_b300 as cg
 
 
 class Surrogate:
-    def __init__(self, graph, h_ref, P, observables, n_hidden=512, seed=0, s1=10.0,
+    def __init__(self, graph, h_ref, P, observables, n_hidden=512, members=2, seed=0, s1=10.0,
                  loose_rtol=1e-6, tight_rtol=1e-10, atol=1e-12):
         import torch
         self.torch = torch
@@ -33,16 +39,19 @@ class Surrogate:
         self.n_in = self.P.shape[1]
         self.s1 = s1
         self.loose_rtol, self.tight_rtol, self.atol = loose_rtol, tight_rtol, atol
-        self.net = cg.MLP(self.n_in, n_hidden, self.n, seed=seed, device=graph.device_index)
+        self.nets = [cg.MLP(self.n_in, n_hidden, self.n, seed=seed + 7919 * k, device=graph.device_index)
+                     for k in range(members)]
         self.theta_scale = 1.0
+        self.tau = None
 
     def _h0(self, theta):
         torch = self.torch
         theta = torch.as_tensor(theta, dtype=torch.float64, device=self.dev)
         return self.h_ref[None, :] + theta @ self.P.T
 
-    def flows(self, theta, precision="fp32", chunk=8192):
-        """Flowed H for every parameter vector (batched kernel)."""
+    def flows(self, theta, precision="fp32", chunk=8192, tile=0):
+        """Flowed H for every parameter vector (batched kernel; tile 0 =
+        autotuned width, which probes every width on a new batch size)."""
         torch = self.torch
         theta = torch.as_tensor(theta, dtype=torch.float64, device=self.dev)
         outs, steps = [], []
@@ -52,83 +61,139 @@ class Surrogate:
             rtol = self.loose_rtol if precision == "fp32" else self.tight_rtol
             atol = 1e-9 if precision == "fp32" else self.atol
             H, _, st, status = self.G.flow_batched(H0, X0, precision=precision, method="dp45", s0=0.0,
-                                                   s1=self.s1, ds=1e-2, rtol=rtol, atol=atol)
+                                                   s1=self.s1, ds=1e-2, rtol=rtol, atol=atol, tile=tile)
             if int(status.abs().max().item()) != 0:
                 raise cg.CutError(int(status.abs().max().item()), "batched flow failed for some instance")
             outs.append(H)
             steps.append(st)
         return torch.cat(outs), torch.cat(steps)
 
-    def fit(self, theta, targets, epochs=40, batch=512, lr=2e-3, weight_decay=0.0, seed=0, log=None):
-        """Standardise the targets, then AdamW on the MSE (library kernels)."""
+    def _x(self, theta):
+        torch = self.torch
+        return (torch.as_tensor(theta, dtype=torch.float32, device=self.dev) / self.theta_scale).contiguous()
+
+    def fit(self, theta, targets, epochs=40, batch=512, lr=2e-3, weight_decay=0.0, seed=0, weight=None, log=None):
+        """Device least-squares affine part, then AdamW on the standardised
+        MSE of each member (library kernels).  `weight` (per output, > 0)
+        makes the chosen outputs count more in the loss.  Returns the mean
+        batch loss per epoch of every member."""
         torch = self.torch
         theta = torch.as_tensor(theta, dtype=torch.float32, device=self.dev)
-        targets = torch.as_tensor(targets, dtype=torch.float64, device=self.dev)
+        targets = torch.as_tensor(targets, dtype=torch.float64, device=self.dev).contiguous()
         self.theta_scale = float(theta.abs().max().item()) or 1.0
         x = (theta / self.theta_scale).contiguous()
-        # linear part by least squares (FP64), the network learns the rest
-        A = torch.cat([torch.ones(x.shape[0], 1, dtype=torch.float64, device=self.dev), x.double()], dim=1)
-        coef = torch.linalg.lstsq(A, targets).solution               # [1 + n_in, n]
-        mu, J = coef[0], coef[1:].T.contiguous()
-        resid = targets - A @ coef
-        sd = resid.std(0).clamp_min(1e-9)
-        self.mu, self.sd, self.J = mu, sd, J
-        self.net.set_output_affine(sd.float().cpu().numpy(), mu.float().cpu().numpy())
-        self.net.set_linear(J.float().cpu().numpy())
         t32 = targets.float()
-        g = torch.Generator(device="cpu").manual_seed(seed)
         N = x.shape[0]
         steps = max(1, N // batch)
         total = epochs * steps
-        hist = []
-        it = 0
-        # fixed staging buffers: every step reuses the same device pointers, so
-        # the library replays its captured forward/backward graph
-        xs = torch.empty(min(batch, N), x.shape[1], dtype=torch.float32, device=self.dev)
-        ts = torch.empty(min(batch, N), t32.shape[1], dtype=torch.float32, device=self.dev)
-        loss = torch.zeros(1, dtype=torch.float32, device=self.dev)
-        for ep in range(epochs):
-            perm = torch.randperm(N, generator=g).to(self.dev)
-            loss.zero_()
-            for s in range(steps):
-                idx = perm[s * batch:(s + 1) * batch]
-                torch.index_select(x, 0, idx, out=xs)
-                torch.index_select(t32, 0, idx, out=ts)
-                # cosine learning-rate decay
-                cur = lr * 0.5 * (1 + np.cos(np.pi * it / total))
-                self.net.backward(xs, ts, loss=loss)
-                self.net.step(lr=cur, weight_decay=weight_decay)
-                it += 1
-            hist.append(float(loss.item()) / steps)   # mean batch loss of the epoch
-            if log:
-                log(ep, hist[-1])
-        self.net.status()
-        return hist
+        hists = []
+        for k, net in enumerate(self.nets):
+            net.fit_linear(x, targets, weight)
+            g = torch.Generator(device="cpu").manual_seed(seed + 104729 * k)
+            # fixed staging buffers: every step reuses the same device pointers,
+            # so the library replays its captured forward/backward graph
+            xs = torch.empty(min(batch, N), x.shape[1], dtype=torch.float32, device=self.dev)
+            ts = torch.empty(min(batch, N), t32.shape[1], dtype=torch.float32, device=self.dev)
+            loss = torch.zeros(1, dtype=torch.float32, device=self.dev)
+            hist, it = [], 0
+            for ep in range(epochs):
+                perm = torch.randperm(N, generator=g).to(self.dev)
+                loss.zero_()
+                for s in range(steps):
+                    idx = perm[s * batch:(s + 1) * batch]
+                    torch.index_select(x, 0, idx, out=xs)
+                    torch.index_select(t32, 0, idx, out=ts)
+                    cur = lr * 0.5 * (1 + np.cos(np.pi * it / total))   # cosine decay
+                    net.backward(xs, ts, loss=loss)
+                    net.step(lr=cur, weight_decay=weight_decay)
+                    it += 1
+                hist.append(float(loss.item()) / steps)
+                if log:
+                    log(k, ep, hist[-1])
+            net.status()
+            hists.append(hist)
+        return hists
 
-    def predict(self, theta):
-        torch = self.torch
-        x = (torch.as_tensor(theta, dtype=torch.float32, device=self.dev) / self.theta_scale).contiguous()
-        return self.net.forward(x).double()
+    def predict_members(self, theta):
+        x = self._x(theta)
+        return [net.forward(x) for net in self.nets]
 
-    def screen(self, theta, screened_idx, tol=1e-4):
-        """Surrogate + fallback.  Returns (H, used_network mask, timings)."""
+    def predict(self, theta, screened_idx=None):
+        """(ensemble mean [B, n] FP64, spread [B] over the screened outputs)."""
+        preds = self.predict_members(theta)
+        mask = np.zeros(self.n, dtype=np.uint8)
+        mask[np.asarray(screened_idx if screened_idx is not None else np.arange(self.n))] = 1
+        mean, spread = cg.ensemble_stats(preds, mask)
+        return mean.double(), spread
+
+    def calibrate(self, theta, exact, screened_idx, tol):
+        """tau = the largest spread for which every validation query with a
+        spread no larger has error <= tol on the screened outputs (-1: none)."""
         torch = self.torch
+        mean, spread = self.predict(theta, screened_idx)
+        idx = torch.as_tensor(np.asarray(screened_idx), device=self.dev)
+        err = (mean[:, idx] - exact[:, idx]).abs().max(dim=1).values.cpu().numpy()
+        sp = spread.cpu().numpy().astype(np.float64)
+        order = np.argsort(sp, kind="stable")
+        worst = np.maximum.accumulate(err[order])
+        ok = np.nonzero(worst <= tol)[0]
+        self.tau = float(sp[order[ok[-1]]]) if ok.size else -1.0
+        return self.tau, float(np.mean(sp <= self.tau))
+
+    def fallback(self, theta):
+        """FP64 flows of the rejected queries.  A batched flow's wall time is
+        set by its longest instance run on few SMs, so a handful of queries
+        is faster through the single-instance flow (all SMs on one
+        instance); larger sets take the batched kernel at a fixed tile
+        width (no autotuning inside a served call)."""
+        torch = self.torch
+        theta = np.asarray(theta)
+        if len(theta) > self.plain_max:
+            H0 = self._h0(theta)
+            X0 = self.obs[None].expand(H0.shape[0], -1, -1).contiguous()
+            H, _, _, status = self.G.flow_batched(H0, X0, precision="fp64", method="dp45", s0=0.0, s1=self.s1,
+                                                  ds=1e-2, rtol=self.tight_rtol, atol=self.atol, tile=8)
+            if int(status.abs().max().item()) != 0:
+                raise cg.CutError(int(status.abs().max().item()), "fallback flow failed")
+            return H
+        H0 = self._h0(theta)
+        outs = []
+        for b in range(len(theta)):
+            h, _, _, _ = self.G.flow(H0[b], list(self.obs), method="dp45", s0=0.0, s1=self.s1, ds=1e-2,
+                                     rtol=self.tight_rtol, atol=self.atol)
+            outs.append(h)
+        return torch.stack(outs)
+
+    plain_max = 32
+
+    def screen(self, theta, screened_idx):
+        """Served answers: the ensemble mean where the spread is <= tau, the
+        FP64 flow elsewhere.  Returns (H, accepted mask (numpy), timings)."""
+        torch = self.torch
+        assert self.tau is not None, "calibrate() first"
+        theta = np.asarray(theta)
         t0 = time.perf_counter()
-        pred = self.predict(theta)
-        torch.cuda.synchronize()
+        mean, spread = self.predict(theta, screened_idx)
+        ok = spread.cpu().numpy().astype(np.float64) <= self.tau
         t1 = time.perf_counter()
-        loose, _ = self.flows(theta, "fp32")
+        rej = np.nonzero(~ok)[0]
+        if rej.size:
+            mean[torch.as_tensor(rej, device=self.dev)] = self.fallback(theta[rej])
         torch.cuda.synchronize()
         t2 = time.perf_counter()
-        idx = torch.as_tensor(screened_idx, device=self.dev)
-        err = (pred[:, idx] - loose[:, idx]).abs().max(dim=1).values
-        ok = err <= tol
-        out = pred.clone()
-        rej = torch.nonzero(~ok).flatten()
-        if rej.numel():
-            tight, _ = self.flows(theta[rej.cpu().numpy()] if isinstance(theta, np.ndarray) else theta[rej], "fp64")
-            out[rej] = tight
+        return mean, ok, {"predict_s": t1 - t0, "fallback_s": t2 - t1, "accepted": int(ok.sum()),
+                          "queries": int(ok.size)}
+
+    def rank_screen(self, theta, coef, frac):
+        """Rank queries by the ensemble's predicted coefficient `coef` and
+        flow (FP64) only the best-ranked `frac` of them: returns (indices of
+        the flowed queries, their exact coefficient, seconds)."""
+        torch = self.torch
+        t0 = time.perf_counter()
+        mean, _ = self.predict(theta, [coef])
+        order = torch.argsort(mean[:, coef]).cpu().numpy()
+        chosen = np.sort(order[: int(frac * len(order))])
+        th = theta[chosen] if isinstance(theta, np.ndarray) else theta[torch.as_tensor(chosen, device=self.dev)]
+        exact, _ = self.flows(th, "fp64", tile=8)
         torch.cuda.synchronize()
-        t3 = time.perf_counter()
-        return out, ok, {"predict_s": t1 - t0, "loose_s": t2 - t1, "fallback_s": t3 - t2,
-                         "accepted": int(ok.sum().item()), "queries": int(ok.numel())}
+        return chosen, exact[:, coef], time.perf_counter() - t0

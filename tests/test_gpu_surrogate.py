@@ -1,23 +1,31 @@
 """The learned surrogate: trained by the library's own kernels on flows the
-batched path generates; checked for what it gains over the plain flow.
+batched path generates; checked for what it gains over the method without it.
 
 Small-scale version of the surrogate workload (the benchmark's --surrogate
 mode runs the 50k-flow one): 8-spin-orbital model, 32 parameters
 theta ~ U(-0.1, 0.1) about the reference Hamiltonian, training set from
-FP32-record batched flows, held-out queries checked against FP64 flows.
+FP32-record batched flows, validation and held-out queries judged by FP64
+flows.  Two networks (different initial weights and data orders) form the
+ensemble whose spread is the gate's error signal; the 36 flowed diagonal
+coefficients weigh 64x in the loss.
 
-Two uses are measured:
-  * screen: find the 10% of queries with the lowest flowed coefficient of n_0
-    (the lowest orbital) by ranking the network's predictions and running the
-    FP64 flow only on the best-ranked 30%; the gain is the FP64 flows avoided
-    at the measured recall;
-  * gate: answers whose prediction of the lowest diagonal coefficient (n_0,
-    the quantity the gradient workload targets) is within 1e-4 of a loose
-    FP32 flow are served by the network, the rest by the FP64 flow -- every
-    answer must then be within the gate of the FP64 flow.  The same gate on
-    all 36 diagonal coefficients is reported (the two-particle diagonals
-    vary roughly with theta near the degenerate pair energies).
+What the network must show:
+  * it learns beyond its own linear part: on held-out queries its error on
+    the lowest diagonal coefficient n_0 is at most half that of the
+    least-squares affine map alone (fitted here with numpy);
+  * the training loss falls below half its first-epoch value: after the
+    affine fit the standardised targets have unit variance per output, so a
+    network that explains none of the residual stays at or above 1;
+  * gate on n_0 at 1e-4: the ensemble answers most held-out queries with no
+    flow at all, every served answer is within 1e-4 of the FP64 flow, and
+    gate + fallback take less time than the FP64 flows of every query;
+  * screen: the true lowest 10% of n_0 among the best-ranked 30% (recall
+    >= 0.9), i.e. 70% of the FP64 flows avoided.
+The same gate on all 36 diagonal coefficients is reported (the network does
+not reach 1e-4 on the two-particle diagonals at this training size).
 """
+import time
+
 import numpy as np
 import pytest
 
@@ -27,45 +35,65 @@ from cut_inputs import make_label, parameter_directions, workload
 pytestmark = pytest.mark.gpu
 
 
-def test_surrogate_screen_and_gate():
+def test_surrogate_gate_and_screen_gain_over_the_plain_flow():
+    import torch
     from paper_2609_14831_b300.surrogate import Surrogate
     w = workload("molecular_8so")
     G = graph_for("mol8", w.alg, w.nmodes, w.labels)
     P = parameter_directions(w.labels, 8)
-    sur = Surrogate(G, w.h, P, w.observables, n_hidden=512, seed=0)
+    n = len(w.labels)
+    diag = np.nonzero([int(l) & 0xFFFFFFFF == int(l) >> 32 for l in w.labels])[0]
+    k0 = int(np.nonzero(w.labels == np.uint64(make_label(1, 1)))[0][0])
+    weight = np.ones(n, dtype=np.float32)
+    weight[diag] = 64.0
+    sur = Surrogate(G, w.h, P, w.observables, n_hidden=512, members=2, seed=0)
     rng = np.random.default_rng(50)
     th_train = rng.uniform(-0.1, 0.1, size=(4096, 32))
+    th_val = rng.uniform(-0.1, 0.1, size=(512, 32))
     th_test = rng.uniform(-0.1, 0.1, size=(512, 32))
     Htr, steps = sur.flows(th_train, "fp32")
     assert len(set(steps.cpu().numpy().tolist())) > 1
-    hist = sur.fit(th_train, Htr, epochs=200, batch=256, lr=3e-3)
-    print(f"training loss {hist[0]:.3e} -> {hist[-1]:.3e}")
-    assert hist[-1] < 0.2 * hist[0]
-    k0 = int(np.nonzero(w.labels == np.uint64(make_label(1, 1)))[0][0])
+    hists = sur.fit(th_train, Htr, epochs=200, batch=256, lr=3e-3, weight=weight)
+    for h in hists:
+        print(f"training loss {h[0]:.6e} -> {h[-1]:.6e}")
+        assert h[-1] < 0.5 * h[0]
+    exact_val, _ = sur.flows(th_val, "fp64")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     exact, _ = sur.flows(th_test, "fp64")
-    pred = sur.predict(th_test)
-    e_true = exact[:, k0].cpu().numpy()
-    e_pred = pred[:, k0].cpu().numpy()
-    # screen: recall of the true lowest 10% among the best-ranked 30%
-    m = len(e_true)
-    target = set(np.argsort(e_true)[: m // 10].tolist())
-    chosen = set(np.argsort(e_pred)[: (3 * m) // 10].tolist())
-    recall = len(target & chosen) / len(target)
-    print(f"screen: recall {recall:.3f} flowing 30% of the queries; |err(n_0)| median "
-          f"{np.median(np.abs(e_pred - e_true)):.2e}")
-    assert recall >= 0.9
-    # gate on the lowest diagonal coefficient: every served answer within
-    # 1e-4 (+ the loose flow's own error) of the FP64 flow
-    out, ok, tm = sur.screen(th_test, [k0], tol=1e-4)
-    ok = ok.cpu().numpy()
+    torch.cuda.synchronize()
+    t_flow = time.perf_counter() - t0
+    mean, _ = sur.predict(th_test, [k0])
+    e_net = np.abs(mean[:, k0].cpu().numpy() - exact[:, k0].cpu().numpy())
+    # the affine map alone (numpy least squares on the same training data)
+    A = np.concatenate([np.ones((len(th_train), 1)), th_train], 1)
+    coef, *_ = np.linalg.lstsq(A, Htr[:, k0].cpu().numpy(), rcond=None)
+    e_lin = np.abs(np.concatenate([np.ones((len(th_test), 1)), th_test], 1) @ coef - exact[:, k0].cpu().numpy())
+    print(f"n_0 held-out error: network median {np.median(e_net):.2e}, affine map alone {np.median(e_lin):.2e}")
+    assert np.median(e_net) <= 0.5 * np.median(e_lin)
+    # gate on n_0
+    tau, frac_val = sur.calibrate(th_val, exact_val, [k0], 1e-4)
+    sur.screen(th_val[:64], [k0])                 # warm-up of the served path
+    out, ok, tm = sur.screen(th_test, [k0])
     err = (out[:, k0] - exact[:, k0]).abs().cpu().numpy()
-    print(f"gate (n_0): served by the network {ok.sum()}/{len(ok)}, timings {tm}")
-    assert np.all(err <= 1e-4 + 1e-5)
-    if (~ok).any():
-        assert np.all(err[~ok] <= 1e-8)
+    t_gate = tm["predict_s"] + tm["fallback_s"]
+    print(f"gate (n_0, 1e-4): tau {tau:.2e}, served by the network {ok.sum()}/{len(ok)}, max served error "
+          f"{err[ok].max() if ok.any() else 0:.2e}; {t_gate:.3f} s against {t_flow:.3f} s of FP64 flows")
     assert ok.mean() > 0.5
+    assert np.all(err[ok] <= 1e-4)
+    assert np.all(err[~ok] <= 1e-8)
+    assert t_gate < t_flow
     # the same gate on all 36 diagonal coefficients (reported)
-    diag = np.nonzero([int(l) & 0xFFFFFFFF == int(l) >> 32 for l in w.labels])[0]
-    e36 = (pred[:, diag] - exact[:, diag]).abs().max(dim=1).values.cpu().numpy()
-    print(f"all 36 diagonals: network max error per query median {np.median(e36):.2e}, "
-          f"within 1e-4: {np.mean(e36 <= 1e-4):.3f}")
+    tau36, frac36 = sur.calibrate(th_val, exact_val, diag, 1e-4)
+    m36, sp36 = sur.predict(th_test, diag)
+    e36 = (m36[:, diag] - exact[:, diag]).abs().max(dim=1).values.cpu().numpy()
+    acc36 = sp36.double().cpu().numpy() <= tau36
+    print(f"all 36 diagonals: ensemble error per query median {np.median(e36):.2e}; gate at 1e-4 serves "
+          f"{acc36.mean():.3f} of held-out queries (max served error {e36[acc36].max() if acc36.any() else 0:.2e})")
+    # screen: recall of the true lowest 10% among the best-ranked 30%
+    chosen, vals, t_scr = sur.rank_screen(th_test, k0, 0.3)
+    e_true = exact[:, k0].cpu().numpy()
+    target = set(np.argsort(e_true)[: len(e_true) // 10].tolist())
+    recall = len(target & set(chosen.tolist())) / len(target)
+    print(f"screen: recall {recall:.3f} flowing 30% of the queries ({t_scr:.3f} s against {t_flow:.3f} s)")
+    assert recall >= 0.9
