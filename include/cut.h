@@ -157,7 +157,12 @@ cut_status cut_graph_records(const cut_graph *g, int stage, int64_t *row_ptr, in
  * device out: dh[n], dx[n_obs][n], xi_out[n_g] (optional, NULL = not kept)
  * Runs asynchronously on `stream`; takes its scratch (the packed operand
  * blocks, n x 64 bytes, and the generator when xi_out is NULL) from the
- * stream-ordered allocator and returns it on the same stream.
+ * stream-ordered allocator and returns it on the same stream.  On a graph
+ * with few long rows (fewer than 16384 rows of 512 or more records on
+ * average) the commutator stage cuts each row into pieces of about 256
+ * records, sums the pieces and then each row's pieces in order (64 more
+ * bytes of scratch per piece); a row's cut depends only on its length, so
+ * the result is the same on every run and on every shard.
  * Errors: INVALID_ARG, CUDA. */
 cut_status cut_rhs(const cut_graph *g, const double *h, int n_obs, const double *x, double *dh,
                    double *dx, double *xi_out, cut_stream_t stream);
@@ -227,7 +232,9 @@ cut_status cut_rhs_jvp(const cut_graph *g, const double *h, int n_obs, const dou
  * library holds it until the process exits.
  *   - Same inputs, outputs and results as cut_rhs with xi_out = NULL, always
  *     in FP64 arithmetic; the operands are gathered one by one instead of
- *     from packed blocks, with the same sums in the same order (same bits).
+ *     from packed blocks, with the same sums in the same order (same bits;
+ *     on graphs with few long rows, which cut_rhs cuts into pieces, the
+ *     rows are summed whole here, so the two agree to rounding).
  *   - Graphs with more than CUT_RHS_NOALLOC_MAX_NG generator coordinates are
  *     rejected with CUT_ERR_INVALID_ARG before anything is queued.
  *   - Makes no cudaMalloc, cudaFree or other allocating call.
@@ -327,11 +334,16 @@ typedef struct {
                                    [batch][record_cap], row b receives the
                                    accepted step sizes of instance b in order
                                    (entries past its step count are untouched) */
+    int64_t pause_after;     /* cut_flow, DP45 only: > 0 stops the flow after
+                                that many attempts with status OK (a
+                                checkpoint, see cut_flow) */
 } cut_flow_opts;
 
 typedef struct {
     int64_t steps, rejects, rhs_calls;
     double s_final;
+    double ds_next;          /* DP45: the step size the next attempt would take */
+    int finished;            /* 1: reached s1; 0: paused (pause_after) */
 } cut_flow_stats;
 
 /* Integrate the stacked state [h; x_1..x_nobs] from s0 to s1.
@@ -341,6 +353,13 @@ typedef struct {
  * max_k |e_k| / (atol + rtol max(|y_k|, |y5_k|)), accept when <= 1,
  * ds *= clamp(0.9 r^-1/5, 0.2, 5) (growth capped at 1 after a rejection).
  * Synchronises `stream` before returning.
+ * Checkpoint and resume (DP45): with opts->pause_after = m the flow stops
+ * after m attempts and returns OK with the state in h, x and stats->s_final,
+ * stats->ds_next, finished = 0.  The controller's next decision depends only
+ * on (state, s, ds), and every kernel is deterministic, so calling cut_flow
+ * again with s0 = s_final and ds = ds_next (same s1, rtol, atol) continues
+ * exactly where the uninterrupted flow would be: the same accepted steps and
+ * the same bits at s1.
  * Errors: INVALID_ARG, CUDA, NONFINITE (a non-finite state was produced),
  * STEP_UNDERFLOW (ds fell below 1e-14 |s|), MAX_STEPS. */
 cut_status cut_flow(const cut_graph *g, double *h, int n_obs, double *x, const cut_flow_opts *opts,

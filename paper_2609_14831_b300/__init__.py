@@ -59,12 +59,13 @@ class FlowOpts(ctypes.Structure):
                 ("ds", ctypes.c_double), ("rtol", ctypes.c_double), ("atol", ctypes.c_double),
                 ("max_steps", ctypes.c_int64), ("replay_steps", ctypes.POINTER(ctypes.c_double)),
                 ("n_replay", ctypes.c_int64), ("record_steps", ctypes.POINTER(ctypes.c_double)),
-                ("record_cap", ctypes.c_int64), ("batch_record_steps", ctypes.c_void_p)]
+                ("record_cap", ctypes.c_int64), ("batch_record_steps", ctypes.c_void_p),
+                ("pause_after", ctypes.c_int64)]
 
 
 class FlowStats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("rejects", ctypes.c_int64), ("rhs_calls", ctypes.c_int64),
-                ("s_final", ctypes.c_double)]
+                ("s_final", ctypes.c_double), ("ds_next", ctypes.c_double), ("finished", ctypes.c_int)]
 
 
 _lib = None
@@ -340,14 +341,19 @@ class Graph:
         return o, keep, rec
 
     def flow(self, h, xs=(), method="rk4", s0=0.0, s1=10.0, ds=1e-3, rtol=1e-10, atol=0.0,
-             max_steps=0, replay=None, record_cap=1 << 20, stream=None):
-        """Integrate [h; x_1..] from s0 to s1.  Returns (h, xs, stats, accepted_steps)."""
+             max_steps=0, replay=None, record_cap=1 << 20, pause_after=0, stream=None):
+        """Integrate [h; x_1..] from s0 to s1.  Returns (h, xs, stats, accepted_steps).
+
+        DP45 with pause_after = m stops after m attempts (stats["finished"]
+        0); flow(h, xs, s0=stats["s_final"], ds=stats["ds_next"], ...)
+        resumes it exactly."""
         torch = _torch()
         h = _dev_f64(h, self.n, "h", self.device).clone()
         n_obs = len(xs)
         x = torch.stack([_dev_f64(v, self.n, "x", self.device) for v in xs]).clone() if n_obs else None
         o, keep, rec = self._opts(method, s0, s1, ds, rtol, atol, max_steps, replay,
                                   record_cap if method == "dp45" else 0)
+        o.pause_after = int(pause_after)
         st = FlowStats()
         check(lib().cut_flow(self._h, _ptr(h), n_obs, _ptr(x), ctypes.byref(o), ctypes.byref(st),
                              _stream(stream)))

@@ -46,6 +46,12 @@ struct DevCSR {
     // the `rows` pieces, and pieces vr[r] .. vr[r+1]-1 make up row r
     uint64_t *vr = nullptr;
     int64_t real_rows = 0;
+    // forward commutator stage of a graph with few, long rows: the same
+    // records cut into `pieces` pieces (prp bounds them, pvr[r] is the first
+    // piece of row r) so that enough lane groups share the work; rp and
+    // rows keep describing whole rows
+    uint64_t *prp = nullptr, *pvr = nullptr;
+    int64_t pieces = 0;
     int64_t lane_rows = 0;   // rows of the whole stage: picks the lanes per row, so
                              // a shard sums each row exactly as the whole graph does
 };
@@ -78,6 +84,8 @@ struct cut_graph {
             cudaFree(c->rp);
             cudaFree(c->rec);
             cudaFree(c->vr);
+            cudaFree(c->prp);
+            cudaFree(c->pvr);
         }
         cudaFree(wtab);
         cudaFree(wtab32);
@@ -136,6 +144,35 @@ static cut_status whole_graph(const cut_graph *g, const char *fn) {
 }
 
 
+// Few long rows (fewer than kManyRows rows holding kPieceAvg records or more
+// on average, as in the Pauli-boson graphs): cut every row of the forward
+// commutator stage into pieces of about kFwdPiece records.  The cut of a row
+// depends only on its own length, so a shard holding whole rows cuts them
+// exactly as the whole graph does.  rp: the whole stage's row pointers;
+// rows [lo, hi) are the resident ones, record offsets rebased to rp[lo].
+constexpr int64_t kManyRowsForPieces = 16384;
+constexpr uint64_t kPieceAvg = 512, kFwdPiece = 256;
+
+static cut_status add_pieces(DevCSR &d, const std::vector<uint64_t> &rp, int64_t lo, int64_t hi, int64_t &bytes) {
+    const int64_t rows = (int64_t)rp.size() - 1;
+    if (rows <= 0 || rows >= kManyRowsForPieces || rp[rows] < (uint64_t)rows * kPieceAvg || hi <= lo) return CUT_OK;
+    std::vector<uint64_t> prp{0}, pvr(hi - lo + 1);
+    for (int64_t r = lo; r < hi; r++) {
+        pvr[r - lo] = prp.size() - 1;
+        const uint64_t b = rp[r] - rp[lo], len = rp[r + 1] - rp[r];
+        const uint64_t np = std::max<uint64_t>(1, (len + kFwdPiece - 1) / kFwdPiece);
+        for (uint64_t q = 1; q <= np; q++) prp.push_back(b + len * q / np);
+    }
+    pvr[hi - lo] = prp.size() - 1;
+    CUDA_TRY(cudaMalloc(&d.prp, prp.size() * 8));
+    CUDA_TRY(cudaMemcpy(d.prp, prp.data(), prp.size() * 8, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMalloc(&d.pvr, pvr.size() * 8));
+    CUDA_TRY(cudaMemcpy(d.pvr, pvr.data(), pvr.size() * 8, cudaMemcpyHostToDevice));
+    d.pieces = (int64_t)prp.size() - 1;
+    bytes += (int64_t)(prp.size() + pvr.size()) * 8;
+    return CUT_OK;
+}
+
 // ----------------------------------------------------------------- RHS core
 // dx_o (o < nops) for operands x_o, given xi; operands processed 4 at a time.
 static k::Weights weights_of(const cut_graph *g) {
@@ -187,10 +224,33 @@ static void comm_launch_x4(const DevCSR &c, const k::Weights &w, const double *x
 // pass).  Both give the same bits.
 static void launch_comm(const cut_graph *g, const double *xi, int nops, const double *const *xs,
                         double *const *dxs, cudaStream_t s, const int *done, int stage = 1,
-                        double *X4 = nullptr, const DevCSR *csr = nullptr) {
+                        double *X4 = nullptr, const DevCSR *csr = nullptr, double *piece = nullptr) {
     const DevCSR &c = csr ? *csr : g->st[stage];
     const k::Weights w = weights_of(g);
     const int lanes = comm_lanes(c.lane_rows);
+    if (X4 && nops <= 8 && c.prp && piece) {
+        // few long rows: 8 lanes per piece, piece sums reduced row by row in
+        // piece order
+        const int64_t n = g->host.n();
+        DevCSR pc = c;
+        pc.rp = c.prp;
+        pc.rows = c.pieces;
+        switch (nops) {
+#define CASE(M)                                                                                       \
+    case M: {                                                                                         \
+        k::Ops<M> ops;                                                                                \
+        for (int t = 0; t < M; t++) { ops.x[t] = xs[t]; ops.dx[t] = piece + t * c.pieces; }            \
+        k::pack_x4<M><<<grid_for_len(n), 256, 0, s>>>(ops, n, X4, done);                               \
+        comm_launch_x4<M, 8>(pc, w, xi, ops, X4, s, done);                                             \
+    } break;
+            CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+#undef CASE
+        }
+        k::Ops<8> red;
+        for (int t = 0; t < nops; t++) { red.x[t] = piece + t * c.pieces; red.dx[t] = dxs[t]; }
+        k::piece_reduce<<<grid_for_len(c.rows), 256, 0, s>>>(c.pvr, c.rows, red, nops, nullptr);
+        return;
+    }
     if (X4 && nops <= 8) {
         const int64_t n = g->host.n();
         for (int o0 = 0; o0 < nops; o0 += 8) {
@@ -247,11 +307,19 @@ static void launch_gen(const cut_graph *g, const double *h, double *xi, cudaStre
 // Double-float commutator stage: split xi and up to three operands at a time
 // into FP32 pairs (xi2[n_g], X2[n][4]) and apply the records on the FP32 pipes.
 static void launch_comm_df(const cut_graph *g, const double *xi, float2 *xi2, float2 *X2, int nops,
-                           const double *const *xs, double *const *dxs, cudaStream_t s, const int *done) {
-    const DevCSR &c = g->st[1];
+                           const double *const *xs, double *const *dxs, cudaStream_t s, const int *done,
+                           double *piece = nullptr) {
+    const DevCSR &rows_c = g->st[1];
+    const bool pieces = rows_c.prp && piece;
+    DevCSR c = rows_c;
+    if (pieces) { c.rp = rows_c.prp; c.rows = rows_c.pieces; }
     const int64_t n = g->host.n(), ng = g->host.n_g();
     const k::Weights w = weights_of(g);
-    const int lanes = comm_lanes(c.lane_rows);
+    // a whole warp per row: bound by L1 gathers, and the 32 records of one
+    // row in a warp instruction share more lines than 4 rows x 8 records
+    // (measured on the 16-orbital graph: 1.676 ms against 1.733 ms at 8);
+    // 8 lanes per piece when few long rows are cut into pieces
+    const int lanes = pieces ? 8 : 32;
     const int grid = grid_for_groups(c.rows, lanes);
     if (ng > 0) k::split_pairs<<<grid_for_len(ng), 256, 0, s>>>(xi, ng, xi2, 1, 0, done);
     for (int o0 = 0; o0 < nops; o0 += 3) {
@@ -262,7 +330,10 @@ static void launch_comm_df(const cut_graph *g, const double *xi, float2 *xi2, fl
 #define CASE(M)                                                                                                   \
     case M: {                                                                                                     \
         k::Ops<M> ops;                                                                                            \
-        for (int t = 0; t < M; t++) { ops.x[t] = xs[o0 + t]; ops.dx[t] = dxs[o0 + t]; }                             \
+        for (int t = 0; t < M; t++) {                                                                             \
+            ops.x[t] = xs[o0 + t];                                                                                \
+            ops.dx[t] = pieces ? piece + t * c.rows : dxs[o0 + t];                                                \
+        }                                                                                                         \
         if (lanes == 8)                                                                                           \
             k::comm_stage_df<M, 8><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, xi2, X4, ops, c.rows, done);        \
         else                                                                                                      \
@@ -271,7 +342,17 @@ static void launch_comm_df(const cut_graph *g, const double *xi, float2 *xi2, fl
             CASE(1) CASE(2) CASE(3)
 #undef CASE
         }
+        if (pieces) {
+            k::Ops<8> red;
+            for (int t = 0; t < m; t++) { red.x[t] = piece + t * c.rows; red.dx[t] = dxs[o0 + t]; }
+            k::piece_reduce<<<grid_for_len(rows_c.rows), 256, 0, s>>>(rows_c.pvr, rows_c.rows, red, m, nullptr);
+        }
     }
+}
+
+// piece sums of the forward stage: after the n x 64-byte operand blocks
+static double *piece_area(const cut_graph *g, float2 *X2) {
+    return X2 ? reinterpret_cast<double *>(X2) + 8 * g->host.n() : nullptr;
 }
 
 // L(h) x_o for given xi (either arithmetic); df buffers may be null for FP64
@@ -279,12 +360,14 @@ static void apply_L(const cut_graph *g, const double *xi, float2 *xi2, float2 *X
                     const double *const *xs, double *const *dxs, cudaStream_t s, const int *done) {
     // without scratch (adjoint recomputation) the stage runs in FP64 with one
     // gather per operand
-    if (g->arith == CUT_ARITH_DF64 && xi2 && X2) launch_comm_df(g, xi, xi2, X2, nops, xs, dxs, s, done);
-    else launch_comm(g, xi, nops, xs, dxs, s, done, 1, reinterpret_cast<double *>(X2));
+    if (g->arith == CUT_ARITH_DF64 && xi2 && X2)
+        launch_comm_df(g, xi, xi2, X2, nops, xs, dxs, s, done, piece_area(g, X2));
+    else
+        launch_comm(g, xi, nops, xs, dxs, s, done, 1, reinterpret_cast<double *>(X2), nullptr, piece_area(g, X2));
 }
 
 static size_t operand_scratch_bytes(const cut_graph *g) {
-    return (size_t)(std::max<int64_t>(1, g->host.n_g()) + 8 * g->host.n()) * 8 + 32;
+    return (size_t)(std::max<int64_t>(1, g->host.n_g()) + 8 * g->host.n() + 8 * g->st[1].pieces) * 8 + 64;
 }
 
 // Operand scratch of the commutator stage: xi2[n_g] pairs (double-float
@@ -347,7 +430,9 @@ cut_status cut_graph_load(const char *path, int device, unsigned flags, cut_grap
         cut_status st = upload_csr(g->st[s], g->host.rp[s], g->host.rec[s], bytes);
         if (st != CUT_OK) return st;
     }
-    cut_status st = upload_weights(g.get());
+    cut_status st = add_pieces(g->st[1], g->host.rp[1], 0, g->host.n(), bytes);
+    if (st != CUT_OK) return st;
+    st = upload_weights(g.get());
     if (st != CUT_OK) return st;
     g->device_bytes += bytes;
     if (flags & CUT_LOAD_ADJOINT) {
@@ -830,13 +915,13 @@ static void stacked_vjp(const cut_graph *g, const double *Y, const double *W, do
         // the rows of the diagonal coordinates hold most of the generator
         // records (every generator record has one diagonal input) and are
         // split into pieces like the other transposed orders
-        if (w.uniform) {
-            if (lh == 4) k::genT_lanes<true, 4><<<grid_for_groups(ch.rows, 4), k::kBlock, 0, s>>>(ch.rp, ch.rec, w, xib, Y, nullptr, hpiece, ch.rows);
-            else k::genT_lanes<true, 8><<<grid_for_groups(ch.rows, 8), k::kBlock, 0, s>>>(ch.rp, ch.rec, w, xib, Y, nullptr, hpiece, ch.rows);
-        } else {
-            if (lh == 4) k::genT_lanes<false, 4><<<grid_for_groups(ch.rows, 4), k::kBlock, 0, s>>>(ch.rp, ch.rec, w, xib, Y, nullptr, hpiece, ch.rows);
-            else k::genT_lanes<false, 8><<<grid_for_groups(ch.rows, 8), k::kBlock, 0, s>>>(ch.rp, ch.rec, w, xib, Y, nullptr, hpiece, ch.rows);
-        }
+        // a whole warp per piece: each record here is two dependent gathers
+        // and one FMA, so a lane's chain of records is all latency
+        (void)lh;
+        if (w.uniform)
+            k::genT_lanes<true, 32><<<grid_for_groups(ch.rows, 32), k::kBlock, 0, s>>>(ch.rp, ch.rec, w, xib, Y, nullptr, hpiece, ch.rows);
+        else
+            k::genT_lanes<false, 32><<<grid_for_groups(ch.rows, 32), k::kBlock, 0, s>>>(ch.rp, ch.rec, w, xib, Y, nullptr, hpiece, ch.rows);
         {
             k::Ops<8> red;
             red.x[0] = hpiece;
@@ -1130,6 +1215,8 @@ extern "C" cut_status cut_flow(const cut_graph *g, double *h, int n_obs, double 
         out.steps = N;
         out.rhs_calls = 4 * N;
         out.s_final = o->s0 + ds * (double)N;
+        out.ds_next = ds;
+        out.finished = 1;
     } else {
         k::Control c;
         memset(&c, 0, sizeof(c));
@@ -1138,6 +1225,7 @@ extern "C" cut_status cut_flow(const cut_graph *g, double *h, int n_obs, double 
         c.rtol = o->rtol;
         c.atol = o->atol;
         c.max_steps = max_steps;
+        c.pause_after = replay ? 0 : std::max<int64_t>(0, o->pause_after);
         c.n_replay = replay ? o->n_replay : 0;
         c.ds = replay ? o->replay_steps[0] : std::min(o->ds, o->s1 - o->s0);
         c.done = (replay || o->s1 > o->s0) ? 0 : 1;
@@ -1171,6 +1259,8 @@ extern "C" cut_status cut_flow(const cut_graph *g, double *h, int n_obs, double 
         out.rejects = hc.rejects;
         out.rhs_calls = 1 + 6 * hc.attempts;
         out.s_final = hc.s;
+        out.ds_next = hc.ds;
+        out.finished = hc.paused ? 0 : 1;
         if (o->record_steps && o->record_cap > 0) {
             int64_t m = std::min<int64_t>(std::min<int64_t>(hc.steps, o->record_cap), nrec);
             cudaMemcpyAsync(o->record_steps, w.record, m * 8, cudaMemcpyDeviceToHost, s);
@@ -1278,7 +1368,8 @@ extern "C" cut_status cut_flow_vjp(const cut_graph *g, const double *h0, int n_o
             double *dxs[64];
             for (int o = 0; o < nops; o++) { xs[o] = U + i * L + o * n; dxs[o] = K + i * L + o * n; }
             launch_gen(g, U + i * L, xi, s, nullptr);
-            launch_comm(g, xi, nops, xs, dxs, s, nullptr, 1, reinterpret_cast<double *>(operand_blocks(g, df)));
+            launch_comm(g, xi, nops, xs, dxs, s, nullptr, 1, reinterpret_cast<double *>(operand_blocks(g, df)),
+                        nullptr, piece_area(g, operand_blocks(g, df)));
         }
         combine(Ynext, Ycur, S, Ks, B, dsd, 0.0);
     };
@@ -1554,6 +1645,8 @@ extern "C" cut_status cut_graph_load_shard(const char *path, int device, int ran
         g->lo[s] = b[rank];
         g->hi[s] = b[rank + 1];
         cut_status st = upload_rows(g->st[s], g->host.rp[s], g->host.rec[s], g->lo[s], g->hi[s], bytes);
+        if (st != CUT_OK) return st;
+        if (s == 1) st = add_pieces(g->st[1], g->host.rp[1], g->lo[1], g->hi[1], bytes);
         if (st != CUT_OK) return st;
     }
     cut_status st = upload_weights(g.get());

@@ -18,6 +18,8 @@ struct Control {
     int nonfinite;
     int done, status, accepted;
     long long steps, rejects, attempts, max_steps, n_replay;
+    long long pause_after;   // > 0: stop (status OK, not finished) after this many attempts
+    int paused;
 };
 
 // r = max_k |ds sum_i e_i K_i[k]| / (atol + rtol max(|y_k|, |y5_k|))
@@ -97,7 +99,8 @@ __global__ void dp_control(Control *ctl, const double *replay, double *record, l
     ds = fmin(ds, ctl->s1 - ctl->s);
     if (ds < 1e-14 * fmax(1.0, fabs(ctl->s))) { ctl->status = 8; ctl->done = 1; return; }  // STEP_UNDERFLOW
     ctl->ds = ds;
-    if (ctl->attempts >= ctl->max_steps) { ctl->status = 9; ctl->done = 1; }             // MAX_STEPS
+    if (ctl->attempts >= ctl->max_steps) { ctl->status = 9; ctl->done = 1; return; }      // MAX_STEPS
+    if (ctl->pause_after > 0 && ctl->attempts >= ctl->pause_after) { ctl->paused = 1; ctl->done = 1; }
 }
 
 // After control: if the attempt was accepted, y <- y5 and K1 <- K7 (FSAL).

@@ -585,10 +585,19 @@ __global__ void __launch_bounds__(kBlock) commT_xi_x4(const uint64_t *__restrict
                     ld_quad64(X4 + 4 * NB * (int64_t)q.y + 4 * b, xv[4 * b], xv[4 * b + 1], xv[4 * b + 2],
                               xv[4 * b + 3]);
                 }
-                double d = wv[0] * xv[0];
+                if (UNIFORM) {
+                    // the factor's sign flips the w values (integer XOR); the
+                    // products then go straight into the row sum: NOPS FP64
+                    // FMAs per record, the forward stage's count
+                    const unsigned long long sb = sg[q.x >> 24];
 #pragma unroll
-                for (int o = 1; o < NOPS; o++) d = fma(wv[o], xv[o], d);
-                acc += UNIFORM ? signed_by(d, sg[q.x >> 24]) : ws[q.x >> 24] * d;
+                    for (int o = 0; o < NOPS; o++) acc = fma(signed_by(wv[o], sb), xv[o], acc);
+                } else {
+                    double d = wv[0] * xv[0];
+#pragma unroll
+                    for (int o = 1; o < NOPS; o++) d = fma(wv[o], xv[o], d);
+                    acc = fma(ws[q.x >> 24], d, acc);
+                }
             }
         }
         acc = group_sum<LANES>(acc);

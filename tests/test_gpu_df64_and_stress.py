@@ -242,3 +242,42 @@ def test_packed_adjoint_operand_counts_match_oracle(n_obs):
     assert_close(np64(hb), want_hb, what="h_bar")
     for g_, w_ in zip(xb, want_xb):
         assert_close(np64(g_), w_, what="x_bar")
+
+
+@pytest.mark.parametrize("arith,n_obs", [("fp64", 1), ("fp64", 4), ("df64", 2)])
+def test_few_long_rows_cut_into_pieces_match_oracle(arith, n_obs):
+    """The closed 6-qubit Pauli registry has 4,096 rows of 2,016 records
+    each, few and long, so the commutator stage cuts every row into pieces
+    of about 256 records and adds each row's pieces in order.  Against the
+    oracle (FP64 and double-float, one to five operands), repeatable bit for
+    bit, and equal within the parity tolerance to the allocation-free entry
+    point, which sums whole rows."""
+    import ctypes
+    import torch
+    import paper_2609_14831_b300 as cg
+    from cut_inputs import ALG_PAULI, pauli_registry
+    labels = pauli_registry(6)
+    rng = np.random.default_rng(77 + n_obs)
+    h = rng.normal(size=len(labels)) * 0.1
+    xs = [rng.normal(size=len(labels)) for _ in range(n_obs)]
+    G = graph_for("pauli6", ALG_PAULI, 6, labels)
+    G.set_arithmetic(arith)
+    try:
+        dh, dxs = G.rhs(h, xs)
+        dh2, dxs2 = G.rhs(h, xs)
+    finally:
+        G.set_arithmetic("fp64")
+    assert torch.equal(dh, dh2) and all(torch.equal(a, b) for a, b in zip(dxs, dxs2))
+    want_dh, want_dxs = oracle.rhs(ALG_PAULI, 6, labels, h, xs)
+    fl = rhs_floor(h, xs)
+    assert_close(np64(dh), want_dh, what=f"dh ({arith})", atol=fl)
+    for g_, w_ in zip(dxs, want_dxs):
+        assert_close(np64(g_), w_, what=f"dx ({arith})", atol=fl)
+    if arith == "fp64":
+        hd = torch.tensor(h, device="cuda")
+        X = torch.tensor(np.stack(xs), device="cuda")
+        oh, oX = torch.empty_like(hd), torch.empty_like(X)
+        P = lambda t: ctypes.c_void_p(t.data_ptr())
+        cg.check(cg.lib().cut_rhs_noalloc(G._h, P(hd), n_obs, P(X), P(oh), P(oX),
+                                          ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+        assert_close(np64(oh), np64(dh), what="whole rows vs pieces", atol=fl)

@@ -239,3 +239,24 @@ def test_flow_reports_nonfinite_state():
     with pytest.raises(cg.CutError) as e:
         G.flow(bad, [], method="dp45", s0=0.0, s1=0.01, ds=1e-3, rtol=1e-8)
     assert e.value.name == "NONFINITE"
+
+
+def test_dp45_flow_pause_and_resume_is_exact():
+    """Checkpoint/resume: a DP45 flow paused twice (after 100, then 150
+    attempts) and resumed from (state, s_final, ds_next) takes the same
+    accepted steps and ends on the same bits as the uninterrupted flow."""
+    w = workload("molecular_8so")
+    G = graph_for("mol8", w.alg, w.nmodes, w.labels)
+    kw = dict(method="dp45", s1=w.s_end, rtol=w.rtol, atol=w.atol)
+    hs, xo, st, steps = G.flow(w.h, w.observables, s0=0.0, ds=w.ds, **kw)
+    assert st["finished"] == 1
+    h, x, s0, ds, got = w.h, list(w.observables), 0.0, w.ds, []
+    for pause in (100, 150, 0):
+        h, x, sti, stp = G.flow(h, x, s0=s0, ds=ds, pause_after=pause, **kw)
+        got += list(stp)
+        s0, ds = sti["s_final"], sti["ds_next"]
+        assert sti["finished"] == (1 if pause == 0 else 0)
+    np.testing.assert_array_equal(np.array(got), steps)
+    np.testing.assert_array_equal(np64(h), np64(hs))
+    for a, b in zip(x, xo):
+        np.testing.assert_array_equal(np64(a), np64(b))

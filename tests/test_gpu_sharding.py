@@ -67,11 +67,20 @@ def _sharded(path, world, h, xs, s1, ds):
     return out
 
 
-@pytest.mark.parametrize("case,world", [("mol8", 2), ("mol8", 3), ("mol5_3body", 2)])
+@pytest.mark.parametrize("case,world", [("mol8", 2), ("mol8", 3), ("mol5_3body", 2), ("pauli6", 3)])
 def test_shards_reproduce_whole_graph_rhs_and_flow(case, world):
+    """pauli6: 4,096 long rows, which the commutator stage cuts into pieces;
+    every shard cuts its rows as the whole graph does."""
     if case == "mol8":
         w = workload("molecular_8so")
         alg, nm, labels, h, xs = w.alg, w.nmodes, w.labels, w.h, list(w.observables)
+    elif case == "pauli6":
+        from cut_inputs import ALG_PAULI, pauli_registry
+        labels = pauli_registry(6)
+        alg, nm = ALG_PAULI, 6
+        rng = np.random.default_rng(78)
+        h = rng.normal(size=len(labels)) * 0.1
+        xs = [rng.normal(size=len(labels))]
     else:
         labels = cfg2_registry(5, keep_shared1=0.3, seed=3)
         alg, nm = ALG_FERMION, 5
