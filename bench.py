@@ -164,6 +164,22 @@ def _build(workload_name, seed, tmpdir, rank):
     return w, path, stats, time.time() - t0
 
 
+# Sizes of the stress graphs as cut_build compiles them (checked against the
+# built graph by the bench itself and by tests/test_gpu_df64_and_stress.py),
+# so that the reference arm states the same workload config without loading
+# the product library.
+GRAPH_SIZES = {"stress_16so": {"n": 212272, "n_g": 211576, "R_g": 3456464, "R_L": 335893116}}
+
+
+def workload_config(name, world, sizes, nops=3, ds=1e-3):
+    """The bench line's `config`: what the workload is (both arms print it)."""
+    R = sizes["R_g"] + sizes["R_L"]
+    return {"workload": name, "n": int(sizes["n"]), "n_g": int(sizes["n_g"]), "R_g": int(sizes["R_g"]),
+            "R_L": int(sizes["R_L"]), "operands": nops, "record_bytes": 8, "integrator": "rk4", "ds": ds,
+            "l2": "inputs larger than L2 (graph %.2f GB resident)" % (8 * R / 1e9),
+            "parallelism": f"{world} independent instance(s)"}
+
+
 # Records of the CPU-sample graphs as cut_build compiles them (R_g + R_L);
 # tests/test_bench_host.py rebuilds both and checks these numbers, so the
 # reference arm can state its throughput in records/s without loading the
@@ -549,7 +565,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"],
             "unit": "records/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": args.workload, "sample": cb["sample"]},
+            "data": "synthetic",
+            "config": (workload_config(args.workload, args.gpus, GRAPH_SIZES[args.workload])
+                       if args.workload in GRAPH_SIZES else {"workload": args.workload}),
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": "records/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -610,6 +628,9 @@ def main():
     R = G.R_g + G.R_L
     n = G.n
     nops = 1 + len(w.observables)
+    sizes = {"n": G.n, "n_g": G.n_g, "R_g": G.R_g, "R_L": G.R_L}
+    if args.workload in GRAPH_SIZES:
+        assert sizes == GRAPH_SIZES[args.workload], (sizes, GRAPH_SIZES[args.workload])
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     h0 = torch.tensor(w.h, dtype=torch.float64, device=dev)
@@ -799,12 +820,10 @@ def main():
             "value": value, "unit": "records/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "n": int(n), "n_g": int(G.n_g), "R_g": int(G.R_g),
-                       "R_L": int(G.R_L), "operands": nops, "record_bytes": 8, "integrator": "rk4",
-                       "ds": ds, "l2": "inputs larger than L2 (graph %.2f GB resident)" % (8 * R / 1e9),
-                       "build_s": round(tbuild, 1), "build_peak_over_stored":
-                           round(bstats["peak_rss_bytes"] / max(1, bstats["bytes_stored"]), 3),
-                       "parallelism": f"{world} independent instance(s)"},
+            "config": workload_config(args.workload, world, sizes, nops, ds),
+            "build": {"seconds": round(tbuild, 1), "bytes_stored": int(bstats["bytes_stored"]),
+                      "peak_rss_over_stored": round(bstats["peak_rss_bytes"] / max(1, bstats["bytes_stored"]), 3),
+                      "note": "compiled in a fresh process; peak resident set of that process"},
             # per RK4 step: 4 right-hand sides (generator stage, then one pack and
             # one commutator launch for up to eight operands, else one commutator
             # launch per eight) and 4 combinations

@@ -112,6 +112,13 @@ def stress():
     return w, G
 
 
+def test_stress_graph_sizes_match_the_bench_table(stress):
+    """The reference arm states the stress graph's sizes from a table."""
+    import bench
+    _, G = stress
+    assert bench.GRAPH_SIZES["stress_16so"] == {"n": G.n, "n_g": G.n_g, "R_g": G.R_g, "R_L": G.R_L}
+
+
 @pytest.mark.parametrize("arith", ["fp64", "df64"])
 def test_stress_graph_full_size_sparse_input_parity(stress, arith):
     w, G = stress
