@@ -237,8 +237,17 @@ def cpu_sample(seconds_budget=20.0, cores=None, gpu_flow_rhs_calls=None):
         t0 = time.time()
         oracle_rhs_parallel(pool, cores, wm.alg, wm.nmodes, wm.labels, wm.h, wm.observables)
         dt8 = time.time() - t0
+    # the oracle as it stands, one thread (one right-hand side of each sample)
+    import oracle
+    t0 = time.time()
+    oracle.rhs(ws.alg, ws.nmodes, ws.labels, ws.h, ws.observables)
+    dt1 = time.time() - t0
+    t0 = time.time()
+    oracle.rhs(wm.alg, wm.nmodes, wm.labels, wm.h, wm.observables)
+    dt81 = time.time() - t0
     rec = SAMPLE_RECORDS["stress_7so"]
     out = {"value": rec / dt, "unit": "records/s", "cores": cores, "kind": "oracle",
+           "single_thread": {"stress_7so_rhs_s": dt1, "records_per_s": rec / dt1, "molecular_8so_rhs_s": dt81},
            "sample": f"oracle right-hand side (H, N, D) of the stress recipe on 7 spin-orbitals (n={len(ws.labels)}, "
                      f"{rec} graph records), {calls} call(s), {dt:.2f} s each on {cores} processes; value = graph "
                      f"records / oracle time",
@@ -384,7 +393,13 @@ def paper_workload(cg, torch, dev, local, diagnostics=False):
     d = tempfile.mkdtemp(prefix="cutpb_")
     path = os.path.join(d, "pb5.cutg")
     st = cg.build_graph(w.alg, w.nmodes, w.labels, path)
+    # lifecycle (Sec. 3.3): validated reload (read, SHA-256 check, upload)
+    cg.Graph(path, device=local).close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     G = cg.Graph(path, device=local)
+    torch.cuda.synchronize()
+    reload_s = time.perf_counter() - t0
     os.remove(path)
     h = torch.tensor(w.h, device=dev)
     xs = [torch.tensor(pauli_boson_hamiltonian(w.labels, 5, seed=100 + i), device=dev) for i in range(7)]
@@ -414,7 +429,8 @@ def paper_workload(cg, torch, dev, local, diagnostics=False):
     torch.cuda.synchronize()
     flow_s = time.perf_counter() - t0
     out = {"workload": "Pauli-boson, 5 modes, degree 4 (4,004 coordinates), 8 operators",
-           "records": int(R), "build_s": round(st["seconds_total"], 2),
+           "records": int(R), "build_s": round(st["seconds_total"], 2), "validated_reload_s": reload_s,
+           "bundle_mb": round(st["bytes_stored"] / 1e6, 1),
            "retained_action_ms": ms, "retained_records_per_s": R / (ms * 1e-3),
            "paper_h100_retained_action_ms": 0.632,
            "flow_100_rk4_steps_s": flow_s, "paper_h100_flow_100_steps_s": 0.498}
