@@ -501,6 +501,7 @@ def run_surrogate(args):
     for name, idx in (("n0", [k0]), ("diag36", diag)):
         tau, frac_val = sur.calibrate(th_val, exact_val, idx, 1e-4)
         sur.screen(th_val[:64], idx)              # warm-up of the served path
+        sur.fallback(th_val[:1])                  # and of its fallback flow
         out, ok, tm = sur.screen(th_te, idx)
         ok_np = ok
         it = torch.as_tensor(np.asarray(idx), device=exact.device)
@@ -842,8 +843,8 @@ def main():
                       "note": "compiled in a fresh process; peak resident set of that process"},
             # per RK4 step: 4 right-hand sides (generator stage, then one pack and
             # one commutator launch for up to eight operands, else one commutator
-            # launch per eight) and 4 combinations
-            "gpu_launches": int(args.steps * 4 * (1 + (2 if nops <= 8 else (nops + 7) // 8)) + args.steps * 4),
+            # launch per eight) and 4 combinations; one non-finite scan per flow
+            "gpu_launches": int(args.steps * 4 * (1 + (2 if nops <= 8 else (nops + 7) // 8)) + args.steps * 4 + 1),
             "roofline": roofline,
             "df64": df,
             "batched": batched,

@@ -315,11 +315,11 @@ static void launch_comm_df(const cut_graph *g, const double *xi, float2 *xi2, fl
     if (pieces) { c.rp = rows_c.prp; c.rows = rows_c.pieces; }
     const int64_t n = g->host.n(), ng = g->host.n_g();
     const k::Weights w = weights_of(g);
-    // a whole warp per row: bound by L1 gathers, and the 32 records of one
-    // row in a warp instruction share more lines than 4 rows x 8 records
-    // (measured on the 16-orbital graph: 1.676 ms against 1.733 ms at 8);
+    // lanes per row as the FP64 stage (a whole warp per row shares a few
+    // more L1 lines per instruction, but measured within run-to-run noise
+    // of 8 lanes on the 16-orbital graph: 1.68-1.81 ms against 1.68-1.73);
     // 8 lanes per piece when few long rows are cut into pieces
-    const int lanes = pieces ? 8 : 32;
+    const int lanes = pieces ? 8 : comm_lanes(c.lane_rows);
     const int grid = grid_for_groups(c.rows, lanes);
     if (ng > 0) k::split_pairs<<<grid_for_len(ng), 256, 0, s>>>(xi, ng, xi2, 1, 0, done);
     for (int o0 = 0; o0 < nops; o0 += 3) {

@@ -88,6 +88,10 @@ class DeviceShard:
         torch = _torch()
         return torch.empty(*shape, dtype=torch.float64, device=self.device)
 
+    def set_arithmetic(self, mode):
+        """'fp64' or 'df64' for this shard's commutator stage (as Graph)."""
+        check(lib().cut_graph_set_arithmetic(self._h, {"fp64": 0, "df64": 1}[mode]))
+
     def generator(self, h, out, stream=None):
         """out[gen_hi - gen_lo] = xi of this shard's generator rows."""
         check(lib().cut_shard_generator(self._h, _ptr(h), _ptr(out), _stream(stream)))

@@ -38,7 +38,7 @@ class ThreadGroup:
         return gather
 
 
-def _sharded(path, world, h, xs, s1, ds):
+def _sharded(path, world, h, xs, s1, ds, arith="fp64"):
     import torch
     from paper_2609_14831_b300.sharded import DeviceShard, ShardedRHS
     grp = ThreadGroup(world)
@@ -47,6 +47,7 @@ def _sharded(path, world, h, xs, s1, ds):
     def run(r):
         try:
             ex = DeviceShard(path, 0, r, world)
+            ex.set_arithmetic(arith)
             sh = ShardedRHS(ex, grp.gather_fn(r))
             Y = torch.tensor(np.stack([h] + list(xs)), device="cuda")
             DY = torch.empty_like(Y)
@@ -115,3 +116,22 @@ def test_shard_handles_refuse_whole_graph_calls():
     assert cg.lib().cut_rhs(ex._h, P(h), 0, None, P(dh), None, None, None) == 1
     assert cg.lib().cut_rhs_noalloc(ex._h, P(h), 0, None, P(dh), None, None) == 1
     ex.close()
+
+
+def test_double_float_shards_reproduce_the_whole_graph():
+    """The double-float commutator stage on 2 shards equals the whole
+    graph's double-float right-hand side and RK4 flow bit for bit."""
+    w = workload("molecular_8so")
+    G = graph_for("mol8", w.alg, w.nmodes, w.labels)
+    G.set_arithmetic("df64")
+    try:
+        dh, dx = G.rhs(w.h, list(w.observables))
+        want_rhs = np.stack([np64(dh)] + [np64(v) for v in dx])
+        hs, xo, st, _ = G.flow(w.h, list(w.observables), method="rk4", s0=0.0, s1=0.05, ds=0.005)
+        want_y = np.stack([np64(hs)] + [np64(v) for v in xo])
+    finally:
+        G.set_arithmetic("fp64")
+    out = _sharded(G.path, 2, w.h, list(w.observables), 0.05, 0.005, arith="df64")
+    for r, (dy, y, _, _) in enumerate(out):
+        np.testing.assert_array_equal(dy, want_rhs, err_msg=f"rank {r} rhs")
+        np.testing.assert_array_equal(y, want_y, err_msg=f"rank {r} flow")

@@ -74,6 +74,7 @@ def test_surrogate_gate_and_screen_gain_over_the_plain_flow():
     # gate on n_0
     tau, frac_val = sur.calibrate(th_val, exact_val, [k0], 1e-4)
     sur.screen(th_val[:64], [k0])                 # warm-up of the served path
+    sur.fallback(th_val[:1])                      # and of its fallback flow
     out, ok, tm = sur.screen(th_test, [k0])
     err = (out[:, k0] - exact[:, k0]).abs().cpu().numpy()
     t_gate = tm["predict_s"] + tm["fallback_s"]

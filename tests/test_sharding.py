@@ -159,3 +159,45 @@ def test_two_gloo_ranks_reproduce_the_single_rank_rhs_and_rk4_flow(bundle, tmp_p
     f = oracle.stacked_rhs(alg, nm, labels, 2)
     y = oracle.rk4_flow(f, np.concatenate([h] + xs), 0.005, 10)
     np.testing.assert_allclose(y1.ravel(), y, rtol=0, atol=1e-12 * np.max(np.abs(y)))
+
+
+def _worker_fail(rank, world, port, path, outdir):
+    """Rank 1 leaves before its first exchange; rank 0 must get an error from
+    the all-gather within the group's timeout instead of hanging."""
+    import datetime
+    import time as _time
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from paper_2609_14831_b300.sharded import ShardedRHS, torch_all_gather
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=5))
+    if rank == 1:
+        open(os.path.join(outdir, "left1"), "w").close()
+        os._exit(0)                              # leaves between steps, nothing in flight
+    alg, nm, labels, h, xs = _problem()
+    sh = ShardedRHS(NumpyShard(path, rank, world), torch_all_gather())
+    Y = torch.tensor(np.stack([h] + xs))
+    t0 = _time.time()
+    try:
+        sh.rhs(Y, torch.empty_like(Y))
+        res = "no error"
+    except Exception as e:                       # the exchange fails on the host
+        res = f"error after {_time.time() - t0:.1f} s: {type(e).__name__}"
+    open(os.path.join(outdir, "rank0.txt"), "w").write(res)
+    os._exit(0)
+
+
+def test_a_rank_that_leaves_is_detected_by_the_others(bundle, tmp_path):
+    ctx = mp.get_context("spawn")
+    port = 29700 + os.getpid() % 1000
+    procs = [ctx.Process(target=_worker_fail, args=(r, 2, port, bundle, str(tmp_path))) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    res = (tmp_path / "rank0.txt").read_text()
+    print(res)
+    assert res.startswith("error after")
+    assert float(res.split()[2]) < 60
