@@ -224,7 +224,8 @@ static void comm_launch_x4(const DevCSR &c, const k::Weights &w, const double *x
 // pass).  Both give the same bits.
 static void launch_comm(const cut_graph *g, const double *xi, int nops, const double *const *xs,
                         double *const *dxs, cudaStream_t s, const int *done, int stage = 1,
-                        double *X4 = nullptr, const DevCSR *csr = nullptr, double *piece = nullptr) {
+                        double *X4 = nullptr, const DevCSR *csr = nullptr, double *piece = nullptr,
+                        bool prepacked = false) {
     const DevCSR &c = csr ? *csr : g->st[stage];
     const k::Weights w = weights_of(g);
     const int lanes = comm_lanes(c.lane_rows);
@@ -240,7 +241,7 @@ static void launch_comm(const cut_graph *g, const double *xi, int nops, const do
     case M: {                                                                                         \
         k::Ops<M> ops;                                                                                \
         for (int t = 0; t < M; t++) { ops.x[t] = xs[t]; ops.dx[t] = piece + t * c.pieces; }            \
-        k::pack_x4<M><<<grid_for_len(n), 256, 0, s>>>(ops, n, X4, done);                               \
+        if (!prepacked) k::pack_x4<M><<<grid_for_len(n), 256, 0, s>>>(ops, n, X4, done);               \
         comm_launch_x4<M, 8>(pc, w, xi, ops, X4, s, done);                                             \
     } break;
             CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
@@ -260,7 +261,7 @@ static void launch_comm(const cut_graph *g, const double *xi, int nops, const do
     case M: {                                                                                         \
         k::Ops<M> ops;                                                                                \
         for (int t = 0; t < M; t++) { ops.x[t] = xs[o0 + t]; ops.dx[t] = dxs[o0 + t]; }                 \
-        k::pack_x4<M><<<grid_for_len(n), 256, 0, s>>>(ops, n, X4, done);                               \
+        if (!prepacked) k::pack_x4<M><<<grid_for_len(n), 256, 0, s>>>(ops, n, X4, done);               \
         if (lanes == 8) comm_launch_x4<M, 8>(c, w, xi, ops, X4, s, done);                              \
         else comm_launch_x4<M, 32>(c, w, xi, ops, X4, s, done);                                        \
     } break;
@@ -1071,17 +1072,57 @@ static void stage_input(const FlowWork &w, const double *A, int i, int64_t L, co
     k::rk_combine<<<grid_for_len(L), 256, 0, s>>>(cb, out, L, dsp, dsc, done);
 }
 
+// K_i = f(Y + ds sum_j A[j] K_j): the stage input, its packed operand
+// blocks and the generator in one launch (stage_gen), then the commutator
+// stage over the packed blocks; U_full (may be null) keeps the stage input.
+// Double-float arithmetic, more than eight operands or no operand scratch
+// take the separate combination and right-hand-side launches.  Same bits.
+static void fused_stage(const cut_graph *g, FlowWork &w, const double *A, int i, int nops, const double *dsp,
+                        double dsc, cudaStream_t s, const int *done, double *U_full, double *Kout) {
+    const int64_t n = g->host.n(), L = (int64_t)nops * n;
+    double *X4 = reinterpret_cast<double *>(operand_blocks(g, w.df));
+    if (g->arith != CUT_ARITH_FP64 || nops > 8 || !X4) {
+        double *U = U_full ? U_full : w.U;
+        const double *in = w.Y;
+        if (i > 0) {
+            stage_input(w, A, i, L, dsp, dsc, s, done, U);
+            in = U;
+        } else if (U_full) {
+            stage_input(w, A, 0, L, dsp, dsc, s, done, U);
+        }
+        stacked_rhs(g, in, Kout, nops, w.xi, s, done, w.df);
+        return;
+    }
+    k::StageIn si;
+    si.base = w.Y;
+    si.nk = 0;
+    for (int j = 0; j < i; j++)
+        if (A[j] != 0.0) { si.K[si.nk] = w.K[j]; si.c[si.nk] = A[j]; si.nk++; }
+    si.ds_ptr = dsp;
+    si.ds_const = dsc;
+    const DevCSR &c0 = g->st[0];
+    const k::Weights wt = weights_of(g);
+    const int gl = gen_lanes(c0.lane_rows);
+    const int grid = std::max(grid_for_len(n), grid_for_groups(c0.rows, gl));
+    switch (nops * 4 + (wt.uniform ? 2 : 0) + (gl == 4 ? 1 : 0)) {
+#define CASE(M)                                                                                                 \
+    case M * 4 + 0: k::stage_gen<M, false, 8><<<grid, k::kBlock, 0, s>>>(si, n, X4, U_full, c0.rp, c0.rec, wt, w.xi, c0.rows, done); break; \
+    case M * 4 + 1: k::stage_gen<M, false, 4><<<grid, k::kBlock, 0, s>>>(si, n, X4, U_full, c0.rp, c0.rec, wt, w.xi, c0.rows, done); break; \
+    case M * 4 + 2: k::stage_gen<M, true, 8><<<grid, k::kBlock, 0, s>>>(si, n, X4, U_full, c0.rp, c0.rec, wt, w.xi, c0.rows, done); break; \
+    case M * 4 + 3: k::stage_gen<M, true, 4><<<grid, k::kBlock, 0, s>>>(si, n, X4, U_full, c0.rp, c0.rec, wt, w.xi, c0.rows, done); break;
+        CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+#undef CASE
+    }
+    const double *xs[8];
+    double *dxs[8];
+    for (int o = 0; o < nops; o++) { xs[o] = nullptr; dxs[o] = Kout + o * n; }
+    launch_comm(g, w.xi, nops, xs, dxs, s, done, 1, X4, nullptr, piece_area(g, reinterpret_cast<float2 *>(X4)), true);
+}
+
 // One RK4 step on w.Y (fixed ds), K/U scratch.
 static void rk4_step(const cut_graph *g, FlowWork &w, int nops, double ds, cudaStream_t s) {
     const int64_t L = (int64_t)nops * g->host.n();
-    for (int i = 0; i < 4; i++) {
-        const double *in = w.Y;
-        if (i > 0) {
-            stage_input(w, RK4_A[i], i, L, nullptr, ds, s, nullptr, w.U);
-            in = w.U;
-        }
-        stacked_rhs(g, in, w.K[i], nops, w.xi, s, nullptr, w.df);
-    }
+    for (int i = 0; i < 4; i++) fused_stage(g, w, RK4_A[i], i, nops, nullptr, ds, s, nullptr, nullptr, w.K[i]);
     k::Combine cb;
     cb.base = w.Y;
     cb.nk = 4;
@@ -1095,12 +1136,8 @@ static void dp_attempt(const cut_graph *g, FlowWork &w, int nops, cudaStream_t s
     const int64_t L = (int64_t)nops * g->host.n();
     const int *done = &w.ctl->done;
     const double *dsp = &w.ctl->ds;
-    for (int i = 1; i < 6; i++) {
-        stage_input(w, DP_A[i], i, L, dsp, 0.0, s, done, w.U);
-        stacked_rhs(g, w.U, w.K[i], nops, w.xi, s, done, w.df);
-    }
-    stage_input(w, DP_A[6], 6, L, dsp, 0.0, s, done, w.Y5);
-    stacked_rhs(g, w.Y5, w.K[6], nops, w.xi, s, done, w.df);
+    for (int i = 1; i < 6; i++) fused_stage(g, w, DP_A[i], i, nops, dsp, 0.0, s, done, nullptr, w.K[i]);
+    fused_stage(g, w, DP_A[6], 6, nops, dsp, 0.0, s, done, w.Y5, w.K[6]);
     if (!replay) {
         k::ErrTerms et;
         for (int i = 0; i < 7; i++) { et.K[i] = w.K[i]; et.e[i] = DP_B[i] - DP_BS[i]; }

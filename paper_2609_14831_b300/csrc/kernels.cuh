@@ -651,6 +651,79 @@ __global__ void piece_reduce(const uint64_t *__restrict__ vr, int64_t rows, Ops<
     }
 }
 
+// ---------------------------------------------------------------- fused stage
+// One Runge-Kutta stage's input and generator in one launch (flows):
+//   U = base + sum_s (c_s ds) K_s   (the rk_combine arithmetic), written in
+//        the packed operand blocks X4[k][4 NB] the commutator stage reads
+//        (and in full to U_full when the caller keeps it);
+//   xi[a] = sum alpha U_0[i] U_0[j]   (gen_stage), the U values it needs
+//        formed on the fly with the same arithmetic, so no block waits for
+//        another's writes.
+// The values are those of rk_combine + pack_x4 + gen_stage bit for bit.
+struct StageIn {
+    const double *base;
+    const double *K[7];
+    double c[7];
+    int nk;
+    const double *ds_ptr;   // ds from the control block, or
+    double ds_const;
+};
+
+__device__ __forceinline__ double stage_u(const StageIn &si, double ds, int64_t e) {
+    double v = si.base[e];
+    for (int s = 0; s < si.nk; s++) v += (si.c[s] * ds) * si.K[s][e];
+    return v;
+}
+
+template <int NOPS, bool UNIFORM, int LANES>
+__global__ void __launch_bounds__(kBlock) stage_gen(StageIn si, int64_t n, double *__restrict__ X4,
+                                                    double *__restrict__ U_full, const uint64_t *__restrict__ rp,
+                                                    const uint2 *__restrict__ rec, Weights wt,
+                                                    double *__restrict__ xi, int64_t rows, const int *done) {
+    constexpr int NB = (NOPS + 3) / 4;
+    constexpr int RPW = 32 / LANES;
+    __shared__ double ws[256];
+    __shared__ unsigned long long sg[256];
+    if (skip(done)) return;
+    load_weights(ws, sg, wt);
+    const double ds = si.ds_ptr ? *si.ds_ptr : si.ds_const;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int o = 0; o < NOPS; o++) {
+            const double u = stage_u(si, ds, o * n + k);
+            X4[4 * NB * k + o] = u;
+            if (U_full) U_full[o * n + k] = u;
+        }
+    }
+    const int lane = threadIdx.x & 31, sub = lane / LANES, sl = lane % LANES;
+    const int64_t nw = (int64_t)gridDim.x * kWarpsPerBlock;
+    for (int64_t rg = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); rg * RPW < rows; rg += nw) {
+        const int64_t r = rg * RPW + sub;
+        double acc = 0.0;
+        if (r < rows) {
+            const uint64_t e = rp[r + 1];
+#define UAT(idx) stage_u(si, ds, (int64_t)(idx))
+#define TERM(q)                                                                   \
+    (UNIFORM ? signed_by(UAT((q).x & kIdx), sg[(q).x >> 24]) * UAT((q).y)         \
+             : ws[(q).x >> 24] * UAT((q).x & kIdx) * UAT((q).y))
+            uint64_t p = rp[r] + sl;
+            for (; p + LANES < e; p += 2 * LANES) {
+                const uint2 q0 = __ldcs(rec + p), q1 = __ldcs(rec + p + LANES);
+                acc += TERM(q0);
+                acc += TERM(q1);
+            }
+            if (p < e) {
+                const uint2 q = __ldcs(rec + p);
+                acc += TERM(q);
+            }
+#undef TERM
+#undef UAT
+        }
+        acc = group_sum<LANES>(acc);
+        if (sl == 0 && r < rows) xi[r] = UNIFORM ? acc * wt.mag : acc;
+    }
+}
+
 // ---------------------------------------------------------------- RK algebra
 // out = base + sum_s coef_s * ds * K_s   (coefficients scaled by *ds_ptr
 // when ds_ptr is given, else by ds_const); vectors of length len.
