@@ -124,7 +124,17 @@ __device__ __forceinline__ int64_t lower_row(const uint32_t *rps, int64_t rows, 
 // lane sums whole rows itself in record order: no cross-lane reduction.
 //   GEN:  out[r][b] = sum alpha U0[i][b] U0[j][b]            (xi, shared memory)
 //   else: out[o][r][b] = sum beta xi[a][b] U_o[j][b]         (slopes, global)
-template <typename T, int TILE, int NOPS, bool GEN>
+// v with its sign bit flipped by the sign bit of mask (bit 31)
+__device__ __forceinline__ float flip_by(float v, uint32_t mask) { return __uint_as_float(__float_as_uint(v) ^ mask); }
+__device__ __forceinline__ double flip_by(double v, uint32_t mask) {
+    return __longlong_as_double(__double_as_longlong(v) ^ ((long long)mask << 32));
+}
+
+// SIGNS: every factor is +-mag (codes < 32).  Then the lane that loads a
+// record decodes it once for the TILE lanes that use it: x = offset of its
+// first input in the gathered array (slot 0) with the factor's sign in bit
+// 31, y = offset of its second input; the using lanes add their slot.
+template <typename T, int TILE, int NOPS, bool GEN, bool SIGNS>
 __device__ __forceinline__ void stage_stream(const uint32_t *__restrict__ rps, int64_t rows,
                                              const uint2 *__restrict__ rec, const T *__restrict__ U,
                                              const T *__restrict__ xis, const T *__restrict__ ws, int64_t n,
@@ -157,18 +167,27 @@ __device__ __forceinline__ void stage_stream(const uint32_t *__restrict__ rps, i
         }
         cur++;
     };
+    constexpr uint32_t SX = GEN ? P : 1;          // stride of the first gathered array
+    auto decode = [&](uint2 q) -> uint2 {
+        if constexpr (SIGNS) {
+            const uint32_t neg = (negmask >> ((q.x >> 24) & 31)) & 1u;
+            return make_uint2(((q.x & kIdx) * (uint32_t)TILE * SX) | (neg << 31), q.y * (uint32_t)TILE * P);
+        } else {
+            return q;
+        }
+    };
     uint2 v[M];
 #pragma unroll
     for (int m = 0; m < M; m++) {
         const uint32_t idx = c + m * TILE + b;
-        v[m] = idx < pe ? __ldg(rec + idx) : make_uint2(0u, 0u);
+        v[m] = decode(idx < pe ? __ldg(rec + idx) : make_uint2(0u, 0u));
     }
     for (; c < pe; c += CH) {
         uint2 nv[M];
 #pragma unroll
         for (int m = 0; m < M; m++) {
             const uint32_t idx = c + CH + m * TILE + b;
-            nv[m] = idx < pe ? __ldg(rec + idx) : make_uint2(0u, 0u);
+            nv[m] = decode(idx < pe ? __ldg(rec + idx) : make_uint2(0u, 0u));
         }
         // one TILE-record slice at a time from v[0]; the slices rotate down
 #pragma unroll 1
@@ -182,14 +201,25 @@ __device__ __forceinline__ void stage_stream(const uint32_t *__restrict__ rps, i
                     uint2 q;
                     q.x = __shfl_sync(gmask, v[0].x, s0 + s, TILE);
                     q.y = __shfl_sync(gmask, v[0].y, s0 + s, TILE);
-                    const int64_t i = (int64_t)(q.x & kIdx) * TILE + b, j = (int64_t)q.y * TILE + b;
-                    const uint32_t code = q.x >> 24;
-                    const T src = GEN ? U[i * P] : xis[i];
-                    cf[s] = signs ? flip_if(src, (negmask >> (code & 31)) & 1u) : ws[code] * src;
-                    if constexpr (GEN) {
-                        uv[s][0] = U[j * P];
+                    if constexpr (SIGNS) {
+                        const uint32_t ix = (q.x & 0x7fffffffu) + (uint32_t)b * SX, iy = q.y + (uint32_t)b * P;
+                        const T src = GEN ? U[ix] : xis[ix];
+                        cf[s] = flip_by(src, q.x & 0x80000000u);
+                        if constexpr (GEN) {
+                            uv[s][0] = U[iy];
+                        } else {
+                            load_ops<NOPS, P>(U + iy, uv[s]);
+                        }
                     } else {
-                        load_ops<NOPS, P>(U + j * P, uv[s]);
+                        const int64_t i = (int64_t)(q.x & kIdx) * TILE + b, j = (int64_t)q.y * TILE + b;
+                        const uint32_t code = q.x >> 24;
+                        const T src = GEN ? U[i * P] : xis[i];
+                        cf[s] = signs ? flip_if(src, (negmask >> (code & 31)) & 1u) : ws[code] * src;
+                        if constexpr (GEN) {
+                            uv[s][0] = U[j * P];
+                        } else {
+                            load_ops<NOPS, P>(U + j * P, uv[s]);
+                        }
                     }
                 }
                 // sum them in record order, closing rows at their ends; most
@@ -229,9 +259,15 @@ template <typename T, int TILE, int NOPS>
 __device__ void rhs_tile(const Args &a, const uint32_t *__restrict__ rps0, const uint32_t *__restrict__ rps1,
                          const T *__restrict__ U, T *__restrict__ xis, const T *__restrict__ ws,
                          T *__restrict__ K) {
-    stage_stream<T, TILE, NOPS, true>(rps0, a.n_g, a.rec0, U, nullptr, ws, a.n, xis, a.signs, a.negmask, T(a.mag));
-    __syncthreads();
-    stage_stream<T, TILE, NOPS, false>(rps1, a.n, a.rec1, U, xis, ws, a.n, K, a.signs, a.negmask, T(a.mag));
+    if (a.signs) {
+        stage_stream<T, TILE, NOPS, true, true>(rps0, a.n_g, a.rec0, U, nullptr, ws, a.n, xis, 1, a.negmask, T(a.mag));
+        __syncthreads();
+        stage_stream<T, TILE, NOPS, false, true>(rps1, a.n, a.rec1, U, xis, ws, a.n, K, 1, a.negmask, T(a.mag));
+    } else {
+        stage_stream<T, TILE, NOPS, true, false>(rps0, a.n_g, a.rec0, U, nullptr, ws, a.n, xis, 0, a.negmask, T(a.mag));
+        __syncthreads();
+        stage_stream<T, TILE, NOPS, false, false>(rps1, a.n, a.rec1, U, xis, ws, a.n, K, 0, a.negmask, T(a.mag));
+    }
 }
 
 // Every (row, slot, operand) element of the RK arrays once: a thread keeps
