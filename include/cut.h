@@ -27,6 +27,13 @@
  *     them until the stream reaches that point.  "host" pointers are
  *     ordinary CPU memory, read or written before the call returns.
  *   - `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *   - "Scratch from the stream-ordered allocator" below means the library's
+ *     own memory pool of the graph's device (cudaMallocFromPoolAsync; freed
+ *     with cudaFreeAsync on the call's stream).  The pool keeps up to 1 GiB
+ *     of freed scratch reserved between calls, so that repeated calls map
+ *     no new device memory; the reserve is released when the process ends
+ *     (or the device's context is destroyed).  Allocations beyond what the
+ *     device can give fail with CUT_ERR_OUT_OF_MEMORY.
  *   - No entry point throws; each returns a cut_status and, on failure,
  *     leaves a message for cut_last_error() (thread-local).  Arguments are
  *     validated before anything is queued: on CUT_ERR_INVALID_ARG nothing

@@ -23,6 +23,7 @@
 #include <tuple>
 #include <vector>
 
+#include "alloc.h"
 #include "cut.h"
 #include "status.h"
 
@@ -574,7 +575,7 @@ static cudaError_t launch_tile(const BatchedGraphView &v, kb::Args args, int max
     size_t need = ws_bytes<T, TILE, NOPS>(v) * ctas;
     if (need > *ws_cap) {
         if (*ws_base) cudaFreeAsync(*ws_base, s);
-        e = cudaMallocAsync(ws_base, need, s);
+        e = cut::scratch_alloc(ws_base, need, s);
         if (e != cudaSuccess) return e;
         *ws_cap = need;
     }
@@ -711,7 +712,7 @@ cut_status flow_batched_impl(const BatchedGraphView &v, int device, int batch, d
     void *ws = nullptr;
     size_t ws_cap = 0;
     int *queue = nullptr;
-    cudaError_t e = cudaMallocAsync(&queue, 256, s);
+    cudaError_t e = cut::scratch_alloc(&queue, 256, s);
     auto finish = [&](cut_status st) {
         if (ws) cudaFreeAsync(ws, s);
         if (queue) cudaFreeAsync(queue, s);
@@ -739,7 +740,7 @@ cut_status flow_batched_impl(const BatchedGraphView &v, int device, int batch, d
             double *hc = nullptr, *xc = nullptr;
             int *so = nullptr;
             size_t hb = (size_t)batch * v.n * 8, xb = (size_t)batch * n_obs * v.n * 8;
-            e = cudaMallocAsync(&hc, hb + xb + 2 * (size_t)batch * 4 + 64, s);
+            e = cut::scratch_alloc(&hc, hb + xb + 2 * (size_t)batch * 4 + 64, s);
             if (e != cudaSuccess) return finish(set_error(CUT_ERR_OUT_OF_MEMORY, "cut_flow_batched: autotune scratch"));
             xc = hc + (size_t)batch * v.n;
             so = (int *)(xc + (size_t)batch * n_obs * v.n);

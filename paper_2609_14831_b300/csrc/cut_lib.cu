@@ -11,6 +11,7 @@
 #include <thread>
 #include <vector>
 
+#include "alloc.h"
 #include "bundle.h"
 #include "cut.h"
 #include "flow_kernels.cuh"
@@ -37,6 +38,44 @@ cut_status set_ok() { return CUT_OK; }
                              std::string(#expr) + ": " + cudaGetErrorString(_e));               \
         }                                                                                       \
     } while (0)
+
+static void *current_context();
+
+// One pool per device, remade when the device's context changes (a device
+// reset invalidates the old handle).
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[256] = {nullptr};
+static void *g_pool_ctx[256] = {nullptr};
+
+cudaError_t scratch_alloc(void **p, size_t bytes, cudaStream_t s) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 256) return cudaMallocAsync(p, bytes, s);
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        void *ctx = current_context();
+        if (!g_pool[dev] || !ctx || ctx != g_pool_ctx[dev]) {
+            cudaMemPoolProps props;
+            memset(&props, 0, sizeof(props));
+            props.allocType = cudaMemAllocationTypePinned;
+            props.handleTypes = cudaMemHandleTypeNone;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            cudaMemPool_t np = nullptr;
+            e = cudaMemPoolCreate(&np, &props);
+            if (e != cudaSuccess) return e;
+            unsigned long long keep = kScratchKeepBytes;
+            e = cudaMemPoolSetAttribute(np, cudaMemPoolAttrReleaseThreshold, &keep);
+            if (e != cudaSuccess) return e;
+            g_pool[dev] = np;
+            g_pool_ctx[dev] = current_context();
+        }
+        pool = g_pool[dev];
+    }
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
 
 struct DevCSR {
     uint64_t *rp = nullptr;
@@ -522,7 +561,7 @@ cut_status cut_rhs_outside(const cut_graph *g, const double *h, int n_obs, const
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = g->host.n(), nout = g->host.n_out();
     double *xi = nullptr;
-    CUDA_TRY(cudaMallocAsync(&xi, std::max<int64_t>(1, g->host.n_g()) * 8, s));
+    CUDA_TRY(scratch_alloc(&xi, std::max<int64_t>(1, g->host.n_g()) * 8, s));
     launch_gen(g, h, xi, s, nullptr);
     const double *xs[64];
     double *cs[64];
@@ -575,9 +614,9 @@ cut_status cut_rhs(const cut_graph *g, const double *h, int n_obs, const double 
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = g->host.n();
     double *xi = xi_out;
-    if (!xi) CUDA_TRY(cudaMallocAsync(&xi, std::max<int64_t>(1, g->host.n_g()) * 8, s));
+    if (!xi) CUDA_TRY(scratch_alloc(&xi, std::max<int64_t>(1, g->host.n_g()) * 8, s));
     void *df = nullptr;
-    CUDA_TRY(cudaMallocAsync(&df, operand_scratch_bytes(g), s));
+    CUDA_TRY(scratch_alloc(&df, operand_scratch_bytes(g), s));
     launch_gen(g, h, xi, s, nullptr);
     const double *xs[64];
     double *dxs[64];
@@ -609,7 +648,7 @@ cut_status cut_apply_L(const cut_graph *g, const double *xi, int n_ops, const do
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = g->host.n();
     void *df = nullptr;
-    CUDA_TRY(cudaMallocAsync(&df, operand_scratch_bytes(g), s));
+    CUDA_TRY(scratch_alloc(&df, operand_scratch_bytes(g), s));
     const double *xs[64];
     double *dxs[64];
     for (int o = 0; o < n_ops; o++) { xs[o] = x + o * n; dxs[o] = dx + o * n; }
@@ -647,7 +686,7 @@ extern "C" cut_status cut_rhs_jvp(const cut_graph *g, const double *h, int n_obs
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = g->host.n(), ng = std::max<int64_t>(1, g->host.n_g());
     double *buf = nullptr;
-    CUDA_TRY(cudaMallocAsync(&buf, 2 * ng * 8, s));
+    CUDA_TRY(scratch_alloc(&buf, 2 * ng * 8, s));
     double *xi = buf, *dxi = buf + ng;
     const k::Weights w = weights_of(g);
     launch_gen(g, h, xi, s, nullptr);
@@ -999,7 +1038,7 @@ extern "C" cut_status cut_rhs_adjoint(const cut_graph *g, const double *h, int n
     // stacked copies so that one code path serves single calls and flows
     double *buf = nullptr;
     const size_t L = (size_t)nops * n;
-    CUDA_TRY(cudaMallocAsync(&buf, (3 * L + 2 * ng + n) * 8 + adjoint_scratch_bytes(g), s));
+    CUDA_TRY(scratch_alloc(&buf, (3 * L + 2 * ng + n) * 8 + adjoint_scratch_bytes(g), s));
     double *Y = buf, *W = buf + L, *YB = buf + 2 * L, *xi = buf + 3 * L, *xib = xi + ng, *xb0 = xib + ng;
     void *pk = xb0 + n;
     CUDA_TRY(cudaMemcpyAsync(Y, h, n * 8, cudaMemcpyDeviceToDevice, s));
@@ -1045,7 +1084,7 @@ static cut_status alloc_work(FlowWork &w, int64_t L, int64_t ng, int64_t nrec, c
                              size_t df_bytes = 0) {
     size_t doubles = (size_t)(3 + 7) * L + ng + 2 * nrec + 64 + df_bytes / 8 + 1;
     size_t bytes = doubles * 8 + sizeof(k::Control) + 64;
-    CUDA_TRY(cudaMallocAsync(&w.base, bytes, s));
+    CUDA_TRY(scratch_alloc(&w.base, bytes, s));
     double *p = (double *)w.base;
     w.Y = p; p += L;
     w.U = p; p += L;
@@ -1075,13 +1114,20 @@ static void stage_input(const FlowWork &w, const double *A, int i, int64_t L, co
 // K_i = f(Y + ds sum_j A[j] K_j): the stage input, its packed operand
 // blocks and the generator in one launch (stage_gen), then the commutator
 // stage over the packed blocks; U_full (may be null) keeps the stage input.
-// Double-float arithmetic, more than eight operands or no operand scratch
-// take the separate combination and right-hand-side launches.  Same bits.
+// The fused generator forms each of a record's two inputs as Y + sum c K
+// (1 + nk loads instead of 1), which only pays where the launches it saves
+// dominate: a generator stage of at most kFuseGenRecords records (8-orbital
+// model, 4.6e3 records: 15.7 us per right-hand side fused against 18.5 us;
+// the 16-orbital stress graph, 3.5e6 records: 48 us per RK4 stage fused
+// against 36 us separate).  Larger graphs, double-float arithmetic, more
+// than eight operands or no operand scratch take the separate combination
+// and right-hand-side launches.  Same bits either way.
+constexpr int64_t kFuseGenRecords = 1 << 16;
 static void fused_stage(const cut_graph *g, FlowWork &w, const double *A, int i, int nops, const double *dsp,
                         double dsc, cudaStream_t s, const int *done, double *U_full, double *Kout) {
     const int64_t n = g->host.n(), L = (int64_t)nops * n;
     double *X4 = reinterpret_cast<double *>(operand_blocks(g, w.df));
-    if (g->arith != CUT_ARITH_FP64 || nops > 8 || !X4) {
+    if (g->arith != CUT_ARITH_FP64 || nops > 8 || !X4 || g->st[0].R > kFuseGenRecords) {
         double *U = U_full ? U_full : w.U;
         const double *in = w.Y;
         if (i > 0) {
@@ -1370,7 +1416,7 @@ extern "C" cut_status cut_flow_vjp(const cut_graph *g, const double *h0, int n_o
     const size_t dfb = operand_scratch_bytes(g) / 8 + 4, pkb = adjoint_scratch_bytes(g) / 8 + 4;
     double *buf = nullptr;
     size_t tot = (size_t)(ncp + (C + 1) + 3 * S + 5) * L + 2 * ng + n + N + 1 + dfb + pkb;
-    cudaError_t e = cudaMallocAsync(&buf, tot * 8, s);
+    cudaError_t e = scratch_alloc(&buf, tot * 8, s);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         end_work(sp);
@@ -1716,7 +1762,7 @@ extern "C" cut_status cut_shard_commutator(const cut_graph *g, const double *xi,
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = g->host.n();
     void *df = nullptr;
-    CUDA_TRY(cudaMallocAsync(&df, operand_scratch_bytes(g), s));
+    CUDA_TRY(scratch_alloc(&df, operand_scratch_bytes(g), s));
     const double *xs[64];
     double *dxs[64];
     for (int o = 0; o < n_ops; o++) { xs[o] = x + o * n; dxs[o] = dx_part + o * rows; }

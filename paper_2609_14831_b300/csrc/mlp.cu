@@ -20,6 +20,7 @@
 #include <string>
 #include <vector>
 
+#include "alloc.h"
 #include "cut.h"
 #include "status.h"
 #include "tc_gemm.cuh"
@@ -650,7 +651,7 @@ cut_status cut_mlp_fit_linear(cut_mlp *m, int batch, const float *x, const doubl
     const int64_t rpc = (batch + chunks - 1) / chunks;
     const size_t np_ = (size_t)chunks * P * ncol, nres = (size_t)chunks * m->n_out;
     double *buf = nullptr;
-    cudaError_t e = cudaMallocAsync(&buf, (np_ + (size_t)P * ncol + (size_t)P * m->n_out + nres + m->n_out) * 8 + 64, s);
+    cudaError_t e = cut::scratch_alloc(&buf, (np_ + (size_t)P * ncol + (size_t)P * m->n_out + nres + m->n_out) * 8 + 64, s);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return set_error(CUT_ERR_OUT_OF_MEMORY, "cut_mlp_fit_linear: scratch");
@@ -659,7 +660,7 @@ cut_status cut_mlp_fit_linear(cut_mlp *m, int batch, const float *x, const doubl
            *ss = rp + nres;
     float *w = nullptr;
     if (weight) {
-        e = cudaMallocAsync(&w, m->n_out * 4, s);
+        e = cut::scratch_alloc(&w, m->n_out * 4, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(w, weight, m->n_out * 4, cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) {
             (void)cudaGetLastError();
