@@ -288,7 +288,7 @@ static void launch_comm(const cut_graph *g, const double *xi, int nops, const do
         }
         k::Ops<8> red;
         for (int t = 0; t < nops; t++) { red.x[t] = piece + t * c.pieces; red.dx[t] = dxs[t]; }
-        k::piece_reduce<<<grid_for_len(c.rows), 256, 0, s>>>(c.pvr, c.rows, red, nops, nullptr);
+        k::piece_reduce<<<grid_for_len(c.rows * nops), 256, 0, s>>>(c.pvr, c.rows, red, nops, nullptr);
         return;
     }
     if (X4 && nops <= 8) {
@@ -344,6 +344,36 @@ static void launch_gen(const cut_graph *g, const double *h, double *xi, cudaStre
     else gen_launch<8>(c, w, h, xi, s, done);
 }
 
+// The generator of h = xs[0] and, when the commutator stage will read packed
+// FP64 blocks (X4 given, at most eight operands, FP64 arithmetic), the
+// packing of xs into X4, in one launch.  Returns whether X4 was packed.
+static bool launch_gen_pack(const cut_graph *g, const double *const *xs, int nops, double *xi, double *X4,
+                            cudaStream_t s, const int *done) {
+    if (!X4 || nops > 8 || g->arith != CUT_ARITH_FP64) {
+        launch_gen(g, xs[0], xi, s, done);
+        return false;
+    }
+    const DevCSR &c = g->st[0];
+    const k::Weights w = weights_of(g);
+    const int64_t n = g->host.n();
+    const int gl = gen_lanes(c.lane_rows);
+    const int grid = std::max(grid_for_len(n), grid_for_groups(c.rows, gl));
+    switch (nops) {
+#define CASE(M)                                                                                       \
+    case M: {                                                                                         \
+        k::Ops<M> ops;                                                                                \
+        for (int t = 0; t < M; t++) { ops.x[t] = xs[t]; ops.dx[t] = nullptr; }                        \
+        if (w.uniform && gl == 4) k::gen_pack<M, true, 4><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, xi, c.rows, ops, n, X4, done); \
+        else if (w.uniform) k::gen_pack<M, true, 8><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, xi, c.rows, ops, n, X4, done); \
+        else if (gl == 4) k::gen_pack<M, false, 4><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, xi, c.rows, ops, n, X4, done); \
+        else k::gen_pack<M, false, 8><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, xi, c.rows, ops, n, X4, done); \
+    } break;
+        CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+#undef CASE
+    }
+    return true;
+}
+
 // Double-float commutator stage: split xi and up to three operands at a time
 // into FP32 pairs (xi2[n_g], X2[n][4]) and apply the records on the FP32 pipes.
 static void launch_comm_df(const cut_graph *g, const double *xi, float2 *xi2, float2 *X2, int nops,
@@ -385,7 +415,7 @@ static void launch_comm_df(const cut_graph *g, const double *xi, float2 *xi2, fl
         if (pieces) {
             k::Ops<8> red;
             for (int t = 0; t < m; t++) { red.x[t] = piece + t * c.rows; red.dx[t] = dxs[o0 + t]; }
-            k::piece_reduce<<<grid_for_len(rows_c.rows), 256, 0, s>>>(rows_c.pvr, rows_c.rows, red, m, nullptr);
+            k::piece_reduce<<<grid_for_len(rows_c.rows * m), 256, 0, s>>>(rows_c.pvr, rows_c.rows, red, m, nullptr);
         }
     }
 }
@@ -397,13 +427,15 @@ static double *piece_area(const cut_graph *g, float2 *X2) {
 
 // L(h) x_o for given xi (either arithmetic); df buffers may be null for FP64
 static void apply_L(const cut_graph *g, const double *xi, float2 *xi2, float2 *X2, int nops,
-                    const double *const *xs, double *const *dxs, cudaStream_t s, const int *done) {
+                    const double *const *xs, double *const *dxs, cudaStream_t s, const int *done,
+                    bool prepacked = false) {
     // without scratch (adjoint recomputation) the stage runs in FP64 with one
     // gather per operand
     if (g->arith == CUT_ARITH_DF64 && xi2 && X2)
         launch_comm_df(g, xi, xi2, X2, nops, xs, dxs, s, done, piece_area(g, X2));
     else
-        launch_comm(g, xi, nops, xs, dxs, s, done, 1, reinterpret_cast<double *>(X2), nullptr, piece_area(g, X2));
+        launch_comm(g, xi, nops, xs, dxs, s, done, 1, reinterpret_cast<double *>(X2), nullptr, piece_area(g, X2),
+                    prepacked);
 }
 
 static size_t operand_scratch_bytes(const cut_graph *g) {
@@ -426,11 +458,12 @@ static float2 *operand_blocks(const cut_graph *g, void *df) {
 static void stacked_rhs(const cut_graph *g, const double *Y, double *DY, int nops, double *xi,
                         cudaStream_t s, const int *done, void *df = nullptr) {
     const int64_t n = g->host.n();
-    launch_gen(g, Y, xi, s, done);
     const double *xs[64];
     double *dxs[64];
     for (int o = 0; o < nops; o++) { xs[o] = Y + o * n; dxs[o] = DY + o * n; }
-    apply_L(g, xi, (float2 *)df, operand_blocks(g, df), nops, xs, dxs, s, done);
+    float2 *X2 = operand_blocks(g, df);
+    const bool packed = launch_gen_pack(g, xs, nops, xi, reinterpret_cast<double *>(X2), s, done);
+    apply_L(g, xi, (float2 *)df, X2, nops, xs, dxs, s, done, packed);
 }
 
 }  // namespace cut
@@ -617,13 +650,14 @@ cut_status cut_rhs(const cut_graph *g, const double *h, int n_obs, const double 
     if (!xi) CUDA_TRY(scratch_alloc(&xi, std::max<int64_t>(1, g->host.n_g()) * 8, s));
     void *df = nullptr;
     CUDA_TRY(scratch_alloc(&df, operand_scratch_bytes(g), s));
-    launch_gen(g, h, xi, s, nullptr);
     const double *xs[64];
     double *dxs[64];
     xs[0] = h;
     dxs[0] = dh;
     for (int o = 0; o < n_obs; o++) { xs[o + 1] = x + o * n; dxs[o + 1] = dx + o * n; }
-    apply_L(g, xi, (float2 *)df, operand_blocks(g, df), n_obs + 1, xs, dxs, s, nullptr);
+    float2 *X2 = operand_blocks(g, df);
+    const bool packed = launch_gen_pack(g, xs, n_obs + 1, xi, reinterpret_cast<double *>(X2), s, nullptr);
+    apply_L(g, xi, (float2 *)df, X2, n_obs + 1, xs, dxs, s, nullptr, packed);
     CUDA_TRY(cudaGetLastError());
     if (!xi_out) CUDA_TRY(cudaFreeAsync(xi, s));
     if (df) CUDA_TRY(cudaFreeAsync(df, s));
@@ -925,7 +959,7 @@ static void stacked_vjp(const cut_graph *g, const double *Y, const double *W, do
         {
             k::Ops<8> red;
             for (int o = 0; o < nops; o++) { red.x[o] = piece + o * ptx; red.dx[o] = o == 0 ? xbar0 : YB + o * n; }
-            k::piece_reduce<<<grid_for_len(n), 256, 0, s>>>(g->tx.vr, n, red, nops, nullptr);
+            k::piece_reduce<<<grid_for_len(n * nops), 256, 0, s>>>(g->tx.vr, n, red, nops, nullptr);
         }
         pack_operands(g, Y, nops, X4, s);
         const k::Weights w = weights_of(g);
@@ -991,7 +1025,7 @@ static void stacked_vjp(const cut_graph *g, const double *Y, const double *W, do
             red.x[t] = piece + t * ptx;
             red.dx[t] = (o0 + t == 0) ? xbar0 : YB + (o0 + t) * n;
         }
-        k::piece_reduce<<<grid_for_len(n), 256, 0, s>>>(g->tx.vr, n, red, m, nullptr);
+        k::piece_reduce<<<grid_for_len(n * m), 256, 0, s>>>(g->tx.vr, n, red, m, nullptr);
     }
     for (int o0 = 0; o0 < nops; o0 += 4) {
         int m = std::min(4, nops - o0);

@@ -67,17 +67,13 @@ __device__ __forceinline__ double group_sum(double v) {
 }
 
 // Generator stage: xi[a] = sum_e alpha_e h[i_e] h[j_e]   (Eq. graph-actions, line 1)
+// over the rows of the calling grid (ws/sg: the factor tables in shared memory)
 template <bool UNIFORM, int LANES>
-__global__ void __launch_bounds__(kBlock) gen_stage(const uint64_t *__restrict__ rp,
-                                                    const uint2 *__restrict__ rec, Weights wt,
-                                                    const double *__restrict__ h,
-                                                    double *__restrict__ xi, int64_t rows,
-                                                    const int *done) {
+__device__ __forceinline__ void gen_rows(const uint64_t *__restrict__ rp, const uint2 *__restrict__ rec,
+                                         const Weights &wt, const double *__restrict__ h,
+                                         double *__restrict__ xi, int64_t rows, const double *ws,
+                                         const unsigned long long *sg) {
     constexpr int RPW = 32 / LANES;
-    __shared__ double ws[256];
-    __shared__ unsigned long long sg[256];
-    if (skip(done)) return;
-    load_weights(ws, sg, wt);
     const int lane = threadIdx.x & 31, sub = lane / LANES, sl = lane % LANES;
     const int64_t nw = (int64_t)gridDim.x * kWarpsPerBlock;
     for (int64_t rg = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5); rg * RPW < rows; rg += nw) {
@@ -103,6 +99,19 @@ __global__ void __launch_bounds__(kBlock) gen_stage(const uint64_t *__restrict__
         acc = group_sum<LANES>(acc);
         if (sl == 0 && r < rows) xi[r] = UNIFORM ? acc * wt.mag : acc;
     }
+}
+
+template <bool UNIFORM, int LANES>
+__global__ void __launch_bounds__(kBlock) gen_stage(const uint64_t *__restrict__ rp,
+                                                    const uint2 *__restrict__ rec, Weights wt,
+                                                    const double *__restrict__ h,
+                                                    double *__restrict__ xi, int64_t rows,
+                                                    const int *done) {
+    __shared__ double ws[256];
+    __shared__ unsigned long long sg[256];
+    if (skip(done)) return;
+    load_weights(ws, sg, wt);
+    gen_rows<UNIFORM, LANES>(rp, rec, wt, h, xi, rows, ws, sg);
 }
 
 template <int NOPS>
@@ -252,6 +261,25 @@ __global__ void pack_x4(Ops<NOPS> ops, int64_t n, double *__restrict__ X4, const
 #pragma unroll
         for (int o = 0; o < NOPS; o++) X4[4 * NB * j + o] = ops.x[o][j];
     }
+}
+
+// pack_x4 and gen_stage in one launch (they are independent: the generator
+// reads h itself, not the packed blocks); the same values as the two.
+template <int NOPS, bool UNIFORM, int LANES>
+__global__ void __launch_bounds__(kBlock) gen_pack(const uint64_t *__restrict__ rp, const uint2 *__restrict__ rec,
+                                                   Weights wt, double *__restrict__ xi, int64_t rows,
+                                                   Ops<NOPS> ops, int64_t n, double *__restrict__ X4,
+                                                   const int *done) {
+    constexpr int NB = (NOPS + 3) / 4;
+    __shared__ double ws[256];
+    __shared__ unsigned long long sg[256];
+    if (skip(done)) return;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int o = 0; o < NOPS; o++) X4[4 * NB * j + o] = ops.x[o][j];
+    }
+    load_weights(ws, sg, wt);
+    gen_rows<UNIFORM, LANES>(rp, rec, wt, ops.x[0], xi, rows, ws, sg);
 }
 
 // ---------------------------------------------------------------- double-float
@@ -638,16 +666,21 @@ __global__ void __launch_bounds__(kBlock) genT_lanes(const uint64_t *__restrict_
 }
 
 // Rows split into pieces: out_o[r] = add[r] (operand 0, if given) + the
-// piece sums in_o[v] for v = vr[r] .. vr[r+1]-1, added in piece order.
+// piece sums in_o[v] for v = vr[r] .. vr[r+1]-1, added in piece order.  One
+// thread per (operand, row); neighbouring threads take neighbouring rows of
+// one operand, so their pieces and outputs are neighbours in memory.
 __global__ void piece_reduce(const uint64_t *__restrict__ vr, int64_t rows, Ops<8> io, int nops,
                              const double *__restrict__ add) {
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t total = rows * nops;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int o = (int)(t / rows);
+        const int64_t r = t - (int64_t)o * rows;
         const uint64_t v0 = vr[r], v1 = vr[r + 1];
-        for (int o = 0; o < nops; o++) {
-            double acc = io.x[o][v0];
-            for (uint64_t v = v0 + 1; v < v1; v++) acc += io.x[o][v];
-            io.dx[o][r] = (add && o == 0) ? add[r] + acc : acc;
-        }
+        const double *__restrict__ in = io.x[o];
+        double acc = in[v0];
+#pragma unroll 4
+        for (uint64_t v = v0 + 1; v < v1; v++) acc += in[v];
+        io.dx[o][r] = (add && o == 0) ? add[r] + acc : acc;
     }
 }
 
