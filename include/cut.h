@@ -430,6 +430,11 @@ cut_status cut_mlp_create(int n_in, int n_hidden, int n_out, uint64_t seed, int 
 cut_status cut_mlp_free(cut_mlp *m);
 /* host in: scale[n_out] (> 0), shift[n_out] */
 cut_status cut_mlp_set_output_affine(cut_mlp *m, const float *scale, const float *shift);
+/* host out: scale[n_out], shift[n_out] (either may be NULL, not both), the
+ * output affine in use (after cut_mlp_fit_linear: the residual RMS of each
+ * output over sqrt(weight), and the intercept).  Waits for the device's
+ * queued work first.  Errors: INVALID_ARG, CUDA. */
+cut_status cut_mlp_get_output_affine(const cut_mlp *m, float *scale, float *shift);
 /* Optional linear skip term: y = scale * y_hat + shift + J x with
  * J[n_out][n_in] (host, FP32, copied), applied in FP32 on the CUDA cores in
  * the last layer's epilogue and removed from the targets in training

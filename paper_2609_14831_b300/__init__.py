@@ -112,6 +112,7 @@ def lib():
         "cut_mlp_create": (st, [i, i, i, ctypes.c_uint64, i, ctypes.POINTER(VP)]),
         "cut_mlp_free": (st, [VP]),
         "cut_mlp_set_output_affine": (st, [VP, VP, VP]),
+        "cut_mlp_get_output_affine": (st, [VP, VP, VP]),
         "cut_mlp_set_linear": (st, [VP, VP]),
         "cut_mlp_param_count": (i64, [VP]),
         "cut_mlp_get_params": (st, [VP, VP, i]),
@@ -448,6 +449,13 @@ class MLP:
         sc = np.ascontiguousarray(scale, dtype=np.float32)
         sh = np.ascontiguousarray(shift, dtype=np.float32)
         check(lib().cut_mlp_set_output_affine(self._h, sc.ctypes.data, sh.ctypes.data))
+
+    def output_affine(self):
+        """(scale, shift) of the outputs (host, FP32) as the model uses them."""
+        sc = np.empty(self.n_out, dtype=np.float32)
+        sh = np.empty(self.n_out, dtype=np.float32)
+        check(lib().cut_mlp_get_output_affine(self._h, sc.ctypes.data, sh.ctypes.data))
+        return sc, sh
 
     def set_linear(self, J):
         """Linear skip y += J x (J: [n_out, n_in]); None removes it."""

@@ -369,6 +369,19 @@ static cut_status make_map(CUtensorMap *map, const void *ptr, int rows, int cols
     return CUT_OK;
 }
 
+// SMs of the current device (148 on B300), read once per device.
+static int num_sms() {
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+    if (!cache[dev]) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        cache[dev] = n > 0 ? n : 148;
+    }
+    return cache[dev];
+}
+
 // C[M][N] = A[M][K] B[N][K]^T, M % 128 == 0, N % 64 == 0, K % (64 splits) == 0.
 // splits > 1: split k, partial products to ep.out_f32 + z ep.split_stride.
 static cut_status gemm(const bf16 *A, const bf16 *B, int M, int N, int K, tc::Epi ep, cudaStream_t s,
@@ -386,11 +399,23 @@ static cut_status gemm(const bf16 *A, const bf16 *B, int M, int N, int K, tc::Ep
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         kern<<<grid, tc::kThreads, sm, s>>>(ma, mb, K / splits, ep);
     };
+    // at most one CTA per SM: the deep ring (one CTA per SM, more copies in flight)
+    const bool deep = (int64_t)grid.x * grid.y * grid.z <= num_sms();
+    constexpr int D = tc::STAGES_DEEP;
     const size_t sm128 = tc::gemm_smem_bytes<128>(), sm64 = tc::gemm_smem_bytes<64>();
-    if (bn == 128) {
+    const size_t sm128d = tc::gemm_smem_bytes<128, D>(), sm64d = tc::gemm_smem_bytes<64, D>();
+    if (bn == 128 && deep) {
+        if (act == tc::kGelu) launch(tc::gemm_bf16_tn<128, tc::kGelu, D>, sm128d);
+        else if (act == tc::kGeluGrad) launch(tc::gemm_bf16_tn<128, tc::kGeluGrad, D>, sm128d);
+        else launch(tc::gemm_bf16_tn<128, tc::kLinear, D>, sm128d);
+    } else if (bn == 128) {
         if (act == tc::kGelu) launch(tc::gemm_bf16_tn<128, tc::kGelu>, sm128);
         else if (act == tc::kGeluGrad) launch(tc::gemm_bf16_tn<128, tc::kGeluGrad>, sm128);
         else launch(tc::gemm_bf16_tn<128, tc::kLinear>, sm128);
+    } else if (deep) {
+        if (act == tc::kGelu) launch(tc::gemm_bf16_tn<64, tc::kGelu, D>, sm64d);
+        else if (act == tc::kGeluGrad) launch(tc::gemm_bf16_tn<64, tc::kGeluGrad, D>, sm64d);
+        else launch(tc::gemm_bf16_tn<64, tc::kLinear, D>, sm64d);
     } else {
         if (act == tc::kGelu) launch(tc::gemm_bf16_tn<64, tc::kGelu>, sm64);
         else if (act == tc::kGeluGrad) launch(tc::gemm_bf16_tn<64, tc::kGeluGrad>, sm64);
@@ -610,6 +635,19 @@ cut_status cut_mlp_set_output_affine(cut_mlp *m, const float *scale, const float
     cudaSetDevice(m->device);
     cudaMemcpy(m->scale, scale, m->n_out * 4, cudaMemcpyHostToDevice);
     cudaMemcpy(m->shift, shift, m->n_out * 4, cudaMemcpyHostToDevice);
+    return set_ok();
+}
+
+cut_status cut_mlp_get_output_affine(const cut_mlp *m, float *scale, float *shift) {
+    if (!m || (!scale && !shift)) return set_error(CUT_ERR_INVALID_ARG, "cut_mlp_get_output_affine: null argument");
+    cudaSetDevice(m->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess && scale) e = cudaMemcpy(scale, m->scale, m->n_out * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && shift) e = cudaMemcpy(shift, m->shift, m->n_out * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return set_error(CUT_ERR_CUDA, std::string("cut_mlp_get_output_affine: ") + cudaGetErrorString(e));
+    }
     return set_ok();
 }
 

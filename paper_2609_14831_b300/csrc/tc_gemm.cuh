@@ -4,7 +4,7 @@
 //   C[M, N] = A[M, K] * B[N, K]^T     (both operands K-major, row-major in HBM)
 //
 // One CTA of 128 threads computes a 128 x BN tile:
-//   warp 0, lane 0 : TMA producer, STAGES-deep ring of 128x64 / BNx64 tiles
+//   warp 0, lane 0 : TMA producer, ST-deep ring of 128x64 / BNx64 tiles
 //                    (128-byte swizzle), one mbarrier pair per stage;
 //   warp 1, lane 0 : issues tcgen05.mma (M=128, N=BN, K=16 per instruction)
 //                    and tcgen05.commit to release each stage;
@@ -26,7 +26,12 @@ namespace tc {
 
 constexpr int BM = 128;
 constexpr int BK = 64;          // one 128-byte swizzle row of BF16
-constexpr int STAGES = 3;          // 97 KB of ring at BN = 128: two CTAs per SM
+// Ring depth: 3 stages (97 KB at BN = 128) let two CTAs share an SM, for
+// grids of more than one wave; a grid of at most one CTA per SM takes 6
+// (193 KB, one CTA per SM), so that each CTA keeps twice the operand copies
+// in flight over its k loop.
+constexpr int STAGES = 3;
+constexpr int STAGES_DEEP = 6;
 constexpr int kThreads = 256;          // 8 warps: two per TMEM lane quarter share the epilogue
 constexpr long long kSpinLimit = 1ll << 26;
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;   // a pipeline wait gives up after 1 s
@@ -139,16 +144,16 @@ __device__ __forceinline__ float dgelu(float x) {
 // the error function on every element).
 enum EpiAct { kLinear = 0, kGelu = 1, kGeluGrad = 2 };
 
-template <int BN, int ACT>
-__global__ void __launch_bounds__(kThreads, 2)
+template <int BN, int ACT, int ST = STAGES>
+__global__ void __launch_bounds__(kThreads, ST <= STAGES ? 2 : 1)
     gemm_bf16_tn(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int K, Epi ep) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte aligned tile ring
     unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
     unsigned char *sA = base;
-    unsigned char *sB = base + STAGES * A_BYTES;
-    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], done;
+    unsigned char *sB = base + ST * A_BYTES;
+    __shared__ __align__(8) uint64_t full[ST], empty[ST], done;
     __shared__ uint32_t tmem_base;
     __shared__ volatile int failed;
 
@@ -161,7 +166,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         // start fetching both tensor maps while the barriers and TMEM are set up
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
-        for (int s = 0; s < STAGES; s++) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        for (int s = 0; s < ST; s++) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
         mbar_init(&done, 1);
         failed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -181,8 +186,8 @@ __global__ void __launch_bounds__(kThreads, 2)
         // producer
         const bool stall = ep.stall && *ep.stall;
         for (int kt = 0; kt < KT && !failed && !stall; kt++) {
-            const int s = kt % STAGES;
-            if (kt >= STAGES && !mbar_wait(&empty[s], ((kt / STAGES) - 1) & 1)) { failed = 1; break; }
+            const int s = kt % ST;
+            if (kt >= ST && !mbar_wait(&empty[s], ((kt / ST) - 1) & 1)) { failed = 1; break; }
             mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
             tma_load_2d(sA + s * A_BYTES, &tmA, &full[s], kbase + kt * BK, m0);
             tma_load_2d(sB + s * B_BYTES, &tmB, &full[s], kbase + kt * BK, n0);
@@ -192,8 +197,8 @@ __global__ void __launch_bounds__(kThreads, 2)
         // MMA issuer
         constexpr uint32_t idesc = idesc_bf16(BN);
         for (int kt = 0; kt < KT; kt++) {
-            const int s = kt % STAGES;
-            if (!mbar_wait(&full[s], (kt / STAGES) & 1)) { failed = 1; break; }
+            const int s = kt % ST;
+            if (!mbar_wait(&full[s], (kt / ST) & 1)) { failed = 1; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
             for (int kk = 0; kk < BK / 16; kk++) {
@@ -228,7 +233,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         // stores are coalesced; the transposed output is written back from
         // the row layout, where it is coalesced too.
         static_assert(BN % 32 == 0, "epilogue works on 32-column slices");
-        static_assert(kThreads / 32 * 2 * 32 * 33 * 4 <= STAGES * (A_BYTES + B_BYTES), "staging fits in the ring");
+        static_assert(kThreads / 32 * 2 * 32 * 33 * 4 <= ST * (A_BYTES + B_BYTES), "staging fits in the ring");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         float *stile = reinterpret_cast<float *>(base) + warp * (2 * 32 * 33);
         float *ltile = stile + 32 * 33;        // linear-skip terms, same layout
@@ -324,8 +329,8 @@ __global__ void __launch_bounds__(kThreads, 2)
     } else {
         if (threadIdx.x == 0) {
             // let the copies this thread issued land before the CTA exits
-            for (int kt = issued - STAGES < 0 ? 0 : issued - STAGES; kt < issued; kt++)
-                mbar_wait(&full[kt % STAGES], (kt / STAGES) & 1);
+            for (int kt = issued - ST < 0 ? 0 : issued - ST; kt < issued; kt++)
+                mbar_wait(&full[kt % ST], (kt / ST) & 1);
             if (ep.err) atomicExch(ep.err, 1);
         }
     }
@@ -334,9 +339,9 @@ __global__ void __launch_bounds__(kThreads, 2)
     if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
 }
 
-template <int BN>
+template <int BN, int ST = STAGES>
 constexpr size_t gemm_smem_bytes() {
-    return 1024 + (size_t)STAGES * (BM * BK * 2 + BN * BK * 2);
+    return 1024 + (size_t)ST * (BM * BK * 2 + BN * BK * 2);
 }
 
 }  // namespace tc

@@ -26,8 +26,12 @@ import paper_2609_14831_b300 as cg
 
 
 class Surrogate:
+    """outputs: the flowed coefficients the networks predict (indices into
+    the registry; None = all of them).  Predictions come back as full-length
+    vectors with NaN in the coefficients the networks do not predict."""
+
     def __init__(self, graph, h_ref, P, observables, n_hidden=512, members=2, seed=0, s1=10.0,
-                 loose_rtol=1e-6, tight_rtol=1e-10, atol=1e-12):
+                 loose_rtol=1e-6, tight_rtol=1e-10, atol=1e-12, outputs=None):
         import torch
         self.torch = torch
         self.G = graph
@@ -39,8 +43,10 @@ class Surrogate:
         self.n_in = self.P.shape[1]
         self.s1 = s1
         self.loose_rtol, self.tight_rtol, self.atol = loose_rtol, tight_rtol, atol
-        self.nets = [cg.MLP(self.n_in, n_hidden, self.n, seed=seed + 7919 * k, device=graph.device_index)
-                     for k in range(members)]
+        self.outputs = np.arange(self.n) if outputs is None else np.asarray(outputs, dtype=np.int64)
+        self._out_dev = torch.as_tensor(self.outputs, device=self.dev)
+        self.nets = [cg.MLP(self.n_in, n_hidden, len(self.outputs), seed=seed + 7919 * k,
+                            device=graph.device_index) for k in range(members)]
         self.theta_scale = 1.0
         self.tau = None
 
@@ -72,23 +78,38 @@ class Surrogate:
         torch = self.torch
         return (torch.as_tensor(theta, dtype=torch.float32, device=self.dev) / self.theta_scale).contiguous()
 
-    def fit(self, theta, targets, epochs=40, batch=512, lr=2e-3, weight_decay=0.0, seed=0, weight=None, log=None):
+    def fit(self, theta, targets, epochs=40, batch=512, lr=2e-3, weight_decay=0.0, seed=0, weight=None, log=None,
+            absolute=False):
         """Device least-squares affine part, then AdamW on the standardised
-        MSE of each member (library kernels).  `weight` (per output, > 0)
-        makes the chosen outputs count more in the loss.  Returns the mean
-        batch loss per epoch of every member."""
+        MSE of each member (library kernels).  targets: [N, n] flowed
+        coefficients (the predicted outputs are taken from them).  `weight`
+        (per coefficient of the registry, > 0) makes the chosen outputs count
+        more in the loss.  absolute: every output's residual is scaled by the
+        same constant instead of its own residual RMS, so the loss weighs
+        absolute errors (what a gate with an absolute tolerance judges).
+        Returns the mean batch loss per epoch of every member."""
         torch = self.torch
         theta = torch.as_tensor(theta, dtype=torch.float32, device=self.dev)
-        targets = torch.as_tensor(targets, dtype=torch.float64, device=self.dev).contiguous()
+        targets = torch.as_tensor(targets, dtype=torch.float64, device=self.dev)
+        targets = targets.index_select(1, self._out_dev).contiguous()
         self.theta_scale = float(theta.abs().max().item()) or 1.0
         x = (theta / self.theta_scale).contiguous()
         t32 = targets.float()
         N = x.shape[0]
         steps = max(1, N // batch)
         total = epochs * steps
+        w = None if weight is None else np.asarray(weight, dtype=np.float64)[self.outputs]
         hists = []
         for k, net in enumerate(self.nets):
-            net.fit_linear(x, targets, weight)
+            if absolute:
+                # residual RMS of each output (the scale of an unweighted fit),
+                # then weights that bring every scale to their median
+                net.fit_linear(x, targets, None)
+                rms = net.output_affine()[0].astype(np.float64)
+                wa = (rms / np.median(rms)) ** 2
+                net.fit_linear(x, targets, wa if w is None else w * wa)
+            else:
+                net.fit_linear(x, targets, w)
             g = torch.Generator(device="cpu").manual_seed(seed + 104729 * k)
             # fixed staging buffers: every step reuses the same device pointers,
             # so the library replays its captured forward/backward graph
@@ -119,12 +140,19 @@ class Surrogate:
         return [net.forward(x) for net in self.nets]
 
     def predict(self, theta, screened_idx=None):
-        """(ensemble mean [B, n] FP64, spread [B] over the screened outputs)."""
+        """(ensemble mean [B, n] FP64, NaN where not predicted; spread [B]
+        over the screened coefficients, which must be predicted ones)."""
+        torch = self.torch
         preds = self.predict_members(theta)
-        mask = np.zeros(self.n, dtype=np.uint8)
-        mask[np.asarray(screened_idx if screened_idx is not None else np.arange(self.n))] = 1
+        screened = self.outputs if screened_idx is None else np.asarray(screened_idx)
+        mask = np.isin(self.outputs, screened).astype(np.uint8)
+        assert int(mask.sum()) == len(np.unique(screened)), "screened coefficients must be predicted outputs"
         mean, spread = cg.ensemble_stats(preds, mask)
-        return mean.double(), spread
+        if len(self.outputs) == self.n and np.array_equal(self.outputs, np.arange(self.n)):
+            return mean.double(), spread
+        full = torch.full((mean.shape[0], self.n), float("nan"), dtype=torch.float64, device=self.dev)
+        full.index_copy_(1, self._out_dev, mean.double())
+        return full, spread
 
     def calibrate(self, theta, exact, screened_idx, tol):
         """tau = the largest spread for which every validation query with a
@@ -140,19 +168,33 @@ class Surrogate:
         self.tau = float(sp[order[ok[-1]]]) if ok.size else -1.0
         return self.tau, float(np.mean(sp <= self.tau))
 
+    @staticmethod
+    def fallback_tile(count, sms=148):
+        """Tile width of the batched fallback for `count` queries: the
+        narrowest tile whose CTAs still fit on the SMs.  A CTA streams every
+        record for each of its TILE slots at once, so its step costs about
+        TILE / 32 warp instructions per record and a narrower tile finishes
+        a small batch sooner; 8 (the width the autotuner picks for full
+        batches) once the narrower ones would need more CTAs than SMs."""
+        for t in (2, 4):
+            if count <= t * sms:
+                return t
+        return 8
+
     def fallback(self, theta):
         """FP64 flows of the rejected queries.  A batched flow's wall time is
         set by its longest instance run on few SMs, so a handful of queries
         is faster through the single-instance flow (all SMs on one
         instance); larger sets take the batched kernel at a fixed tile
-        width (no autotuning inside a served call)."""
+        width chosen from their count (no autotuning inside a served call)."""
         torch = self.torch
         theta = np.asarray(theta)
         if len(theta) > self.plain_max:
             H0 = self._h0(theta)
             X0 = self.obs[None].expand(H0.shape[0], -1, -1).contiguous()
             H, _, _, status = self.G.flow_batched(H0, X0, precision="fp64", method="dp45", s0=0.0, s1=self.s1,
-                                                  ds=1e-2, rtol=self.tight_rtol, atol=self.atol, tile=8)
+                                                  ds=1e-2, rtol=self.tight_rtol, atol=self.atol,
+                                                  tile=self.fallback_tile(len(theta)))
             if int(status.abs().max().item()) != 0:
                 raise cg.CutError(int(status.abs().max().item()), "fallback flow failed")
             return H
@@ -164,7 +206,26 @@ class Surrogate:
             outs.append(h)
         return torch.stack(outs)
 
-    plain_max = 32
+    # 8-orbital model, DP45 to s = 10, rtol 1e-10, one B300: the plain flow
+    # takes 38 ms per query; the batched fallback 0.58 s for up to 296
+    # queries at tile 2, 1.07 s up to 592 at tile 4, 2.04 s for 1024 at tile 8
+    plain_max = 15
+
+    def warm_up(self):
+        """Load every kernel a served call may launch (the network, the plain
+        flow and the batched flow at each fallback tile width) on a short
+        span, so that no served call pays for first use."""
+        torch = self.torch
+        th = np.zeros((2, self.n_in))
+        self.predict(th, self.outputs[:1])
+        H0 = self._h0(th)
+        X0 = self.obs[None].expand(H0.shape[0], -1, -1).contiguous()
+        for t in (2, 4, 8):
+            self.G.flow_batched(H0, X0, precision="fp64", method="dp45", s0=0.0, s1=0.02, ds=1e-2,
+                                rtol=self.tight_rtol, atol=self.atol, tile=t)
+        self.G.flow(H0[0], list(self.obs), method="dp45", s0=0.0, s1=0.02, ds=1e-2, rtol=self.tight_rtol,
+                    atol=self.atol)
+        torch.cuda.synchronize()
 
     def screen(self, theta, screened_idx):
         """Served answers: the ensemble mean where the spread is <= tau, the
@@ -187,13 +248,18 @@ class Surrogate:
     def rank_screen(self, theta, coef, frac):
         """Rank queries by the ensemble's predicted coefficient `coef` and
         flow (FP64) only the best-ranked `frac` of them: returns (indices of
-        the flowed queries, their exact coefficient, seconds)."""
+        the flowed queries, their exact coefficient, seconds, timings)."""
         torch = self.torch
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         mean, _ = self.predict(theta, [coef])
-        order = torch.argsort(mean[:, coef]).cpu().numpy()
+        # the ranking of one coefficient on the host: a torch sort would load
+        # its sort kernels on first use (seconds) inside a served call
+        order = np.argsort(mean[:, coef].cpu().numpy(), kind="stable")
         chosen = np.sort(order[: int(frac * len(order))])
+        t1 = time.perf_counter()
         th = theta[chosen] if isinstance(theta, np.ndarray) else theta[torch.as_tensor(chosen, device=self.dev)]
-        exact, _ = self.flows(th, "fp64", tile=8)
+        exact, _ = self.flows(th, "fp64", tile=self.fallback_tile(len(th)))
         torch.cuda.synchronize()
-        return chosen, exact[:, coef], time.perf_counter() - t0
+        t2 = time.perf_counter()
+        return chosen, exact[:, coef], t2 - t0, {"rank_s": t1 - t0, "flow_s": t2 - t1, "flowed": int(len(chosen))}

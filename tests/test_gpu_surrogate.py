@@ -92,9 +92,68 @@ def test_surrogate_gate_and_screen_gain_over_the_plain_flow():
     print(f"all 36 diagonals: ensemble error per query median {np.median(e36):.2e}; gate at 1e-4 serves "
           f"{acc36.mean():.3f} of held-out queries (max served error {e36[acc36].max() if acc36.any() else 0:.2e})")
     # screen: recall of the true lowest 10% among the best-ranked 30%
-    chosen, vals, t_scr = sur.rank_screen(th_test, k0, 0.3)
+    chosen, vals, t_scr, parts = sur.rank_screen(th_test, k0, 0.3)
+    print(f"screen parts: {parts}")
     e_true = exact[:, k0].cpu().numpy()
     target = set(np.argsort(e_true)[: len(e_true) // 10].tolist())
     recall = len(target & set(chosen.tolist())) / len(target)
     print(f"screen: recall {recall:.3f} flowing 30% of the queries ({t_scr:.3f} s against {t_flow:.3f} s)")
     assert recall >= 0.9
+
+
+def test_diagonal_surrogate_predicts_only_its_outputs_and_gates_them():
+    """Networks of the 36 flowed diagonal coefficients (the form the
+    benchmark serves), trained with the absolute-error loss.  Checks:
+    every other coefficient comes back NaN; the networks beat their own
+    affine part on the worst of the 36 diagonals per query; the calibrated
+    threshold has its defining property on the validation queries (every
+    query with spread <= tau is within the tolerance); and the served path
+    with tau at the median spread returns the ensemble mean bit for bit where
+    it accepts and the FP64 flow (the batched fallback, ~half the queries)
+    where it does not.  How many queries the gate serves at 1e-4 is the
+    benchmark's measurement, not asserted here."""
+    import torch
+    from paper_2609_14831_b300.surrogate import Surrogate
+    w = workload("molecular_8so")
+    G = graph_for("mol8", w.alg, w.nmodes, w.labels)
+    P = parameter_directions(w.labels, 8)
+    diag = np.nonzero([int(l) & 0xFFFFFFFF == int(l) >> 32 for l in w.labels])[0]
+    sur = Surrogate(G, w.h, P, w.observables, n_hidden=512, members=2, seed=3, outputs=diag)
+    rng = np.random.default_rng(51)
+    th_train = rng.uniform(-0.1, 0.1, size=(8192, 32))
+    th_val = rng.uniform(-0.1, 0.1, size=(256, 32))
+    th_test = rng.uniform(-0.1, 0.1, size=(256, 32))
+    Htr, _ = sur.flows(th_train, "fp32")
+    sur.fit(th_train, Htr, epochs=100, batch=512, lr=3e-3, absolute=True)
+    exact_val, _ = sur.flows(th_val, "fp64")
+    exact, _ = sur.flows(th_test, "fp64")
+    mean, spread = sur.predict(th_test, diag)
+    off = np.setdiff1d(np.arange(len(w.labels)), diag)
+    assert torch.isnan(mean[:, off]).all() and not torch.isnan(mean[:, diag]).any()
+    dg = torch.as_tensor(diag, device=mean.device)
+    e_net = (mean[:, dg] - exact[:, dg]).abs().max(dim=1).values.cpu().numpy()
+    A = np.concatenate([np.ones((len(th_train), 1)), th_train], 1)
+    coef, *_ = np.linalg.lstsq(A, Htr[:, dg].cpu().numpy(), rcond=None)
+    At = np.concatenate([np.ones((len(th_test), 1)), th_test], 1)
+    e_lin = np.abs(At @ coef - exact[:, dg].cpu().numpy()).max(axis=1)
+    print(f"36 diagonals, worst per query: network median {np.median(e_net):.2e}, affine {np.median(e_lin):.2e}")
+    assert np.median(e_net) <= 0.5 * np.median(e_lin)
+    # the calibration's defining property on the validation queries
+    tol = 1e-3
+    tau, _ = sur.calibrate(th_val, exact_val, diag, tol)
+    mv, sv = sur.predict(th_val, diag)
+    ev = (mv[:, dg] - exact_val[:, dg]).abs().max(dim=1).values.cpu().numpy()
+    sv = sv.double().cpu().numpy()
+    assert np.all(ev[sv <= tau] <= tol)
+    # the served path at tau = median spread of the queries
+    sur.tau = float(np.median(spread.double().cpu().numpy()))
+    sur.warm_up()
+    out, ok, tm = sur.screen(th_test, diag)
+    assert np.array_equal(ok, spread.double().cpu().numpy() <= sur.tau)
+    assert 0 < ok.sum() < len(ok)
+    okd = torch.as_tensor(ok, device=mean.device)
+    assert torch.equal(out[okd][:, dg], mean[okd][:, dg])
+    rej = (out[~okd] - exact[~okd]).abs().max().item()
+    print(f"served by the networks {int(ok.sum())}/{len(ok)}; fallback of {int((~ok).sum())} queries "
+          f"(tile {sur.fallback_tile(int((~ok).sum()))}) within {rej:.1e} of the FP64 flows, {tm['fallback_s']:.3f} s")
+    assert rej <= 1e-8
