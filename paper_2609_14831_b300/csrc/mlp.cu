@@ -387,13 +387,14 @@ static int num_sms() {
 static cut_status gemm(const bf16 *A, const bf16 *B, int M, int N, int K, tc::Epi ep, cudaStream_t s,
                        int splits = 1, bool gelu = false) {
     if (M % 128 || N % 64 || splits < 1 || K % (64 * splits)) return set_error(CUT_ERR_INVALID_ARG, "gemm: shape not padded");
+    if (M / 128 > 65535) return set_error(CUT_ERR_INVALID_ARG, "gemm: more than 65535 row tiles (batch above 8,388,480)");
     CUtensorMap ma, mb;
     const int bn = (N % 128 == 0) ? 128 : 64;
     cut_status st = make_map(&ma, A, M, K, 128);
     if (st != CUT_OK) return st;
     st = make_map(&mb, B, N, K, bn);
     if (st != CUT_OK) return st;
-    dim3 grid(M / 128, N / bn, splits);
+    dim3 grid(N / bn, M / 128, splits);
     const int act = ep.dgelu_z ? tc::kGeluGrad : (gelu ? tc::kGelu : tc::kLinear);
     auto launch = [&](auto kern, size_t sm) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -550,6 +551,13 @@ static cut_status forward(cut_mlp *m, int batch, const float *x, cudaStream_t s,
             e.ld_bf16 = Ly.out_p;
             e.out_t = m->ht[l];
             e.ld_t = Mp;
+            if (y_out) {
+                // inference: the pre-activations and the transposed
+                // activations serve only the backward pass, which runs its
+                // own forward pass
+                e.out_f32 = nullptr;
+                e.out_t = nullptr;
+            }
         } else if (y_out) {
             // inference: valid region only, with the output affine and skip
             e.M = batch;

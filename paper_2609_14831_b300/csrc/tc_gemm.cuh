@@ -158,7 +158,9 @@ __global__ void __launch_bounds__(kThreads, ST <= STAGES ? 2 : 1)
     __shared__ volatile int failed;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    // column tiles fastest: the CTAs that share a row tile of A run together,
+    // so a large A is read from DRAM once and B stays in L2
+    const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
     const int KT = K / BK;                 // K columns per split; split z starts at z K
     const int kbase = blockIdx.z * K;
 
