@@ -476,7 +476,8 @@ def run_surrogate(args):
     n = len(w.labels)
     diag = np.nonzero([int(l) & 0xFFFFFFFF == int(l) >> 32 for l in w.labels])[0]
     k0 = int(np.nonzero(w.labels == np.uint64(make_label(1, 1)))[0][0])
-    sur = Surrogate(G, w.h, P, w.observables, n_hidden=args.surrogate_hidden, members=2, seed=0, outputs=diag)
+    sur = Surrogate(G, w.h, P, w.observables, n_hidden=args.surrogate_hidden, members=args.surrogate_members, seed=0,
+                    outputs=diag)
     rng = np.random.default_rng(4)
     n_train, n_test = args.surrogate_train, 1024
     th_tr = rng.uniform(-0.1, 0.1, size=(n_train, 32))
@@ -572,7 +573,8 @@ def run_surrogate(args):
                                   "frac_of_measured_bf16": fwd_flop / (fwd_ms * 1e-3) / 1e12 / _peak_bf16()},
             "network": {"widths": [32, H_, H_, n_o], "outputs": "the 36 flowed diagonal coefficients",
                         "epochs": args.surrogate_epochs, "loss": "absolute errors (outputs scaled alike)"},
-            "config": {"workload": "molecular_8so surrogate, 32 parameters, 2 networks", "gate": 1e-4}}
+            "config": {"workload": f"molecular_8so surrogate, 32 parameters, {args.surrogate_members} networks",
+                       "gate": 1e-4}}
     print(json.dumps(line), flush=True)
 
 
@@ -614,6 +616,7 @@ def main():
     ap.add_argument("--surrogate-train", type=int, default=400000)
     ap.add_argument("--surrogate-epochs", type=int, default=400)
     ap.add_argument("--surrogate-hidden", type=int, default=2048)
+    ap.add_argument("--surrogate-members", type=int, default=2)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
