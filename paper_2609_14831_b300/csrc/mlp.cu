@@ -103,22 +103,24 @@ __global__ void __launch_bounds__(256) mse_grad(const float *__restrict__ Y, int
     if (tid == 0 && loss) atomicAdd(loss, red[0] * inv);
 }
 
-// db[c] = sum_m dz[m][c] (valid rows): 32 columns per block, 8 row groups
+// db[c] = sum_m dz[m][c] (valid rows): 32 columns per block, 32 row groups
+// (a thread adds every 32nd row, its loads independent of one another)
 // summed in a fixed order (coalesced rows, deterministic result)
-__global__ void __launch_bounds__(256) col_sum(const float *__restrict__ dz, int ld, int rows, int cols,
-                                               float *__restrict__ db) {
-    __shared__ float part[8][33];
+constexpr int kColSumGroups = 32;
+__global__ void __launch_bounds__(32 * kColSumGroups) col_sum(const float *__restrict__ dz, int ld, int rows, int cols,
+                                                             float *__restrict__ db) {
+    __shared__ float part[kColSumGroups][33];
     const int tx = threadIdx.x, ty = threadIdx.y, c = blockIdx.x * 32 + tx;
     float s = 0.0f;
     if (c < cols) {
-#pragma unroll 4
-        for (int m = ty; m < rows; m += 8) s += dz[(int64_t)m * ld + c];
+#pragma unroll 8
+        for (int m = ty; m < rows; m += kColSumGroups) s += dz[(int64_t)m * ld + c];
     }
     part[ty][tx] = s;
     __syncthreads();
     if (ty == 0 && c < cols) {
         float t = 0.0f;
-        for (int g = 0; g < 8; g++) t += part[g][tx];
+        for (int g = 0; g < kColSumGroups; g++) t += part[g][tx];
         db[c] = t;
     }
 }
@@ -132,12 +134,13 @@ __global__ void sum_splits(const float *__restrict__ part, int splits, int64_t c
     }
 }
 
-// AdamW (Loshchilov & Hutter): decoupled weight decay; refreshes the BF16
-// copies W and W^T.  Parameters are [out][in] (bias: in = 1, no transpose).
-// Every parameter segment of the network in one launch.
+// AdamW (Loshchilov & Hutter): decoupled weight decay.  Parameters are
+// [out][in] (bias: in = 1).  adamw_all updates a list of segments element by
+// element (the biases); adamw_tiles the weight matrices, refreshing their
+// BF16 copies W and W^T.
 struct AdamSeg {
     float *w, *g, *m, *v;
-    bf16 *wb, *wt;      // BF16 copies (weights only)
+    bf16 *wb, *wt;      // BF16 copies, row-major and transposed (weights only)
     int64_t count, start;
     int in_p, out_p;
     float wd;
@@ -147,6 +150,49 @@ struct AdamSegs {
     int n;
     int64_t total;
 };
+
+// The three weight matrices W [out_p][in_p], walked in 32 x 32 tiles.
+struct AdamTiles {
+    AdamSeg s[3];
+    int tiles_x[3];             // tiles per row of tiles (in_p / 32)
+    int64_t tile_start[4];      // first tile of each matrix; tile_start[3] = all tiles
+};
+
+// The AdamW update of a weight tile (adamw_all's arithmetic), its BF16 copy
+// row-major and, through shared memory, transposed W^T [in_p][out_p]: reads
+// and writes of both copies coalesced.
+__global__ void __launch_bounds__(256) adamw_tiles(AdamTiles a, float lr, float b1, float b2, float eps, float bc1,
+                                                   float bc2) {
+    __shared__ bf16 tile[32][34];
+    for (int64_t t = blockIdx.x; t < a.tile_start[3]; t += gridDim.x) {
+        const int k = t >= a.tile_start[2] ? 2 : (t >= a.tile_start[1] ? 1 : 0);
+        const AdamSeg &S = a.s[k];
+        const int64_t lt = t - a.tile_start[k];
+        const int c0 = (int)(lt % a.tiles_x[k]) * 32, r0 = (int)(lt / a.tiles_x[k]) * 32;
+        for (int j = threadIdx.y; j < 32; j += 8) {
+            const int r = r0 + j, c = c0 + threadIdx.x;
+            if (r >= S.out_p || c >= S.in_p) continue;
+            const int64_t e = (int64_t)r * S.in_p + c;
+            const float gr = S.g[e];
+            const float mm = b1 * S.m[e] + (1.0f - b1) * gr;
+            const float vv = b2 * S.v[e] + (1.0f - b2) * gr * gr;
+            S.m[e] = mm;
+            S.v[e] = vv;
+            float x = S.w[e];
+            x -= lr * ((mm / bc1) / (sqrtf(vv / bc2) + eps) + S.wd * x);
+            S.w[e] = x;
+            const bf16 bv = __float2bfloat16(x);
+            S.wb[e] = bv;
+            tile[j][threadIdx.x] = bv;
+        }
+        __syncthreads();
+        for (int j = threadIdx.y; j < 32; j += 8) {
+            const int c = c0 + j, r = r0 + threadIdx.x;
+            if (r < S.out_p && c < S.in_p) S.wt[(int64_t)c * S.out_p + r] = tile[threadIdx.x][j];
+        }
+        __syncthreads();
+    }
+}
 
 __global__ void adamw_all(AdamSegs segs, float lr, float b1, float b2, float eps, float bc1, float bc2) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < segs.total;
@@ -163,11 +209,6 @@ __global__ void adamw_all(AdamSegs segs, float lr, float b1, float b2, float eps
         float x = S.w[e];
         x -= lr * ((mm / bc1) / (sqrtf(vv / bc2) + eps) + S.wd * x);
         S.w[e] = x;
-        if (S.wb) {
-            const bf16 bv = __float2bfloat16(x);
-            S.wb[e] = bv;
-            S.wt[(e % S.in_p) * (int64_t)S.out_p + e / S.in_p] = bv;
-        }
     }
 }
 
@@ -840,7 +881,8 @@ static cut_status backward_body(cut_mlp *m, int batch, const float *x, const flo
         if (st != CUT_OK) return st;
         if (splits > 1)
             mlpk::sum_splits<<<grid_of(e.split_stride), 256, 0, s>>>(m->splitbuf, splits, e.split_stride, Ly.gw);
-        mlpk::col_sum<<<(Ly.out_p + 31) / 32, dim3(32, 8), 0, s>>>(dz32, Ly.out_p, batch, Ly.out_p, Ly.gb);
+        mlpk::col_sum<<<(Ly.out_p + 31) / 32, dim3(32, mlpk::kColSumGroups), 0, s>>>(dz32, Ly.out_p, batch, Ly.out_p,
+                                                                                   Ly.gb);
         if (l == 0) break;
         // dZ_{l-1} = (dZ_l W_l) * GELU'(Z_{l-1})
         Layer &Lp = L[l - 1];
@@ -915,20 +957,25 @@ cut_status cut_mlp_adamw_step(cut_mlp *m, float lr, float beta1, float beta2, fl
     m->t++;
     const float bc1 = 1.0f - (float)std::pow((double)beta1, (double)m->t);
     const float bc2 = 1.0f - (float)std::pow((double)beta2, (double)m->t);
+    // weights in tiles (with both BF16 copies), biases element by element
+    mlpk::AdamTiles tw;
+    memset(&tw, 0, sizeof(tw));
     mlpk::AdamSegs segs;
     memset(&segs, 0, sizeof(segs));
     int64_t start = 0;
     for (int l = 0; l < 3; l++) {
         Layer &Ly = m->L[l];
-        mlpk::AdamSeg &W = segs.s[segs.n++];
-        W = {Ly.w, Ly.gw, Ly.mw, Ly.vw, Ly.wb, Ly.wt, (int64_t)Ly.in_p * Ly.out_p, start, Ly.in_p, Ly.out_p,
-             weight_decay};
-        start += W.count;
+        tw.s[l] = {Ly.w, Ly.gw, Ly.mw, Ly.vw, Ly.wb, Ly.wt, (int64_t)Ly.in_p * Ly.out_p, 0, Ly.in_p, Ly.out_p,
+                   weight_decay};
+        tw.tiles_x[l] = (Ly.in_p + 31) / 32;
+        tw.tile_start[l + 1] = tw.tile_start[l] + (int64_t)tw.tiles_x[l] * ((Ly.out_p + 31) / 32);
         mlpk::AdamSeg &B = segs.s[segs.n++];
         B = {Ly.b, Ly.gb, Ly.mb, Ly.vb, nullptr, nullptr, (int64_t)Ly.out_p, start, 1, 1, 0.0f};
         start += B.count;
     }
     segs.total = start;
+    mlpk::adamw_tiles<<<(int)std::min<int64_t>(tw.tile_start[3], 148 * 8), dim3(32, 8), 0, s>>>(
+        tw, lr, beta1, beta2, eps, bc1, bc2);
     mlpk::adamw_all<<<grid_of(start), 256, 0, s>>>(segs, lr, beta1, beta2, eps, bc1, bc2);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(CUT_ERR_CUDA, std::string("cut_mlp_adamw_step: ") + cudaGetErrorString(e));
