@@ -9,6 +9,7 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <utility>
 #include <vector>
 
 #include "alloc.h"
@@ -38,6 +39,27 @@ cut_status set_ok() { return CUT_OK; }
                              std::string(#expr) + ": " + cudaGetErrorString(_e));               \
         }                                                                                       \
     } while (0)
+
+// Kernel launch with programmatic stream serialization: the kernel's blocks
+// may be scheduled while its predecessor on the stream is finishing; every
+// kernel of the library first waits on the device for that predecessor
+// (k::pdl_enter), so only launch latency is overlapped.
+template <typename... P, typename... A>
+static void pdl_launch(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A &&...args) {
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at;
+    memset(&at, 0, sizeof(at));
+    at.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
 
 static void *current_context();
 
@@ -241,9 +263,9 @@ static void comm_launch(const DevCSR &c, const k::Weights &w, const double *xi, 
                         cudaStream_t s, const int *done) {
     const int grid = grid_for_groups(c.rows, L);
     if (w.uniform)
-        k::comm_stage<M, true, L><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, xi, ops, c.rows, done);
+        pdl_launch(k::comm_stage<M, true, L>, grid, k::kBlock, 0, s, c.rp, c.rec, w, xi, ops, c.rows, done);
     else
-        k::comm_stage<M, false, L><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, xi, ops, c.rows, done);
+        pdl_launch(k::comm_stage<M, false, L>, grid, k::kBlock, 0, s, c.rp, c.rec, w, xi, ops, c.rows, done);
 }
 
 template <int M, int L>
@@ -251,9 +273,9 @@ static void comm_launch_x4(const DevCSR &c, const k::Weights &w, const double *x
                            const double *X4, cudaStream_t s, const int *done) {
     const int grid = grid_for_groups(c.rows, L);
     if (w.uniform)
-        k::comm_stage_x4<M, true, L><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, xi, X4, ops, c.rows, done);
+        pdl_launch(k::comm_stage_x4<M, true, L>, grid, k::kBlock, 0, s, c.rp, c.rec, w, xi, X4, ops, c.rows, done);
     else
-        k::comm_stage_x4<M, false, L><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, xi, X4, ops, c.rows, done);
+        pdl_launch(k::comm_stage_x4<M, false, L>, grid, k::kBlock, 0, s, c.rp, c.rec, w, xi, X4, ops, c.rows, done);
 }
 
 // X4: optional scratch of n x 64 bytes on a 32-byte boundary.  With it, and
@@ -280,7 +302,7 @@ static void launch_comm(const cut_graph *g, const double *xi, int nops, const do
     case M: {                                                                                         \
         k::Ops<M> ops;                                                                                \
         for (int t = 0; t < M; t++) { ops.x[t] = xs[t]; ops.dx[t] = piece + t * c.pieces; }            \
-        if (!prepacked) k::pack_x4<M><<<grid_for_len(n), 256, 0, s>>>(ops, n, X4, done);               \
+        if (!prepacked) pdl_launch(k::pack_x4<M>, grid_for_len(n), 256, 0, s, ops, n, X4, done);               \
         comm_launch_x4<M, 8>(pc, w, xi, ops, X4, s, done);                                             \
     } break;
             CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
@@ -288,7 +310,7 @@ static void launch_comm(const cut_graph *g, const double *xi, int nops, const do
         }
         k::Ops<8> red;
         for (int t = 0; t < nops; t++) { red.x[t] = piece + t * c.pieces; red.dx[t] = dxs[t]; }
-        k::piece_reduce<<<grid_for_len(c.rows * nops), 256, 0, s>>>(c.pvr, c.rows, red, nops, nullptr);
+        pdl_launch(k::piece_reduce, grid_for_len(c.rows * nops), 256, 0, s, c.pvr, c.rows, red, nops, nullptr);
         return;
     }
     if (X4 && nops <= 8) {
@@ -300,7 +322,7 @@ static void launch_comm(const cut_graph *g, const double *xi, int nops, const do
     case M: {                                                                                         \
         k::Ops<M> ops;                                                                                \
         for (int t = 0; t < M; t++) { ops.x[t] = xs[o0 + t]; ops.dx[t] = dxs[o0 + t]; }                 \
-        if (!prepacked) k::pack_x4<M><<<grid_for_len(n), 256, 0, s>>>(ops, n, X4, done);               \
+        if (!prepacked) pdl_launch(k::pack_x4<M>, grid_for_len(n), 256, 0, s, ops, n, X4, done);               \
         if (lanes == 8) comm_launch_x4<M, 8>(c, w, xi, ops, X4, s, done);                              \
         else comm_launch_x4<M, 32>(c, w, xi, ops, X4, s, done);                                        \
     } break;
@@ -332,9 +354,9 @@ static void gen_launch(const DevCSR &c, const k::Weights &w, const double *h, do
                        const int *done) {
     const int grid = grid_for_groups(c.rows, L);
     if (w.uniform)
-        k::gen_stage<true, L><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, h, xi, c.rows, done);
+        pdl_launch(k::gen_stage<true, L>, grid, k::kBlock, 0, s, c.rp, c.rec, w, h, xi, c.rows, done);
     else
-        k::gen_stage<false, L><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, h, xi, c.rows, done);
+        pdl_launch(k::gen_stage<false, L>, grid, k::kBlock, 0, s, c.rp, c.rec, w, h, xi, c.rows, done);
 }
 
 static void launch_gen(const cut_graph *g, const double *h, double *xi, cudaStream_t s, const int *done) {
@@ -363,10 +385,10 @@ static bool launch_gen_pack(const cut_graph *g, const double *const *xs, int nop
     case M: {                                                                                         \
         k::Ops<M> ops;                                                                                \
         for (int t = 0; t < M; t++) { ops.x[t] = xs[t]; ops.dx[t] = nullptr; }                        \
-        if (w.uniform && gl == 4) k::gen_pack<M, true, 4><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, xi, c.rows, ops, n, X4, done); \
-        else if (w.uniform) k::gen_pack<M, true, 8><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, xi, c.rows, ops, n, X4, done); \
-        else if (gl == 4) k::gen_pack<M, false, 4><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, xi, c.rows, ops, n, X4, done); \
-        else k::gen_pack<M, false, 8><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, xi, c.rows, ops, n, X4, done); \
+        if (w.uniform && gl == 4) pdl_launch(k::gen_pack<M, true, 4>, grid, k::kBlock, 0, s, c.rp, c.rec, w, xi, c.rows, ops, n, X4, done); \
+        else if (w.uniform) pdl_launch(k::gen_pack<M, true, 8>, grid, k::kBlock, 0, s, c.rp, c.rec, w, xi, c.rows, ops, n, X4, done); \
+        else if (gl == 4) pdl_launch(k::gen_pack<M, false, 4>, grid, k::kBlock, 0, s, c.rp, c.rec, w, xi, c.rows, ops, n, X4, done); \
+        else pdl_launch(k::gen_pack<M, false, 8>, grid, k::kBlock, 0, s, c.rp, c.rec, w, xi, c.rows, ops, n, X4, done); \
     } break;
         CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
 #undef CASE
@@ -391,10 +413,10 @@ static void launch_comm_df(const cut_graph *g, const double *xi, float2 *xi2, fl
     // 8 lanes per piece when few long rows are cut into pieces
     const int lanes = pieces ? 8 : comm_lanes(c.lane_rows);
     const int grid = grid_for_groups(c.rows, lanes);
-    if (ng > 0) k::split_pairs<<<grid_for_len(ng), 256, 0, s>>>(xi, ng, xi2, 1, 0, done);
+    if (ng > 0) pdl_launch(k::split_pairs, grid_for_len(ng), 256, 0, s, xi, ng, xi2, 1, 0, done);
     for (int o0 = 0; o0 < nops; o0 += 3) {
         const int m = std::min(3, nops - o0);
-        for (int t = 0; t < m; t++) k::split_pairs<<<grid_for_len(n), 256, 0, s>>>(xs[o0 + t], n, X2, 4, t, done);
+        for (int t = 0; t < m; t++) pdl_launch(k::split_pairs, grid_for_len(n), 256, 0, s, xs[o0 + t], n, X2, 4, t, done);
         const float4 *X4 = reinterpret_cast<const float4 *>(X2);
         switch (m) {
 #define CASE(M)                                                                                                   \
@@ -405,9 +427,9 @@ static void launch_comm_df(const cut_graph *g, const double *xi, float2 *xi2, fl
             ops.dx[t] = pieces ? piece + t * c.rows : dxs[o0 + t];                                                \
         }                                                                                                         \
         if (lanes == 8)                                                                                           \
-            k::comm_stage_df<M, 8><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, xi2, X4, ops, c.rows, done);        \
+            pdl_launch(k::comm_stage_df<M, 8>, grid, k::kBlock, 0, s, c.rp, c.rec, w, xi2, X4, ops, c.rows, done);        \
         else                                                                                                      \
-            k::comm_stage_df<M, 32><<<grid, k::kBlock, 0, s>>>(c.rp, c.rec, w, xi2, X4, ops, c.rows, done);       \
+            pdl_launch(k::comm_stage_df<M, 32>, grid, k::kBlock, 0, s, c.rp, c.rec, w, xi2, X4, ops, c.rows, done);       \
     } break;
             CASE(1) CASE(2) CASE(3)
 #undef CASE
@@ -415,7 +437,7 @@ static void launch_comm_df(const cut_graph *g, const double *xi, float2 *xi2, fl
         if (pieces) {
             k::Ops<8> red;
             for (int t = 0; t < m; t++) { red.x[t] = piece + t * c.rows; red.dx[t] = dxs[o0 + t]; }
-            k::piece_reduce<<<grid_for_len(rows_c.rows * m), 256, 0, s>>>(rows_c.pvr, rows_c.rows, red, m, nullptr);
+            pdl_launch(k::piece_reduce, grid_for_len(rows_c.rows * m), 256, 0, s, rows_c.pvr, rows_c.rows, red, m, nullptr);
         }
     }
 }
@@ -704,7 +726,7 @@ extern "C" cut_status cut_assemble(int n_src, int64_t n, const double *X, int n_
     if (smem > 48 * 1024)
         CUDA_TRY(cudaFuncSetAttribute(k::assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int64_t blocks = (n + 31) / 32;
-    k::assemble<<<(unsigned)blocks, 256, smem, s>>>(X, n_src, n, C, n_out, out);
+    pdl_launch(k::assemble, (unsigned)blocks, 256, smem, s, X, n_src, n, C, n_out, out);
     CUDA_TRY(cudaGetLastError());
     return set_ok();
 }
@@ -725,7 +747,7 @@ extern "C" cut_status cut_rhs_jvp(const cut_graph *g, const double *h, int n_obs
     const k::Weights w = weights_of(g);
     launch_gen(g, h, xi, s, nullptr);
     const DevCSR &c0 = g->st[0], &c1 = g->st[1];
-    k::gen_jvp<<<grid_for_rows(c0.rows), k::kBlock, 0, s>>>(c0.rp, c0.rec, w, h, dh, dxi, c0.rows);
+    pdl_launch(k::gen_jvp, grid_for_rows(c0.rows), k::kBlock, 0, s, c0.rp, c0.rec, w, h, dh, dxi, c0.rows);
     const int nops = n_obs + 1;
     const double *xs[64], *dxs[64];
     double *outs[64];
@@ -740,7 +762,7 @@ extern "C" cut_status cut_rhs_jvp(const cut_graph *g, const double *h, int n_obs
     case M: {                                                                                       \
         k::TanOps<M> t;                                                                             \
         for (int u = 0; u < M; u++) { t.x[u] = xs[o0 + u]; t.dx[u] = dxs[o0 + u]; t.out[u] = outs[o0 + u]; } \
-        k::comm_jvp<M><<<grid_for_rows(c1.rows), k::kBlock, 0, s>>>(c1.rp, c1.rec, w, xi, dxi, t, c1.rows); \
+        pdl_launch(k::comm_jvp<M>, grid_for_rows(c1.rows), k::kBlock, 0, s, c1.rp, c1.rec, w, xi, dxi, t, c1.rows); \
     } break;
             CASE(1) CASE(2) CASE(3) CASE(4)
 #undef CASE
@@ -922,7 +944,7 @@ static void pack_operands(const cut_graph *g, const double *Y, int nops, double 
     case M: {                                                                         \
         k::Ops<M> ops;                                                                \
         for (int t = 0; t < M; t++) { ops.x[t] = Y + t * n; ops.dx[t] = nullptr; }      \
-        k::pack_x4<M><<<grid_for_len(n), 256, 0, s>>>(ops, n, X4, nullptr);           \
+        pdl_launch(k::pack_x4<M>, grid_for_len(n), 256, 0, s, ops, n, X4, nullptr);           \
     } break;
         CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
 #undef CASE
@@ -959,7 +981,7 @@ static void stacked_vjp(const cut_graph *g, const double *Y, const double *W, do
         {
             k::Ops<8> red;
             for (int o = 0; o < nops; o++) { red.x[o] = piece + o * ptx; red.dx[o] = o == 0 ? xbar0 : YB + o * n; }
-            k::piece_reduce<<<grid_for_len(n * nops), 256, 0, s>>>(g->tx.vr, n, red, nops, nullptr);
+            pdl_launch(k::piece_reduce, grid_for_len(n * nops), 256, 0, s, g->tx.vr, n, red, nops, nullptr);
         }
         pack_operands(g, Y, nops, X4, s);
         const k::Weights w = weights_of(g);
@@ -970,11 +992,11 @@ static void stacked_vjp(const cut_graph *g, const double *Y, const double *W, do
 #define CASE(M)                                                                                                 \
     case M:                                                                                                     \
         if (w.uniform) {                                                                                        \
-            if (lx == 8) k::commT_xi_x4<M, true, 8><<<grid_for_groups(cx.rows, 8), k::kBlock, 0, s>>>(cx.rp, cx.rec, w, W4, X4, xpiece, cx.rows); \
-            else k::commT_xi_x4<M, true, 32><<<grid_for_groups(cx.rows, 32), k::kBlock, 0, s>>>(cx.rp, cx.rec, w, W4, X4, xpiece, cx.rows); \
+            if (lx == 8) pdl_launch(k::commT_xi_x4<M, true, 8>, grid_for_groups(cx.rows, 8), k::kBlock, 0, s, cx.rp, cx.rec, w, W4, X4, xpiece, cx.rows); \
+            else pdl_launch(k::commT_xi_x4<M, true, 32>, grid_for_groups(cx.rows, 32), k::kBlock, 0, s, cx.rp, cx.rec, w, W4, X4, xpiece, cx.rows); \
         } else {                                                                                                \
-            if (lx == 8) k::commT_xi_x4<M, false, 8><<<grid_for_groups(cx.rows, 8), k::kBlock, 0, s>>>(cx.rp, cx.rec, w, W4, X4, xpiece, cx.rows); \
-            else k::commT_xi_x4<M, false, 32><<<grid_for_groups(cx.rows, 32), k::kBlock, 0, s>>>(cx.rp, cx.rec, w, W4, X4, xpiece, cx.rows); \
+            if (lx == 8) pdl_launch(k::commT_xi_x4<M, false, 8>, grid_for_groups(cx.rows, 8), k::kBlock, 0, s, cx.rp, cx.rec, w, W4, X4, xpiece, cx.rows); \
+            else pdl_launch(k::commT_xi_x4<M, false, 32>, grid_for_groups(cx.rows, 32), k::kBlock, 0, s, cx.rp, cx.rec, w, W4, X4, xpiece, cx.rows); \
         }                                                                                                       \
         break;
             CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
@@ -984,7 +1006,7 @@ static void stacked_vjp(const cut_graph *g, const double *Y, const double *W, do
             k::Ops<8> red;
             red.x[0] = xpiece;
             red.dx[0] = xib;
-            k::piece_reduce<<<grid_for_len(ng), 256, 0, s>>>(cx.vr, ng, red, 1, nullptr);
+            pdl_launch(k::piece_reduce, grid_for_len(ng), 256, 0, s, cx.vr, ng, red, 1, nullptr);
         }
         // the rows of the diagonal coordinates hold most of the generator
         // records (every generator record has one diagonal input) and are
@@ -993,14 +1015,14 @@ static void stacked_vjp(const cut_graph *g, const double *Y, const double *W, do
         // and one FMA, so a lane's chain of records is all latency
         (void)lh;
         if (w.uniform)
-            k::genT_lanes<true, 32><<<grid_for_groups(ch.rows, 32), k::kBlock, 0, s>>>(ch.rp, ch.rec, w, xib, Y, nullptr, hpiece, ch.rows);
+            pdl_launch(k::genT_lanes<true, 32>, grid_for_groups(ch.rows, 32), k::kBlock, 0, s, ch.rp, ch.rec, w, xib, Y, nullptr, hpiece, ch.rows);
         else
-            k::genT_lanes<false, 32><<<grid_for_groups(ch.rows, 32), k::kBlock, 0, s>>>(ch.rp, ch.rec, w, xib, Y, nullptr, hpiece, ch.rows);
+            pdl_launch(k::genT_lanes<false, 32>, grid_for_groups(ch.rows, 32), k::kBlock, 0, s, ch.rp, ch.rec, w, xib, Y, nullptr, hpiece, ch.rows);
         {
             k::Ops<8> red;
             red.x[0] = hpiece;
             red.dx[0] = YB;
-            k::piece_reduce<<<grid_for_len(n), 256, 0, s>>>(ch.vr, n, red, 1, xbar0);
+            pdl_launch(k::piece_reduce, grid_for_len(n), 256, 0, s, ch.vr, n, red, 1, xbar0);
         }
         return;
     }
@@ -1015,7 +1037,7 @@ static void stacked_vjp(const cut_graph *g, const double *Y, const double *W, do
     case M: {                                                                                \
         k::Ops<M> ops;                                                                       \
         for (int t = 0; t < M; t++) { ops.x[t] = W + (o0 + t) * n; ops.dx[t] = piece + t * ptx; } \
-        k::commT_x<M><<<grid_for_rows(ptx), k::kBlock, 0, s>>>(g->tx.rp, g->tx.rec, g->wtab, nc, xi, ops, ptx); \
+        pdl_launch(k::commT_x<M>, grid_for_rows(ptx), k::kBlock, 0, s, g->tx.rp, g->tx.rec, g->wtab, nc, xi, ops, ptx); \
     } break;
             CASE(1) CASE(2) CASE(3) CASE(4)
 #undef CASE
@@ -1025,7 +1047,7 @@ static void stacked_vjp(const cut_graph *g, const double *Y, const double *W, do
             red.x[t] = piece + t * ptx;
             red.dx[t] = (o0 + t == 0) ? xbar0 : YB + (o0 + t) * n;
         }
-        k::piece_reduce<<<grid_for_len(n * m), 256, 0, s>>>(g->tx.vr, n, red, m, nullptr);
+        pdl_launch(k::piece_reduce, grid_for_len(n * m), 256, 0, s, g->tx.vr, n, red, m, nullptr);
     }
     for (int o0 = 0; o0 < nops; o0 += 4) {
         int m = std::min(4, nops - o0);
@@ -1034,7 +1056,7 @@ static void stacked_vjp(const cut_graph *g, const double *Y, const double *W, do
     case M: {                                                                                \
         k::Pairs<M> pr;                                                                      \
         for (int t = 0; t < M; t++) { pr.x[t] = Y + (o0 + t) * n; pr.w[t] = W + (o0 + t) * n; } \
-        k::commT_xi<M><<<grid_for_rows(pxi), k::kBlock, 0, s>>>(g->txi.rp, g->txi.rec, g->wtab, nc, pr, piece, pxi, o0 > 0); \
+        pdl_launch(k::commT_xi<M>, grid_for_rows(pxi), k::kBlock, 0, s, g->txi.rp, g->txi.rec, g->wtab, nc, pr, piece, pxi, o0 > 0); \
     } break;
             CASE(1) CASE(2) CASE(3) CASE(4)
 #undef CASE
@@ -1044,14 +1066,14 @@ static void stacked_vjp(const cut_graph *g, const double *Y, const double *W, do
         k::Ops<8> red;
         red.x[0] = piece;
         red.dx[0] = xib;
-        k::piece_reduce<<<grid_for_len(ng), 256, 0, s>>>(g->txi.vr, ng, red, 1, nullptr);
+        pdl_launch(k::piece_reduce, grid_for_len(ng), 256, 0, s, g->txi.vr, ng, red, 1, nullptr);
     }
-    k::genT<<<grid_for_rows(pth), k::kBlock, 0, s>>>(g->th.rp, g->th.rec, g->wtab, nc, xib, Y, nullptr, piece, pth);
+    pdl_launch(k::genT, grid_for_rows(pth), k::kBlock, 0, s, g->th.rp, g->th.rec, g->wtab, nc, xib, Y, nullptr, piece, pth);
     {
         k::Ops<8> red;
         red.x[0] = piece;
         red.dx[0] = YB;
-        k::piece_reduce<<<grid_for_len(n), 256, 0, s>>>(g->th.vr, n, red, 1, xbar0);
+        pdl_launch(k::piece_reduce, grid_for_len(n), 256, 0, s, g->th.vr, n, red, 1, xbar0);
     }
 }
 
@@ -1142,7 +1164,7 @@ static void stage_input(const FlowWork &w, const double *A, int i, int64_t L, co
     cb.nk = 0;
     for (int j = 0; j < i; j++)
         if (A[j] != 0.0) { cb.K[cb.nk] = w.K[j]; cb.c[cb.nk] = A[j]; cb.nk++; }
-    k::rk_combine<<<grid_for_len(L), 256, 0, s>>>(cb, out, L, dsp, dsc, done);
+    pdl_launch(k::rk_combine, grid_for_len(L), 256, 0, s, cb, out, L, dsp, dsc, done);
 }
 
 // K_i = f(Y + ds sum_j A[j] K_j): the stage input, its packed operand
@@ -1186,10 +1208,10 @@ static void fused_stage(const cut_graph *g, FlowWork &w, const double *A, int i,
     const int grid = std::max(grid_for_len(n), grid_for_groups(c0.rows, gl));
     switch (nops * 4 + (wt.uniform ? 2 : 0) + (gl == 4 ? 1 : 0)) {
 #define CASE(M)                                                                                                 \
-    case M * 4 + 0: k::stage_gen<M, false, 8><<<grid, k::kBlock, 0, s>>>(si, n, X4, U_full, c0.rp, c0.rec, wt, w.xi, c0.rows, done); break; \
-    case M * 4 + 1: k::stage_gen<M, false, 4><<<grid, k::kBlock, 0, s>>>(si, n, X4, U_full, c0.rp, c0.rec, wt, w.xi, c0.rows, done); break; \
-    case M * 4 + 2: k::stage_gen<M, true, 8><<<grid, k::kBlock, 0, s>>>(si, n, X4, U_full, c0.rp, c0.rec, wt, w.xi, c0.rows, done); break; \
-    case M * 4 + 3: k::stage_gen<M, true, 4><<<grid, k::kBlock, 0, s>>>(si, n, X4, U_full, c0.rp, c0.rec, wt, w.xi, c0.rows, done); break;
+    case M * 4 + 0: pdl_launch(k::stage_gen<M, false, 8>, grid, k::kBlock, 0, s, si, n, X4, U_full, c0.rp, c0.rec, wt, w.xi, c0.rows, done); break; \
+    case M * 4 + 1: pdl_launch(k::stage_gen<M, false, 4>, grid, k::kBlock, 0, s, si, n, X4, U_full, c0.rp, c0.rec, wt, w.xi, c0.rows, done); break; \
+    case M * 4 + 2: pdl_launch(k::stage_gen<M, true, 8>, grid, k::kBlock, 0, s, si, n, X4, U_full, c0.rp, c0.rec, wt, w.xi, c0.rows, done); break; \
+    case M * 4 + 3: pdl_launch(k::stage_gen<M, true, 4>, grid, k::kBlock, 0, s, si, n, X4, U_full, c0.rp, c0.rec, wt, w.xi, c0.rows, done); break;
         CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
 #undef CASE
     }
@@ -1207,7 +1229,7 @@ static void rk4_step(const cut_graph *g, FlowWork &w, int nops, double ds, cudaS
     cb.base = w.Y;
     cb.nk = 4;
     for (int j = 0; j < 4; j++) { cb.K[j] = w.K[j]; cb.c[j] = RK4_B[j]; }
-    k::rk_combine<<<grid_for_len(L), 256, 0, s>>>(cb, w.Y, L, nullptr, ds, nullptr);
+    pdl_launch(k::rk_combine, grid_for_len(L), 256, 0, s, cb, w.Y, L, nullptr, ds, nullptr);
 }
 
 // One Dormand-Prince attempt under device control (w.K[0] holds f(Y)).
@@ -1221,10 +1243,10 @@ static void dp_attempt(const cut_graph *g, FlowWork &w, int nops, cudaStream_t s
     if (!replay) {
         k::ErrTerms et;
         for (int i = 0; i < 7; i++) { et.K[i] = w.K[i]; et.e[i] = DP_B[i] - DP_BS[i]; }
-        k::dp_error<<<grid_for_len(L), 256, 0, s>>>(et, w.Y, w.Y5, L, w.ctl);
+        pdl_launch(k::dp_error, grid_for_len(L), 256, 0, s, et, w.Y, w.Y5, L, w.ctl);
     }
-    k::dp_control<<<1, 1, 0, s>>>(w.ctl, replay ? w.replay : nullptr, w.record, record_cap);
-    k::dp_accept<<<grid_for_len(L), 256, 0, s>>>(w.ctl, w.Y, w.Y5, w.K[0], w.K[6], L);
+    pdl_launch(k::dp_control, 1, 1, 0, s, w.ctl, replay ? w.replay : nullptr, w.record, record_cap);
+    pdl_launch(k::dp_accept, grid_for_len(L), 256, 0, s, w.ctl, w.Y, w.Y5, w.K[0], w.K[6], L);
 }
 
 struct StreamPair {
@@ -1323,7 +1345,7 @@ extern "C" cut_status cut_flow(const cut_graph *g, double *h, int n_obs, double 
         st = replay_graph(s, N / chunk, [&]() { for (int t = 0; t < chunk; t++) rk4_step(g, w, nops, ds, s); });
         if (st != CUT_OK) return fail(st);
         for (int64_t t = 0; t < N % chunk; t++) rk4_step(g, w, nops, ds, s);
-        k::scan_nonfinite<<<grid_for_len(L), 256, 0, s>>>(w.Y, L, w.flag);
+        pdl_launch(k::scan_nonfinite, grid_for_len(L), 256, 0, s, w.Y, L, w.flag);
         int flag = 0;
         cudaMemcpyAsync(&flag, w.flag, 4, cudaMemcpyDeviceToHost, s);
         cudaError_t e = cudaStreamSynchronize(s);
@@ -1472,7 +1494,7 @@ extern "C" cut_status cut_flow_vjp(const cut_graph *g, const double *h0, int n_o
         cb.nk = 0;
         for (int j = 0; j < nk; j++)
             if (cs[j] != 0.0) { cb.K[cb.nk] = Ks[j]; cb.c[cb.nk] = cs[j]; cb.nk++; }
-        k::rk_combine<<<grid_for_len(L), 256, 0, s>>>(cb, out, L, dsp, dsc, nullptr);
+        pdl_launch(k::rk_combine, grid_for_len(L), 256, 0, s, cb, out, L, dsp, dsc, nullptr);
     };
     // one explicit RK step Ycur -> Ynext of size *dsd, stages kept in U/K
     auto step = [&]() {
@@ -1818,7 +1840,7 @@ extern "C" cut_status cut_combine(int64_t len, const double *base, int nk, const
         if (!K[s]) return set_error(CUT_ERR_INVALID_ARG, "cut_combine: null slope");
         if (c[s] != 0.0) { cb.K[cb.nk] = K[s]; cb.c[cb.nk] = c[s]; cb.nk++; }
     }
-    k::rk_combine<<<grid_for_len(len), 256, 0, (cudaStream_t)stream>>>(cb, out, len, nullptr, ds, nullptr);
+    pdl_launch(k::rk_combine, grid_for_len(len), 256, 0, (cudaStream_t)stream, cb, out, len, nullptr, ds, nullptr);
     CUDA_TRY(cudaGetLastError());
     return set_ok();
 }

@@ -30,6 +30,7 @@ struct ErrTerms {
 
 __global__ void dp_error(ErrTerms et, const double *__restrict__ y, const double *__restrict__ y5,
                          int64_t len, Control *ctl) {
+    pdl_enter();
     __shared__ double red[32];
     if (ctl->done) return;
     const double ds = ctl->ds, rtol = ctl->rtol, atol = ctl->atol;
@@ -60,6 +61,7 @@ __global__ void dp_error(ErrTerms et, const double *__restrict__ y, const double
 
 // One thread: accept/reject, next step size, termination.
 __global__ void dp_control(Control *ctl, const double *replay, double *record, long long record_cap) {
+    pdl_enter();
     if (ctl->done) { ctl->accepted = 0; return; }
     const double r = __longlong_as_double((long long)ctl->err_bits);
     const bool replaying = replay != nullptr;
@@ -106,6 +108,7 @@ __global__ void dp_control(Control *ctl, const double *replay, double *record, l
 // After control: if the attempt was accepted, y <- y5 and K1 <- K7 (FSAL).
 __global__ void dp_accept(const Control *ctl, double *__restrict__ y, const double *__restrict__ y5,
                           double *__restrict__ k1, const double *__restrict__ k7, int64_t len) {
+    pdl_enter();
     if (!ctl->accepted) return;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -116,6 +119,7 @@ __global__ void dp_accept(const Control *ctl, double *__restrict__ y, const doub
 
 // Non-finite scan of a state (RK4 end check).
 __global__ void scan_nonfinite(const double *__restrict__ y, int64_t len, int *flag) {
+    pdl_enter();
     int bad = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
          i += (int64_t)gridDim.x * blockDim.x)

@@ -25,6 +25,18 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 __device__ __forceinline__ bool skip(const int *done) { return done != nullptr && *done != 0; }
 
+// Programmatic dependent launch: the library launches its kernels with the
+// programmatic-serialization attribute, so a kernel's blocks may be resident
+// before the kernel it follows on the stream has finished.  Every kernel
+// first waits until the grids it depends on have completed and their writes
+// are visible (at once for a kernel launched without the attribute), then
+// lets the next grid on the stream be scheduled; that grid waits the same
+// way, so only the launch latency overlaps, never the work.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Load the exact factor table (<= 256 values) into shared memory.
 __device__ __forceinline__ void load_table(double *ws, const double *wtab, int n_codes) {
     for (int c = threadIdx.x; c < n_codes; c += blockDim.x) ws[c] = wtab[c];
@@ -107,6 +119,7 @@ __global__ void __launch_bounds__(kBlock) gen_stage(const uint64_t *__restrict__
                                                     const double *__restrict__ h,
                                                     double *__restrict__ xi, int64_t rows,
                                                     const int *done) {
+    pdl_enter();
     __shared__ double ws[256];
     __shared__ unsigned long long sg[256];
     if (skip(done)) return;
@@ -127,6 +140,7 @@ __global__ void __launch_bounds__(kBlock) comm_stage(const uint64_t *__restrict_
                                                      const uint2 *__restrict__ rec, Weights wt,
                                                      const double *__restrict__ xi, Ops<NOPS> ops,
                                                      int64_t rows, const int *done) {
+    pdl_enter();
     constexpr int RPW = 32 / LANES;
     __shared__ double ws[256];
     __shared__ unsigned long long sg[256];
@@ -193,6 +207,7 @@ __global__ void __launch_bounds__(kBlock) comm_stage_x4(const uint64_t *__restri
                                                         const double *__restrict__ xi,
                                                         const double *__restrict__ X4, Ops<NOPS> ops,
                                                         int64_t rows, const int *done) {
+    pdl_enter();
     static_assert(NOPS <= 8, "at most two packed blocks");
     constexpr int NB = (NOPS + 3) / 4;
     constexpr int RPW = 32 / LANES;
@@ -255,6 +270,7 @@ __global__ void __launch_bounds__(kBlock) comm_stage_x4(const uint64_t *__restri
 // remaining slots are never used)
 template <int NOPS>
 __global__ void pack_x4(Ops<NOPS> ops, int64_t n, double *__restrict__ X4, const int *done) {
+    pdl_enter();
     constexpr int NB = (NOPS + 3) / 4;
     if (skip(done)) return;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
@@ -270,6 +286,7 @@ __global__ void __launch_bounds__(kBlock) gen_pack(const uint64_t *__restrict__ 
                                                    Weights wt, double *__restrict__ xi, int64_t rows,
                                                    Ops<NOPS> ops, int64_t n, double *__restrict__ X4,
                                                    const int *done) {
+    pdl_enter();
     constexpr int NB = (NOPS + 3) / 4;
     __shared__ double ws[256];
     __shared__ unsigned long long sg[256];
@@ -325,6 +342,7 @@ __global__ void __launch_bounds__(kBlock) comm_stage_df(const uint64_t *__restri
                                                         const float2 *__restrict__ xi2,
                                                         const float4 *__restrict__ X2, Ops<NOPS> ops,
                                                         int64_t rows, const int *done) {
+    pdl_enter();
     static_assert(NOPS <= 3, "three operands per interleaved pair block");
     constexpr int RPW = 32 / LANES;
     __shared__ double ws[256];
@@ -390,6 +408,7 @@ __global__ void __launch_bounds__(kBlock) comm_stage_df(const uint64_t *__restri
 // Split doubles into FP32 pairs: out[i * stride + slot] = (hi, lo)
 __global__ void split_pairs(const double *__restrict__ in, int64_t len, float2 *__restrict__ out, int stride,
                             int slot, const int *done) {
+    pdl_enter();
     if (skip(done)) return;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
         const double v = in[i];
@@ -408,6 +427,7 @@ __global__ void split_pairs(const double *__restrict__ in, int64_t len, float2 *
 __global__ void __launch_bounds__(256) assemble(const double *__restrict__ X, int n_src, int64_t n,
                                                 const double *__restrict__ C, int n_out,
                                                 double *__restrict__ out) {
+    pdl_enter();
     extern __shared__ double xs[];                     // [n_src][32]
     const int64_t k0 = (int64_t)blockIdx.x * 32;
     const int kc = threadIdx.x & 31;
@@ -434,6 +454,7 @@ __global__ void __launch_bounds__(kBlock) gen_jvp(const uint64_t *__restrict__ r
                                                   Weights wt, const double *__restrict__ h,
                                                   const double *__restrict__ dh, double *__restrict__ dxi,
                                                   int64_t rows) {
+    pdl_enter();
     __shared__ double ws[256];
     __shared__ unsigned long long sg[256];
     load_weights(ws, sg, wt);
@@ -461,6 +482,7 @@ template <int NOPS>
 __global__ void __launch_bounds__(kBlock) comm_jvp(const uint64_t *__restrict__ rp, const uint2 *__restrict__ rec,
                                                    Weights wt, const double *__restrict__ xi,
                                                    const double *__restrict__ dxi, TanOps<NOPS> t, int64_t rows) {
+    pdl_enter();
     __shared__ double ws[256];
     __shared__ unsigned long long sg[256];
     load_weights(ws, sg, wt);
@@ -495,6 +517,7 @@ __global__ void __launch_bounds__(kBlock) commT_x(const uint64_t *__restrict__ r
                                                   const double *__restrict__ wtab, int n_codes,
                                                   const double *__restrict__ xi, Ops<NOPS> ops,
                                                   int64_t rows) {
+    pdl_enter();
     __shared__ double ws[256];
     load_table(ws, wtab, n_codes);
     const int lane = threadIdx.x & 31;
@@ -531,6 +554,7 @@ __global__ void __launch_bounds__(kBlock) commT_xi(const uint64_t *__restrict__ 
                                                    const double *__restrict__ wtab, int n_codes,
                                                    Pairs<NOPS> pr, double *__restrict__ xi_bar,
                                                    int64_t rows, int accumulate) {
+    pdl_enter();
     __shared__ double ws[256];
     load_table(ws, wtab, n_codes);
     const int lane = threadIdx.x & 31;
@@ -560,6 +584,7 @@ __global__ void __launch_bounds__(kBlock) genT(const uint64_t *__restrict__ rp,
                                                const double *__restrict__ h,
                                                const double *__restrict__ x0_bar,
                                                double *__restrict__ h_bar, int64_t rows) {
+    pdl_enter();
     __shared__ double ws[256];
     load_table(ws, wtab, n_codes);
     const int lane = threadIdx.x & 31;
@@ -590,6 +615,7 @@ __global__ void __launch_bounds__(kBlock) commT_xi_x4(const uint64_t *__restrict
                                                       const double *__restrict__ W4,
                                                       const double *__restrict__ X4,
                                                       double *__restrict__ xi_bar, int64_t rows) {
+    pdl_enter();
     static_assert(NOPS <= 8, "at most two packed blocks");
     constexpr int NB = (NOPS + 3) / 4;
     constexpr int RPW = 32 / LANES;
@@ -643,6 +669,7 @@ __global__ void __launch_bounds__(kBlock) genT_lanes(const uint64_t *__restrict_
                                                      const double *__restrict__ h,
                                                      const double *__restrict__ x0_bar,
                                                      double *__restrict__ h_bar, int64_t rows) {
+    pdl_enter();
     constexpr int RPW = 32 / LANES;
     __shared__ double ws[256];
     __shared__ unsigned long long sg[256];
@@ -671,6 +698,7 @@ __global__ void __launch_bounds__(kBlock) genT_lanes(const uint64_t *__restrict_
 // one operand, so their pieces and outputs are neighbours in memory.
 __global__ void piece_reduce(const uint64_t *__restrict__ vr, int64_t rows, Ops<8> io, int nops,
                              const double *__restrict__ add) {
+    pdl_enter();
     const int64_t total = rows * nops;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         const int o = (int)(t / rows);
@@ -713,6 +741,7 @@ __global__ void __launch_bounds__(kBlock) stage_gen(StageIn si, int64_t n, doubl
                                                     double *__restrict__ U_full, const uint64_t *__restrict__ rp,
                                                     const uint2 *__restrict__ rec, Weights wt,
                                                     double *__restrict__ xi, int64_t rows, const int *done) {
+    pdl_enter();
     constexpr int NB = (NOPS + 3) / 4;
     constexpr int RPW = 32 / LANES;
     __shared__ double ws[256];
@@ -769,6 +798,7 @@ struct Combine {
 
 __global__ void rk_combine(Combine cb, double *__restrict__ out, int64_t len, const double *ds_ptr,
                            double ds_const, const int *done) {
+    pdl_enter();
     if (skip(done)) return;
     const double ds = ds_ptr ? *ds_ptr : ds_const;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
