@@ -27,6 +27,13 @@
  *     them until the stream reaches that point.  "host" pointers are
  *     ordinary CPU memory, read or written before the call returns.
  *   - `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *   - The graph kernels are launched with programmatic stream serialization
+ *     and let the next grid on the stream be scheduled as soon as they
+ *     start.  Work the caller queues with ordinary launches, copies or
+ *     events still waits for them to complete.  A kernel the caller
+ *     launches right after a call with that attribute set must wait on the
+ *     device (cudaGridDependencySynchronize) before it reads the call's
+ *     outputs.
  *   - "Scratch from the stream-ordered allocator" below means the library's
  *     own memory pool of the graph's device (cudaMallocFromPoolAsync; freed
  *     with cudaFreeAsync on the call's stream).  The pool keeps up to 1 GiB
