@@ -245,16 +245,50 @@ __global__ void __launch_bounds__(kBlock) comm_stage_x4(const uint64_t *__restri
 #pragma unroll
                     for (int o = 0; o < NOPS; o++) acc[o] += c[u] * xv[u][o];
             }
-            for (; p < e; p += LANES) {
-                const uint2 q = __ldcs(rec + p);
-                const double c = COEF(q);
-                double xv[4 * NB];
+            // the lane's last records (fewer than U).  Rows of a 32-lane
+            // stage are short (a graph of fewer than 16,384 rows; often
+            // every record of a lane is here): their loads are issued
+            // together, then summed in record order as one at a time would
+            // be.  Long rows keep the one-at-a-time tail, which needs fewer
+            // registers (6 CTAs per SM for the 8-lane FP64 stage).
+            if constexpr (LANES == 32) {
+                if (p < e) {
+                    uint2 q[U];
+                    bool ok[U];
 #pragma unroll
-                for (int b = 0; b < NB; b++)
-                    ld_quad64(X4 + 4 * NB * (int64_t)q.y + 4 * b, xv[4 * b], xv[4 * b + 1], xv[4 * b + 2],
-                              xv[4 * b + 3]);
+                    for (int u = 0; u < U; u++) {
+                        ok[u] = p + u * LANES < e;
+                        q[u] = ok[u] ? __ldcs(rec + p + u * LANES) : make_uint2(0u, 0u);
+                    }
+                    double c[U], xv[U][4 * NB];
 #pragma unroll
-                for (int o = 0; o < NOPS; o++) acc[o] += c * xv[o];
+                    for (int u = 0; u < U; u++) {
+                        if (!ok[u]) continue;
+                        c[u] = COEF(q[u]);
+#pragma unroll
+                        for (int b = 0; b < NB; b++)
+                            ld_quad64(X4 + 4 * NB * (int64_t)q[u].y + 4 * b, xv[u][4 * b], xv[u][4 * b + 1],
+                                      xv[u][4 * b + 2], xv[u][4 * b + 3]);
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; u++)
+                        if (ok[u]) {
+#pragma unroll
+                            for (int o = 0; o < NOPS; o++) acc[o] += c[u] * xv[u][o];
+                        }
+                }
+            } else {
+                for (; p < e; p += LANES) {
+                    const uint2 q = __ldcs(rec + p);
+                    const double c = COEF(q);
+                    double xv[4 * NB];
+#pragma unroll
+                    for (int b = 0; b < NB; b++)
+                        ld_quad64(X4 + 4 * NB * (int64_t)q.y + 4 * b, xv[4 * b], xv[4 * b + 1], xv[4 * b + 2],
+                                  xv[4 * b + 3]);
+#pragma unroll
+                    for (int o = 0; o < NOPS; o++) acc[o] += c * xv[o];
+                }
             }
 #undef COEF
         }
