@@ -259,6 +259,25 @@ def cpu_sample(seconds_budget=20.0, cores=None, gpu_flow_rhs_calls=None):
     return out
 
 
+def rk4_launches(steps, nops, r_g):
+    """Kernels cut_flow launches for `steps` RK4 steps (then one non-finite
+    scan).  A stage: with at most eight operands, a generator stage of at most
+    65,536 records fuses the stage input, operand packing and generator into
+    one launch, larger ones launch the stage input (stages 2-4) and then
+    packing + generator together; one commutator launch.  More than eight
+    operands: stage input, generator, and one commutator launch per eight
+    operands.  Plus the final combination of each step.  (FP64 arithmetic;
+    a graph whose few long rows are cut into pieces adds one piece-sum
+    launch per right-hand side, which the stress graphs do not.)"""
+    if nops <= 8 and r_g <= 65536:
+        per_step = 4 * 2 + 1
+    elif nops <= 8:
+        per_step = 4 * 2 + 3 + 1
+    else:
+        per_step = 4 * (1 + (nops + 7) // 8) + 3 + 1
+    return int(steps * per_step + 1)
+
+
 def batched_vs_plain(cg, torch, dev, local, batch=1024, plain_sample=8):
     """Batched flows/s against the plain single-instance GPU flow.
 
@@ -855,7 +874,7 @@ def main():
             # per RK4 step: 4 right-hand sides (generator stage, then one pack and
             # one commutator launch for up to eight operands, else one commutator
             # launch per eight) and 4 combinations; one non-finite scan per flow
-            "gpu_launches": int(args.steps * 4 * (1 + (2 if nops <= 8 else (nops + 7) // 8)) + args.steps * 4 + 1),
+            "gpu_launches": rk4_launches(args.steps, nops, G.R_g),
             "roofline": roofline,
             "df64": df,
             "batched": batched,
