@@ -40,27 +40,6 @@ cut_status set_ok() { return CUT_OK; }
         }                                                                                       \
     } while (0)
 
-// Kernel launch with programmatic stream serialization: the kernel's blocks
-// may be scheduled while its predecessor on the stream is finishing; every
-// kernel of the library first waits on the device for that predecessor
-// (k::pdl_enter), so only launch latency is overlapped.
-template <typename... P, typename... A>
-static void pdl_launch(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A &&...args) {
-    cudaLaunchConfig_t cfg;
-    memset(&cfg, 0, sizeof(cfg));
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute at;
-    memset(&at, 0, sizeof(at));
-    at.id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at.val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = &at;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
-}
-
 static void *current_context();
 
 // One pool per device, remade when the device's context changes (a device

@@ -10,6 +10,8 @@
 #pragma once
 #include <cstdint>
 
+#include "pdl.cuh"
+
 namespace cut {
 namespace k {
 
@@ -25,17 +27,6 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 __device__ __forceinline__ bool skip(const int *done) { return done != nullptr && *done != 0; }
 
-// Programmatic dependent launch: the library launches its kernels with the
-// programmatic-serialization attribute, so a kernel's blocks may be resident
-// before the kernel it follows on the stream has finished.  Every kernel
-// first waits until the grids it depends on have completed and their writes
-// are visible (at once for a kernel launched without the attribute), then
-// lets the next grid on the stream be scheduled; that grid waits the same
-// way, so only the launch latency overlaps, never the work.
-__device__ __forceinline__ void pdl_enter() {
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
 
 // Load the exact factor table (<= 256 values) into shared memory.
 __device__ __forceinline__ void load_table(double *ws, const double *wtab, int n_codes) {

@@ -32,6 +32,7 @@ namespace mlpk {
 
 __global__ void pack_input(const float *__restrict__ x, int batch, int n_in, int in_p, int Mp, bf16 *__restrict__ xb,
                            bf16 *__restrict__ xt) {
+    pdl_enter();
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)Mp * in_p;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int m = (int)(e / in_p), c = (int)(e % in_p);
@@ -53,6 +54,7 @@ __global__ void __launch_bounds__(256) mse_grad(const float *__restrict__ Y, int
                                                 bf16 *__restrict__ dz, bf16 *__restrict__ dzt,
                                                 float *__restrict__ dz32, float *__restrict__ loss,
                                                 const float *__restrict__ J, const float *__restrict__ x, int K) {
+    pdl_enter();
     __shared__ float Js[32][65], Xs[32][65], Gs[32][33], red[256];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
     const int c0 = blockIdx.x * 32, m0 = blockIdx.y * 32, c = c0 + tx;
@@ -109,6 +111,7 @@ __global__ void __launch_bounds__(256) mse_grad(const float *__restrict__ Y, int
 constexpr int kColSumGroups = 32;
 __global__ void __launch_bounds__(32 * kColSumGroups) col_sum(const float *__restrict__ dz, int ld, int rows, int cols,
                                                              float *__restrict__ db) {
+    pdl_enter();
     __shared__ float part[kColSumGroups][33];
     const int tx = threadIdx.x, ty = threadIdx.y, c = blockIdx.x * 32 + tx;
     float s = 0.0f;
@@ -127,6 +130,7 @@ __global__ void __launch_bounds__(32 * kColSumGroups) col_sum(const float *__res
 
 // Split-K partial products: out[e] = sum_z part[z][e] in z order.
 __global__ void sum_splits(const float *__restrict__ part, int splits, int64_t count, float *__restrict__ out) {
+    pdl_enter();
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
         float t = 0.0f;
         for (int z = 0; z < splits; z++) t += part[(int64_t)z * count + e];
@@ -163,6 +167,7 @@ struct AdamTiles {
 // and writes of both copies coalesced.
 __global__ void __launch_bounds__(256) adamw_tiles(AdamTiles a, float lr, float b1, float b2, float eps, float bc1,
                                                    float bc2) {
+    pdl_enter();
     __shared__ bf16 tile[32][34];
     for (int64_t t = blockIdx.x; t < a.tile_start[3]; t += gridDim.x) {
         const int k = t >= a.tile_start[2] ? 2 : (t >= a.tile_start[1] ? 1 : 0);
@@ -195,6 +200,7 @@ __global__ void __launch_bounds__(256) adamw_tiles(AdamTiles a, float lr, float 
 }
 
 __global__ void adamw_all(AdamSegs segs, float lr, float b1, float b2, float eps, float bc1, float bc2) {
+    pdl_enter();
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < segs.total;
          t += (int64_t)gridDim.x * blockDim.x) {
         int k = 0;
@@ -214,6 +220,7 @@ __global__ void adamw_all(AdamSegs segs, float lr, float b1, float b2, float eps
 
 __global__ void to_bf16(const float *__restrict__ w, int64_t count, int in_p, int out_p, bf16 *__restrict__ wb,
                         bf16 *__restrict__ wt) {
+    pdl_enter();
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
         const bf16 b = __float2bfloat16(w[e]);
         wb[e] = b;
@@ -236,6 +243,7 @@ __device__ __forceinline__ double fit_a(const float *x, int n_in, int64_t b, int
 __global__ void __launch_bounds__(128) fit_gram_partials(const float *__restrict__ x, const double *__restrict__ t,
                                                          int64_t batch, int n_in, int n_out, int64_t rows_per_chunk,
                                                          double *__restrict__ partial) {
+    pdl_enter();
     const int P = n_in + 1, ncol = P + n_out;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t b0 = (int64_t)blockIdx.y * rows_per_chunk, b1 = min(batch, b0 + rows_per_chunk);
@@ -263,6 +271,7 @@ __global__ void __launch_bounds__(128) fit_gram_partials(const float *__restrict
 
 // M[p][c] = sum_ch partial[ch][p][c] (chunk order)
 __global__ void fit_reduce(const double *__restrict__ partial, int chunks, int64_t len, double *__restrict__ M) {
+    pdl_enter();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
         double s = 0.0;
         for (int ch = 0; ch < chunks; ch++) s += partial[ch * len + i];
@@ -274,6 +283,7 @@ __global__ void fit_reduce(const double *__restrict__ partial, int chunks, int64
 // G coef[:, o] = M[:, P + o] for its outputs; coef[P][n_out].
 __global__ void __launch_bounds__(256) fit_solve(const double *__restrict__ M, int n_in, int n_out, double ridge,
                                                  double *__restrict__ coef, int *__restrict__ bad) {
+    pdl_enter();
     const int P = n_in + 1, ncol = P + n_out;
     __shared__ double Lm[kFitP][kFitP];
     __shared__ int ok;
@@ -314,6 +324,7 @@ __global__ void __launch_bounds__(128) fit_resid_partials(const float *__restric
                                                           const double *__restrict__ coef, int64_t batch, int n_in,
                                                           int n_out, int64_t rows_per_chunk,
                                                           double *__restrict__ partial) {
+    pdl_enter();
     const int P = n_in + 1;
     const int o = blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t b0 = (int64_t)blockIdx.y * rows_per_chunk, b1 = min(batch, b0 + rows_per_chunk);
@@ -333,6 +344,7 @@ __global__ void __launch_bounds__(128) fit_resid_partials(const float *__restric
 __global__ void fit_write(const double *__restrict__ coef, const double *__restrict__ ss, const float *__restrict__ w,
                           int64_t batch, int n_in, int n_out, float *__restrict__ scale, float *__restrict__ shift,
                           float *__restrict__ J) {
+    pdl_enter();
     for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < n_out; o += gridDim.x * blockDim.x) {
         shift[o] = (float)coef[o];
         for (int i = 0; i < n_in; i++) J[(int64_t)o * n_in + i] = (float)coef[(int64_t)(1 + i) * n_out + o];
@@ -350,6 +362,7 @@ struct Members {
 // order) and spread[b] = max over the masked outputs of max_k - min_k.
 __global__ void __launch_bounds__(256) ensemble_stats(Members m, int K, int n_out, const uint8_t *__restrict__ mask,
                                                       float *__restrict__ mean, float *__restrict__ spread) {
+    pdl_enter();
     __shared__ float red[256];
     const int64_t b = blockIdx.x;
     float sp = 0.0f;
@@ -439,7 +452,7 @@ static cut_status gemm(const bf16 *A, const bf16 *B, int M, int N, int K, tc::Ep
     const int act = ep.dgelu_z ? tc::kGeluGrad : (gelu ? tc::kGelu : tc::kLinear);
     auto launch = [&](auto kern, size_t sm) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        kern<<<grid, tc::kThreads, sm, s>>>(ma, mb, K / splits, ep);
+        pdl_launch(kern, grid, tc::kThreads, sm, s, ma, mb, K / splits, ep);
     };
     // at most one CTA per SM: the deep ring (one CTA per SM, more copies in flight)
     const bool deep = (int64_t)grid.x * grid.y * grid.z <= num_sms();
@@ -578,7 +591,7 @@ static cut_status forward(cut_mlp *m, int batch, const float *x, cudaStream_t s,
     const int Mp = pad_to(batch, 128);
     cut_status st = ensure_batch(m, Mp);
     if (st != CUT_OK) return st;
-    mlpk::pack_input<<<grid_of((int64_t)Mp * m->L[0].in_p), 256, 0, s>>>(x, batch, m->n_in, m->L[0].in_p, Mp, m->xb,
+    pdl_launch(mlpk::pack_input, grid_of((int64_t)Mp * m->L[0].in_p), 256, 0, s, x, batch, m->n_in, m->L[0].in_p, Mp, m->xb,
                                                                           m->xt);
     const bf16 *in = m->xb;
     for (int l = 0; l < 3; l++) {
@@ -656,7 +669,7 @@ cut_status cut_mlp_create(int n_in, int n_hidden, int n_out, uint64_t seed, int 
                 hw[(size_t)o * Ly.in_p + i] = (float)((2.0 * u - 1.0) * a);
             }
         cudaMemcpy(Ly.w, hw.data(), cnt * 4, cudaMemcpyHostToDevice);
-        mlpk::to_bf16<<<grid_of(cnt), 256>>>(Ly.w, cnt, Ly.in_p, Ly.out_p, Ly.wb, Ly.wt);
+        pdl_launch(mlpk::to_bf16, grid_of(cnt), 256, 0, 0, Ly.w, cnt, Ly.in_p, Ly.out_p, Ly.wb, Ly.wt);
     }
     size_t wmax = 0;
     for (int l = 0; l < 3; l++) wmax = std::max(wmax, (size_t)m->L[l].in_p * m->L[l].out_p);
@@ -755,16 +768,16 @@ cut_status cut_mlp_fit_linear(cut_mlp *m, int batch, const float *x, const doubl
             return set_error(CUT_ERR_OUT_OF_MEMORY, "cut_mlp_fit_linear: weights");
         }
     }
-    mlpk::fit_gram_partials<<<dim3((ncol + 127) / 128, chunks), 128, 0, s>>>(x, t, batch, m->n_in, m->n_out, rpc,
+    pdl_launch(mlpk::fit_gram_partials, dim3((ncol + 127) / 128, chunks), 128, 0, s, x, t, batch, m->n_in, m->n_out, rpc,
                                                                               partial);
-    mlpk::fit_reduce<<<grid_of((int64_t)P * ncol), 256, 0, s>>>(partial, chunks, (int64_t)P * ncol, M);
+    pdl_launch(mlpk::fit_reduce, grid_of((int64_t)P * ncol), 256, 0, s, partial, chunks, (int64_t)P * ncol, M);
     // a relative ridge of 1e-12 of the Gram matrix's scale keeps the solve
     // defined when an input never varies
-    mlpk::fit_solve<<<1, 256, 0, s>>>(M, m->n_in, m->n_out, 1e-12 * (double)batch, coef, nullptr);
-    mlpk::fit_resid_partials<<<dim3((m->n_out + 127) / 128, chunks), 128, 0, s>>>(x, t, coef, batch, m->n_in,
+    pdl_launch(mlpk::fit_solve, 1, 256, 0, s, M, m->n_in, m->n_out, 1e-12 * (double)batch, coef, nullptr);
+    pdl_launch(mlpk::fit_resid_partials, dim3((m->n_out + 127) / 128, chunks), 128, 0, s, x, t, coef, batch, m->n_in,
                                                                                    m->n_out, rpc, rp);
-    mlpk::fit_reduce<<<grid_of(m->n_out), 256, 0, s>>>(rp, chunks, m->n_out, ss);
-    mlpk::fit_write<<<grid_of(m->n_out), 256, 0, s>>>(coef, ss, w, batch, m->n_in, m->n_out, m->scale, m->shift,
+    pdl_launch(mlpk::fit_reduce, grid_of(m->n_out), 256, 0, s, rp, chunks, m->n_out, ss);
+    pdl_launch(mlpk::fit_write, grid_of(m->n_out), 256, 0, s, coef, ss, w, batch, m->n_in, m->n_out, m->scale, m->shift,
                                                       m->J);
     e = cudaGetLastError();
     cudaFreeAsync(buf, s);
@@ -783,7 +796,7 @@ cut_status cut_mlp_ensemble_stats(int K, int batch, int n_out, const float *cons
         mb.p[k] = preds[k];
     }
     if (batch == 0) return set_ok();
-    mlpk::ensemble_stats<<<batch, 256, 0, (cudaStream_t)stream>>>(mb, K, n_out, mask, mean, spread);
+    pdl_launch(mlpk::ensemble_stats, batch, 256, 0, (cudaStream_t)stream, mb, K, n_out, mask, mean, spread);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(CUT_ERR_CUDA, std::string("cut_mlp_ensemble_stats: ") + cudaGetErrorString(e));
     return set_ok();
@@ -817,7 +830,7 @@ static cut_status params_io(cut_mlp *m, float *host, int to_host, int which) {
         off += Ly.out;
         if (!to_host && !which) {
             const size_t cnt = (size_t)Ly.in_p * Ly.out_p;
-            mlpk::to_bf16<<<grid_of(cnt), 256>>>(Ly.w, cnt, Ly.in_p, Ly.out_p, Ly.wb, Ly.wt);
+            pdl_launch(mlpk::to_bf16, grid_of(cnt), 256, 0, 0, Ly.w, cnt, Ly.in_p, Ly.out_p, Ly.wb, Ly.wt);
         }
     }
     cudaError_t e = cudaDeviceSynchronize();
@@ -855,7 +868,7 @@ static cut_status backward_body(cut_mlp *m, int batch, const float *x, const flo
     const int Mp = pad_to(batch, 128);
     Layer *L = m->L;
     // output layer
-    mlpk::mse_grad<<<dim3(L[2].out_p / 32, Mp / 32), dim3(32, 8), 0, s>>>(
+    pdl_launch(mlpk::mse_grad, dim3(L[2].out_p / 32, Mp / 32), dim3(32, 8), 0, s, 
         m->z[2], L[2].out_p, target, batch, m->n_out, m->scale, m->shift, Mp, L[2].out_p, m->dzb, m->dzt, m->dz32,
         loss, m->J, x, m->n_in);
     bf16 *dzb = m->dzb, *dzt = m->dzt, *nb = m->dzb2, *nt = m->dzt2;
@@ -880,8 +893,8 @@ static cut_status backward_body(cut_mlp *m, int batch, const float *x, const flo
         st = gemm(dzt, inT, Ly.out_p, Ly.in_p, Mp, e, s, splits);
         if (st != CUT_OK) return st;
         if (splits > 1)
-            mlpk::sum_splits<<<grid_of(e.split_stride), 256, 0, s>>>(m->splitbuf, splits, e.split_stride, Ly.gw);
-        mlpk::col_sum<<<(Ly.out_p + 31) / 32, dim3(32, mlpk::kColSumGroups), 0, s>>>(dz32, Ly.out_p, batch, Ly.out_p,
+            pdl_launch(mlpk::sum_splits, grid_of(e.split_stride), 256, 0, s, m->splitbuf, splits, e.split_stride, Ly.gw);
+        pdl_launch(mlpk::col_sum, (Ly.out_p + 31) / 32, dim3(32, mlpk::kColSumGroups), 0, s, dz32, Ly.out_p, batch, Ly.out_p,
                                                                                    Ly.gb);
         if (l == 0) break;
         // dZ_{l-1} = (dZ_l W_l) * GELU'(Z_{l-1})
@@ -974,9 +987,9 @@ cut_status cut_mlp_adamw_step(cut_mlp *m, float lr, float beta1, float beta2, fl
         start += B.count;
     }
     segs.total = start;
-    mlpk::adamw_tiles<<<(int)std::min<int64_t>(tw.tile_start[3], 148 * 8), dim3(32, 8), 0, s>>>(
+    pdl_launch(mlpk::adamw_tiles, (int)std::min<int64_t>(tw.tile_start[3], 148 * 8), dim3(32, 8), 0, s, 
         tw, lr, beta1, beta2, eps, bc1, bc2);
-    mlpk::adamw_all<<<grid_of(start), 256, 0, s>>>(segs, lr, beta1, beta2, eps, bc1, bc2);
+    pdl_launch(mlpk::adamw_all, grid_of(start), 256, 0, s, segs, lr, beta1, beta2, eps, bc1, bc2);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(CUT_ERR_CUDA, std::string("cut_mlp_adamw_step: ") + cudaGetErrorString(e));
     return set_ok();

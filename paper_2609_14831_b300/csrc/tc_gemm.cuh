@@ -21,6 +21,8 @@
 
 #include <cstdint>
 
+#include "pdl.cuh"
+
 namespace cut {
 namespace tc {
 
@@ -182,6 +184,9 @@ __global__ void __launch_bounds__(kThreads, ST <= STAGES ? 2 : 1)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
+    // the barriers and the accumulator are set up while the previous kernel
+    // on the stream may still run; no global memory is touched before this
+    pdl_enter();
 
     int issued = 0;
     if (warp == 0 && lane == 0) {
