@@ -27,7 +27,7 @@
  *     them until the stream reaches that point.  "host" pointers are
  *     ordinary CPU memory, read or written before the call returns.
  *   - `stream` is a cudaStream_t (NULL = the legacy default stream).
- *   - The graph kernels are launched with programmatic stream serialization
+ *   - The library's kernels are launched with programmatic stream serialization
  *     and let the next grid on the stream be scheduled as soon as they
  *     start.  Work the caller queues with ordinary launches, copies or
  *     events still waits for them to complete.  A kernel the caller
