@@ -69,3 +69,18 @@ def test_parallel_oracle_rhs_equals_the_oracle():
     dh, dxs = oracle.rhs(w.alg, w.nmodes, w.labels, w.h, w.observables)
     for g, want in zip(got, [dh] + list(dxs)):
         np.testing.assert_allclose(g, want, rtol=0, atol=1e-13 * max(1.0, np.max(np.abs(want))))
+
+
+def test_launch_count_follows_the_stage_structure():
+    """The bench's gpu_launches claim for the timed RK4 flow: on the stress
+    graph (3.5e6 generator records, three operands) a step is four stages of
+    generator+packing and commutator launches, three stage inputs and the
+    final combination; an ncu launch list of the timed region counts
+    40 + 40 + 40 + 1 for ten steps."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.rk4_launches(10, 3, 3456464) == 121
+    # a small graph: stage input, packing and generator fused into one launch
+    assert bench.rk4_launches(10, 3, 4648) == 10 * (4 * 2 + 1) + 1
+    # nine operands: generator, then two commutator passes of up to eight
+    assert bench.rk4_launches(1, 9, 3456464) == 4 * (1 + 2) + 3 + 1 + 1
