@@ -12,6 +12,8 @@
 // input 2), so the bundle is bitwise reproducible for any thread count.
 #include <sys/resource.h>
 
+#include "trace.h"
+
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -251,6 +253,7 @@ void build_graph(const cut_build_opts &o, int64_t n, const uint64_t *labels, Hos
                  cut_build_stats *st) {
     using clk = std::chrono::steady_clock;
     auto t0 = clk::now();
+    TraceRange count("cut_build/count");
     Ctx c;
     c.alg = o.algebra;
     c.nmodes = o.nmodes;
@@ -401,6 +404,8 @@ void build_graph(const cut_build_opts &o, int64_t n, const uint64_t *labels, Hos
     out_cnt_map.clear();
     LabelIndex oidx(g.out_labels);
     auto t1 = clk::now();
+    count.end();
+    TraceRange write("cut_build/write");
 
     // ---- traversal 2: write every record into its final slot
     {
@@ -442,6 +447,7 @@ void build_graph(const cut_build_opts &o, int64_t n, const uint64_t *labels, Hos
     sort_segments(T, g.rp[1], g.rec[1]);
     sort_segments(T, g.rp[2], g.rec[2]);
     auto t2 = clk::now();
+    write.end();
     if (st) {
         st->n = n;
         st->n_g = ng;
@@ -463,13 +469,18 @@ extern "C" cut_status cut_build(const cut_build_opts *opts, int64_t n, const uin
         return set_error(CUT_ERR_INVALID_ARG, "cut_build: unknown algebra");
     if (opts->nmodes < 1 || opts->nmodes > 32) return set_error(CUT_ERR_INVALID_ARG, "cut_build: nmodes must be 1..32");
     auto t0 = std::chrono::steady_clock::now();
+    TraceRange trace("cut_build");
     cut_build_stats local;
     memset(&local, 0, sizeof(local));
     try {
         HostGraph g;
         build_graph(*opts, n, labels, g, &local);
         int64_t bytes = 0;
-        std::string e = write_bundle(g, path, &bytes);
+        std::string e;
+        {
+            TraceRange tr("cut_build/store");
+            e = write_bundle(g, path, &bytes);
+        }
         if (!e.empty()) return set_error(CUT_ERR_IO, "cut_build: " + e);
         local.bytes_stored = bytes;
     } catch (const std::invalid_argument &e) {

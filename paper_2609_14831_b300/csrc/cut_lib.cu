@@ -18,6 +18,7 @@
 #include "flow_kernels.cuh"
 #include "kernels.cuh"
 #include "status.h"
+#include "trace.h"
 
 namespace cut {
 
@@ -477,6 +478,7 @@ const char *cut_last_error(void) { return g_err.c_str(); }
 const char *cut_version(void) { return "cutgraph-b300 0.1 (sm_103a)"; }
 
 cut_status cut_graph_load(const char *path, int device, unsigned flags, cut_graph **out) {
+    TraceRange trace_("cut_graph_load");
     if (!path || !out) return set_error(CUT_ERR_INVALID_ARG, "cut_graph_load: null argument");
     if (flags & ~(unsigned)CUT_LOAD_ADJOINT) return set_error(CUT_ERR_INVALID_ARG, "cut_graph_load: unknown flags");
     *out = nullptr;
@@ -489,7 +491,9 @@ cut_status cut_graph_load(const char *path, int device, unsigned flags, cut_grap
     std::unique_ptr<cut_graph> g(new cut_graph());
     g->device = device;
     std::string err;
+    TraceRange read("cut_graph_load/read_verify");
     int rc = read_bundle(path, g->host, &err);
+    read.end();
     if (rc != 0) return set_error((cut_status)rc, "cut_graph_load: " + err);
     if (device == -1) {  // host-only handle: query, labels, weights, records
         g->st[0].rows = g->host.n_g(); g->st[0].R = g->host.R(0);
@@ -500,6 +504,7 @@ cut_status cut_graph_load(const char *path, int device, unsigned flags, cut_grap
     }
     DeviceGuard dg(device);
     int64_t bytes = 0;
+    TraceRange upload("cut_graph_load/upload");
     for (int s = 0; s < 3; s++) {
         cut_status st = upload_csr(g->st[s], g->host.rp[s], g->host.rec[s], bytes);
         if (st != CUT_OK) return st;
@@ -509,7 +514,9 @@ cut_status cut_graph_load(const char *path, int device, unsigned flags, cut_grap
     st = upload_weights(g.get());
     if (st != CUT_OK) return st;
     g->device_bytes += bytes;
+    upload.end();
     if (flags & CUT_LOAD_ADJOINT) {
+        TraceRange tr("cut_graph_load/transposes");
         st = ensure_transposes(g.get());
         if (st != CUT_OK) return st;
     }
@@ -586,6 +593,7 @@ cut_status cut_graph_outside_labels(const cut_graph *g, uint64_t *out) {
 
 cut_status cut_rhs_outside(const cut_graph *g, const double *h, int n_obs, const double *x, double *c,
                            cut_stream_t stream) {
+    TraceRange trace_("cut_rhs_outside");
     if (whole_graph(g, "cut_rhs_outside") != CUT_OK) return CUT_ERR_INVALID_ARG;
     if (!g || g->device < 0 || !h || !c || n_obs < 0 || n_obs > 63 || (n_obs > 0 && !x))
         return set_error(CUT_ERR_INVALID_ARG, "cut_rhs_outside: bad argument");
@@ -641,6 +649,7 @@ cut_status cut_graph_records(const cut_graph *g, int stage, int64_t *row_ptr, in
 
 cut_status cut_rhs(const cut_graph *g, const double *h, int n_obs, const double *x, double *dh, double *dx,
                    double *xi_out, cut_stream_t stream) {
+    TraceRange trace_("cut_rhs");
     if (whole_graph(g, "cut_rhs") != CUT_OK) return CUT_ERR_INVALID_ARG;
     if (!g || g->device < 0 || !h || !dh || n_obs < 0 || n_obs > 63 || (n_obs > 0 && (!x || !dx)))
         return set_error(CUT_ERR_INVALID_ARG, "cut_rhs: bad argument");
@@ -676,6 +685,7 @@ cut_status cut_graph_set_arithmetic(cut_graph *g, int arith) {
 
 cut_status cut_apply_L(const cut_graph *g, const double *xi, int n_ops, const double *x, double *dx,
                        cut_stream_t stream) {
+    TraceRange trace_("cut_apply_L");
     if (whole_graph(g, "cut_apply_L") != CUT_OK) return CUT_ERR_INVALID_ARG;
     if (!g || g->device < 0 || !xi || n_ops < 1 || n_ops > 64 || !x || !dx)
         return set_error(CUT_ERR_INVALID_ARG, "cut_apply_L: bad argument");
@@ -698,6 +708,7 @@ cut_status cut_apply_L(const cut_graph *g, const double *xi, int n_ops, const do
 // ----------------------------------------------------------------- assembly
 extern "C" cut_status cut_assemble(int n_src, int64_t n, const double *X, int n_out, const double *C, double *out,
                                    cut_stream_t stream) {
+    TraceRange trace_("cut_assemble");
     if (n_src < 1 || n_src > 3000 || n < 1 || n_out < 1 || !X || !C || !out)
         return set_error(CUT_ERR_INVALID_ARG, "cut_assemble: bad argument (1 <= n_src <= 3000)");
     cudaStream_t s = (cudaStream_t)stream;
@@ -713,6 +724,7 @@ extern "C" cut_status cut_assemble(int n_src, int64_t n, const double *X, int n_
 // ----------------------------------------------------------------- tangent
 extern "C" cut_status cut_rhs_jvp(const cut_graph *g, const double *h, int n_obs, const double *x, const double *dh,
                                   const double *dx, double *out_h, double *out_x, cut_stream_t stream) {
+    TraceRange trace_("cut_rhs_jvp");
     if (whole_graph(g, "cut_rhs_jvp") != CUT_OK) return CUT_ERR_INVALID_ARG;
     if (!g || g->device < 0 || !h || !dh || !out_h || n_obs < 0 || n_obs > 63 ||
         (n_obs > 0 && (!x || !dx || !out_x)))
@@ -1061,6 +1073,7 @@ static void stacked_vjp(const cut_graph *g, const double *Y, const double *W, do
 extern "C" cut_status cut_rhs_adjoint(const cut_graph *g, const double *h, int n_obs, const double *x,
                                       const double *w_h, const double *w_x, double *h_bar, double *x_bar,
                                       cut_stream_t stream) {
+    TraceRange trace_("cut_rhs_adjoint");
     if (whole_graph(g, "cut_rhs_adjoint") != CUT_OK) return CUT_ERR_INVALID_ARG;
     if (!g || g->device < 0 || !h || !w_h || !h_bar || n_obs < 0 || n_obs > 63 || (n_obs > 0 && (!x || !w_x || !x_bar)))
         return set_error(CUT_ERR_INVALID_ARG, "cut_rhs_adjoint: bad argument");
@@ -1291,6 +1304,7 @@ static int64_t rk4_nsteps(const cut_flow_opts *o, double *ds_eff) {
 
 extern "C" cut_status cut_flow(const cut_graph *g, double *h, int n_obs, double *x, const cut_flow_opts *o,
                                cut_flow_stats *stats, cut_stream_t stream) {
+    TraceRange trace_("cut_flow");
     if (whole_graph(g, "cut_flow") != CUT_OK) return CUT_ERR_INVALID_ARG;
     if (!g || g->device < 0 || !h || n_obs < 0 || n_obs > 63 || (n_obs > 0 && !x)) return set_error(CUT_ERR_INVALID_ARG, "cut_flow: bad argument");
     cut_status st = check_opts(o);
@@ -1403,6 +1417,7 @@ extern "C" cut_status cut_flow(const cut_graph *g, double *h, int n_obs, double 
 extern "C" cut_status cut_flow_vjp(const cut_graph *g, const double *h0, int n_obs, const double *x0,
                                    const cut_flow_opts *o, int checkpoint_every, const double *yb_h,
                                    const double *yb_x, double *gh, double *gx, cut_stream_t stream) {
+    TraceRange trace_("cut_flow_vjp");
     if (whole_graph(g, "cut_flow_vjp") != CUT_OK) return CUT_ERR_INVALID_ARG;
     if (!g || g->device < 0 || !h0 || !yb_h || !gh || n_obs < 0 || n_obs > 63 || (n_obs > 0 && (!x0 || !yb_x || !gx)) ||
         checkpoint_every < 1)
@@ -1602,6 +1617,7 @@ static thread_local int g_last_tile = 0;
 extern "C" cut_status cut_flow_batched(const cut_graph *g, int batch, double *h, int n_obs, double *x, int precision,
                                        const cut_flow_opts *o, int tile, int *steps_out, int *status_out,
                                        cut_stream_t stream) {
+    TraceRange trace_("cut_flow_batched");
     if (whole_graph(g, "cut_flow_batched") != CUT_OK) return CUT_ERR_INVALID_ARG;
     if (!g || g->device < 0 || batch < 1 || !h || n_obs < 0 || n_obs > 3 || (n_obs > 0 && !x) || !steps_out ||
         !status_out || (precision != CUT_FP64 && precision != CUT_FP32REC_FP64STATE) || tile < 0)
@@ -1744,6 +1760,7 @@ extern "C" cut_status cut_graph_partition(const cut_graph *g, int stage, int par
 
 extern "C" cut_status cut_graph_load_shard(const char *path, int device, int rank, int world, unsigned flags,
                                            cut_graph **out) {
+    TraceRange trace_("cut_graph_load_shard");
     if (!path || !out || device < 0 || world < 1 || world > 65536 || rank < 0 || rank >= world || flags != 0)
         return set_error(CUT_ERR_INVALID_ARG, "cut_graph_load_shard: bad argument");
     *out = nullptr;
@@ -1777,6 +1794,7 @@ extern "C" cut_status cut_graph_load_shard(const char *path, int device, int ran
 }
 
 extern "C" cut_status cut_shard_generator(const cut_graph *g, const double *h, double *xi_part, cut_stream_t stream) {
+    TraceRange trace_("cut_shard_generator");
     if (!g || g->device < 0 || g->shard_world < 1 || !h || (!xi_part && g->hi[0] > g->lo[0]))
         return set_error(CUT_ERR_INVALID_ARG, "cut_shard_generator: bad argument (needs a shard handle)");
     if (g->hi[0] == g->lo[0]) return set_ok();
@@ -1788,6 +1806,7 @@ extern "C" cut_status cut_shard_generator(const cut_graph *g, const double *h, d
 
 extern "C" cut_status cut_shard_commutator(const cut_graph *g, const double *xi, int n_ops, const double *x,
                                            double *dx_part, cut_stream_t stream) {
+    TraceRange trace_("cut_shard_commutator");
     if (!g || g->device < 0 || g->shard_world < 1 || !xi || n_ops < 1 || n_ops > 64 || !x ||
         (!dx_part && g->hi[1] > g->lo[1]))
         return set_error(CUT_ERR_INVALID_ARG, "cut_shard_commutator: bad argument (needs a shard handle)");

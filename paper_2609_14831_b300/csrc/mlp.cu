@@ -23,6 +23,7 @@
 #include "alloc.h"
 #include "cut.h"
 #include "status.h"
+#include "trace.h"
 #include "tc_gemm.cuh"
 
 using bf16 = __nv_bfloat16;
@@ -732,6 +733,7 @@ cut_status cut_mlp_set_linear(cut_mlp *m, const float *J) {
 
 cut_status cut_mlp_fit_linear(cut_mlp *m, int batch, const float *x, const double *t, const float *weight,
                               cut_stream_t stream) {
+    TraceRange trace_("cut_mlp_fit_linear");
     if (!m || batch < 2 || !x || !t) return set_error(CUT_ERR_INVALID_ARG, "cut_mlp_fit_linear: bad argument");
     if (m->n_in + 1 > mlpk::kFitP) return set_error(CUT_ERR_UNSUPPORTED, "cut_mlp_fit_linear: more than 63 inputs");
     if (weight)
@@ -849,6 +851,7 @@ cut_status cut_mlp_set_params(cut_mlp *m, const float *host) {
 }
 
 cut_status cut_mlp_forward(cut_mlp *m, int batch, const float *x, float *y, cut_stream_t stream) {
+    TraceRange trace_("cut_mlp_forward");
     if (!m || batch < 1 || !x || !y) return set_error(CUT_ERR_INVALID_ARG, "cut_mlp_forward: bad argument");
     cudaSetDevice(m->device);
     cudaStream_t s = (cudaStream_t)stream;
@@ -922,6 +925,7 @@ static cut_status backward_body(cut_mlp *m, int batch, const float *x, const flo
 extern "C" {
 cut_status cut_mlp_backward(cut_mlp *m, int batch, const float *x, const float *target, float *loss,
                             cut_stream_t stream) {
+    TraceRange trace_("cut_mlp_backward");
     if (!m || batch < 1 || !x || !target) return set_error(CUT_ERR_INVALID_ARG, "cut_mlp_backward: bad argument");
     cudaSetDevice(m->device);
     cudaStream_t s = (cudaStream_t)stream;
@@ -963,6 +967,7 @@ cut_status cut_mlp_backward(cut_mlp *m, int batch, const float *x, const float *
 
 cut_status cut_mlp_adamw_step(cut_mlp *m, float lr, float beta1, float beta2, float eps, float weight_decay,
                               cut_stream_t stream) {
+    TraceRange trace_("cut_mlp_adamw_step");
     if (!m || !(lr >= 0) || !(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1) || !(eps > 0))
         return set_error(CUT_ERR_INVALID_ARG, "cut_mlp_adamw_step: bad hyper-parameters");
     cudaSetDevice(m->device);
