@@ -257,3 +257,40 @@ def test_diagnostics_leave_the_retained_records_unchanged(tmp_path):
         rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
         return {(int(r), int(gl[x]), int(y)): int(num[z]) for r, x, y, z in zip(rows, a, b, c)}
     assert by_label(G0, g0) == by_label(G1, g1)
+
+
+def test_reload_range_checks_every_record_index(tmp_path):
+    """A bundle whose checksum matches but one of whose records points past
+    the registry is refused (FORMAT) before anything reaches the GPU: the
+    kernels index with the stored values unchecked, so the reload checks
+    every input index and factor code once.  Layout: 160-byte header (SHA-256
+    of the payload at byte 72), then the sections labels, generator labels,
+    diagonal mask, factor numerators and denominators, generator row
+    pointers and records, commutator row pointers and records, ... each
+    padded to 64 bytes."""
+    import hashlib
+    import struct
+    labels = fermion_registry(4)
+    p = str(tmp_path / "g.cutg")
+    cg.build_graph(ALG_FERMION, 4, labels, p)
+    blob = bytearray(open(p, "rb").read())
+    n, n_g, R0, R1 = struct.unpack_from("<4Q", blob, 24)
+    n_codes = struct.unpack_from("<I", blob, 56)[0]
+    pad = lambda b: (b + 63) // 64 * 64
+    sizes = [8 * n, 8 * n_g, n, 4 * n_codes, 4 * n_codes, 8 * (n_g + 1), 8 * R0, 8 * (n + 1)]
+    rec1 = 160 + sum(pad(b) for b in sizes)
+    for field, value in ((4, n), (0, n_g)):          # second input past n; first input past n_g
+        bad = bytearray(blob)
+        w = struct.unpack_from("<I", bad, rec1 + field)[0]
+        new = value if field == 4 else (w & ~0xFFFFFF) | value
+        struct.pack_into("<I", bad, rec1 + field, new)
+        bad[72:104] = hashlib.sha256(bytes(bad[160:])).digest()
+        q = str(tmp_path / f"range{field}.cutg")
+        open(q, "wb").write(bad)
+        with pytest.raises(cg.CutError) as e:
+            cg.Graph(q, device=-1)
+        assert e.value.name == "FORMAT" and "out of range" in str(e.value)
+    # the unmodified bytes, re-signed the same way, still load
+    ok = bytearray(blob)
+    ok[72:104] = hashlib.sha256(bytes(ok[160:])).digest()
+    assert ok == blob
