@@ -41,6 +41,10 @@
  *     no new device memory; the reserve is released when the process ends
  *     (or the device's context is destroyed).  Allocations beyond what the
  *     device can give fail with CUT_ERR_OUT_OF_MEMORY.
+ *   - Phases (compile, reload, each traversal or flow) are marked as NVTX
+ *     ranges named after the entry point ("cut_flow", "cut_graph_load/upload",
+ *     ...).  With the environment variable CUT_LOG=1 each also writes one
+ *     line "[cut] <name> <ms> ms" to stderr when it ends.
  *   - No entry point throws; each returns a cut_status and, on failure,
  *     leaves a message for cut_last_error() (thread-local).  Arguments are
  *     validated before anything is queued: on CUT_ERR_INVALID_ARG nothing

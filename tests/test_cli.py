@@ -55,3 +55,17 @@ def test_info_refuses_a_damaged_bundle(tmp_path):
     r = _run("info", out)
     assert r.returncode == 1
     assert "CHECKSUM" in r.stderr or "FORMAT" in r.stderr
+
+
+def test_cut_log_reports_the_phases_only_when_asked(tmp_path):
+    out = str(tmp_path / "p4.cutg")
+    env = dict(os.environ, CUT_LOG="1")
+    r = subprocess.run([sys.executable, "-m", "paper_2609_14831_b300", "build", "--workload", "closed_pauli_4q",
+                        "--out", out], cwd=ROOT, capture_output=True, text=True, timeout=600, env=env)
+    assert r.returncode == 0, r.stderr
+    names = [l.split()[1] for l in r.stderr.splitlines() if l.startswith("[cut] ")]
+    assert names == ["cut_build/count", "cut_build/write", "cut_build/store", "cut_build"]
+    env.pop("CUT_LOG")
+    r = subprocess.run([sys.executable, "-m", "paper_2609_14831_b300", "info", out], cwd=ROOT,
+                       capture_output=True, text=True, timeout=600, env=env)
+    assert r.returncode == 0 and "[cut]" not in r.stderr
