@@ -408,11 +408,19 @@ cut_status cut_flow_vjp(const cut_graph *g, const double *h0, int n_obs, const d
  * and, when opts->batch_record_steps is set, each instance's accepted step
  * sizes (so that a reference can replay that instance's path).
  * host in: opts (replay_steps and the host record_steps are ignored).  `tile` chooses the instance
- * tile width (0 = autotuned).  Synchronises `stream` before returning.
+ * tile width (0 = autotuned: a short probe of every width that fits, the
+ * choice remembered per graph, batch, operands, precision, method and GPU;
+ * with the environment variable CUT_TUNE_CACHE naming a file, choices are
+ * read from it and new ones appended, one line each: "<graph SHA-256 hex>
+ * <batch> <operands> <fp32 0|1> <method> <tile> <GPU name>").
+ * Synchronises `stream` before returning.
  * Errors: INVALID_ARG, CUDA, OUT_OF_MEMORY. */
 cut_status cut_flow_batched(const cut_graph *g, int batch, double *h, int n_obs, double *x,
                             int precision, const cut_flow_opts *opts, int tile, int *steps_out,
                             int *status_out, cut_stream_t stream);
+/* Tile width the calling thread's last cut_flow_batched call ran with (0 if
+ * none). */
+int cut_flow_batched_last_tile(void);
 
 /* ------------------------------------------------------------------ */
 /* Measured roofs                                                       */

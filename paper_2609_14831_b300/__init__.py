@@ -109,6 +109,7 @@ def lib():
         "cut_shard_commutator": (st, [VP, VP, i, VP, VP, VP]),
         "cut_combine": (st, [i64, VP, i, VP, VP, ctypes.c_double, VP, VP]),
         "cut_measure_fma_rate": (st, [i, i, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
+        "cut_flow_batched_last_tile": (i, []),
         "cut_mlp_create": (st, [i, i, i, ctypes.c_uint64, i, ctypes.POINTER(VP)]),
         "cut_mlp_free": (st, [VP]),
         "cut_mlp_set_output_affine": (st, [VP, VP, VP]),
@@ -403,6 +404,11 @@ class Graph:
         check(lib().cut_flow_batched(self._h, B, _ptr(H), n_obs, _ptr(X), prec, ctypes.byref(o),
                                      int(tile), _ptr(steps), _ptr(status), _stream(stream)))
         return (H, X, steps, status) if rec is None else (H, X, steps, status, rec)
+
+    @staticmethod
+    def last_batched_tile():
+        """Tile width this thread's last flow_batched call ran with (0: none)."""
+        return int(lib().cut_flow_batched_last_tile())
 
 
 def ensemble_stats(preds, mask, stream=None):

@@ -15,9 +15,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <cmath>
 #include <map>
+#include <set>
 #include <mutex>
 #include <string>
 #include <tuple>
@@ -659,10 +662,65 @@ static kb::Tableau make_tableau(int method) {
     return t;
 }
 
-// Tile width chosen per (graph, batch, operands, precision, method) by timing
-// a two-attempt probe of every width that fits in shared memory.
+// Tile width chosen per (graph, batch, operands, precision, method, GPU) by
+// timing a two-attempt probe of every width that fits in shared memory.
+// With CUT_TUNE_CACHE=<file> in the environment the choices persist: the
+// file is read once per process (lines "<graph SHA-256, hex> <batch>
+// <operands> <fp32 0|1> <method> <tile> <GPU name>"; lines that do not parse
+// are skipped) and every new choice is appended, so a later process skips
+// the probes.
+using TuneKey = std::tuple<std::string, int, int, int, int, std::string>;
 static std::mutex g_tune_mu;
-static std::map<std::tuple<std::string, int, int, int, int>, int> g_tune;
+static std::map<TuneKey, int> g_tune;
+static std::set<std::string> g_tune_read;   // cache files already read
+
+static std::string hex_of(const std::string &raw) {
+    static const char *d = "0123456789abcdef";
+    std::string h;
+    for (unsigned char c : raw) { h += d[c >> 4]; h += d[c & 15]; }
+    return h;
+}
+
+static std::string gpu_name(int device) {
+    cudaDeviceProp p;
+    if (cudaGetDeviceProperties(&p, device) != cudaSuccess) { (void)cudaGetLastError(); return "unknown"; }
+    return p.name;
+}
+
+// caller holds g_tune_mu
+static void read_tune_file(const std::string &path) {
+    if (path.empty() || !g_tune_read.insert(path).second) return;
+    FILE *f = fopen(path.c_str(), "r");
+    if (!f) return;
+    char line[512];
+    while (fgets(line, sizeof line, f)) {
+        char sha[80];
+        int batch, nops, fp32, method, tile, used = 0;
+        if (sscanf(line, "%70s %d %d %d %d %d %n", sha, &batch, &nops, &fp32, &method, &tile, &used) != 6) continue;
+        if (strlen(sha) != 64 || batch < 1 || nops < 1 || (fp32 != 0 && fp32 != 1)) continue;
+        if (tile != 2 && tile != 4 && tile != 8 && tile != 16 && tile != 32) continue;
+        std::string raw;
+        bool ok = true;
+        for (int i = 0; i < 64 && ok; i += 2) {
+            unsigned v;
+            ok = sscanf(sha + i, "%2x", &v) == 1;
+            raw += (char)v;
+        }
+        std::string name(line + used);
+        while (!name.empty() && (name.back() == '\n' || name.back() == '\r')) name.pop_back();
+        if (ok && !name.empty()) g_tune[TuneKey(raw, batch, nops, fp32, method, name)] = tile;
+    }
+    fclose(f);
+}
+
+static void append_tune_file(const std::string &path, const TuneKey &k, int tile) {
+    if (path.empty()) return;
+    FILE *f = fopen(path.c_str(), "a");
+    if (!f) return;
+    fprintf(f, "%s %d %d %d %d %d %s\n", hex_of(std::get<0>(k)).c_str(), std::get<1>(k), std::get<2>(k),
+            std::get<3>(k), std::get<4>(k), tile, std::get<5>(k).c_str());
+    fclose(f);
+}
 
 cut_status flow_batched_impl(const BatchedGraphView &v, int device, int batch, double *h, int n_obs, double *x,
                              int precision, const cut_flow_opts *o, int tile, int *steps_out, int *status_out,
@@ -729,11 +787,16 @@ cut_status flow_batched_impl(const BatchedGraphView &v, int device, int batch, d
     a.status_out = status_out;
 
     if (tile == 0) {
-        auto key = std::make_tuple(std::string((const char *)v.sha, 32), batch, nops, (int)fp32, o->method);
+        const char *cache_env = getenv("CUT_TUNE_CACHE");
+        const std::string cache = cache_env ? cache_env : "";
+        const TuneKey key(std::string((const char *)v.sha, 32), batch, nops, (int)fp32, o->method, gpu_name(device));
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
+            read_tune_file(cache);
             auto it = g_tune.find(key);
-            if (it != g_tune.end()) tile = it->second;
+            // a remembered width that no longer fits is probed again
+            if (it != g_tune.end() && std::find(cands.begin(), cands.end(), it->second) != cands.end())
+                tile = it->second;
         }
         if (tile == 0) {
             // probe on scratch copies so the caller's state is untouched
@@ -774,6 +837,7 @@ cut_status flow_batched_impl(const BatchedGraphView &v, int device, int batch, d
             if (tile == 0) return finish(set_error(CUT_ERR_CUDA, "cut_flow_batched: no tile width ran"));
             std::lock_guard<std::mutex> lk(g_tune_mu);
             g_tune[key] = tile;
+            append_tune_file(cache, key, tile);
         }
     }
     if (chosen_tile) *chosen_tile = tile;

@@ -1633,6 +1633,8 @@ extern "C" cut_status cut_flow_batched(const cut_graph *g, int batch, double *h,
                              (cudaStream_t)stream, &g_last_tile);
 }
 
+extern "C" int cut_flow_batched_last_tile(void) { return g_last_tile; }
+
 // ----------------------------------------------------------------- no-alloc RHS
 // A right-hand side for callers that must not allocate device memory: the
 // generator scratch lives in a fixed array inside the library's device image.

@@ -5,6 +5,8 @@ RTOL = 1e-10.  FP64 batched DP45 takes each instance's own adaptive path and
 is compared with the single-instance GPU flow (same controller) and its step
 count.  The FP32-record path is compared with FP64 and its error reported.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -265,3 +267,40 @@ def test_batched_full_size_dp45_matches_oracle_replay():
     print(f"FP32-record batch vs oracle-checked FP64 batch, per instance (1024): median {np.median(err):.2e}, "
           f"p99 {np.percentile(err, 99):.2e}, max {err.max():.2e}")
     assert err.max() < 1e-4
+
+
+def test_tile_choices_persist_in_the_tune_cache_file(tmp_path):
+    """CUT_TUNE_CACHE: the autotuner appends its choice (graph SHA-256,
+    batch, operands, precision, method, tile, GPU name) and a later lookup
+    takes a remembered width from a file instead of probing.  Every width
+    sums each instance in record order, so the width changes no bits."""
+    import torch
+    w = workload("molecular_4so")
+    G = graph_for("mol4_workload", w.alg, w.nmodes, w.labels)
+    B = 29                                  # a batch size no other test tunes
+    H = torch.tensor(batched_parameters(w.labels, 4, B, seed=77))
+    X = torch.tensor(np.stack([np.stack(w.observables)] * B))
+    first = tmp_path / "tune1.txt"
+    os.environ["CUT_TUNE_CACHE"] = str(first)
+    try:
+        Ha, Xa, sa, sta = G.flow_batched(H, X, precision="fp64", method="dp45", s0=0.0, s1=0.5, ds=1e-2,
+                                         rtol=1e-8, atol=1e-12)
+        tuned = G.last_batched_tile()
+        lines = first.read_text().splitlines()
+        assert len(lines) == 1
+        sha, batch, nops, fp32, method, tile, *name = lines[0].split()
+        assert (int(batch), int(nops), int(fp32), int(tile)) == (B, 1 + len(w.observables), 0, tuned)
+        assert len(sha) == 64 and name
+        # a second file remembers another width for the same key
+        other = 4 if tuned != 4 else 2
+        second = tmp_path / "tune2.txt"
+        second.write_text(" ".join([sha, batch, nops, fp32, method, str(other)] + name) + "\n")
+        os.environ["CUT_TUNE_CACHE"] = str(second)
+        Hb, Xb, sb, stb = G.flow_batched(H, X, precision="fp64", method="dp45", s0=0.0, s1=0.5, ds=1e-2,
+                                         rtol=1e-8, atol=1e-12)
+        assert G.last_batched_tile() == other
+        assert second.read_text().count("\n") == 1      # nothing probed, nothing appended
+        np.testing.assert_array_equal(np64(Hb), np64(Ha))
+        np.testing.assert_array_equal(np64(sb), np64(sa))
+    finally:
+        os.environ.pop("CUT_TUNE_CACHE", None)
