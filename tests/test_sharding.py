@@ -201,3 +201,23 @@ def test_a_rank_that_leaves_is_detected_by_the_others(bundle, tmp_path):
     print(res)
     assert res.startswith("error after")
     assert float(res.split()[2]) < 60
+
+
+def test_three_gloo_ranks_with_uneven_pieces_reproduce_the_single_rank_flow(bundle, tmp_path):
+    """Three ranks: the record-balanced row ranges have different lengths, so
+    the all-gather pads them to the longest and each rank must cut its
+    neighbours' pieces back out in rank order.  Same bits as one rank."""
+    dy1, y1, _ = _run(bundle, 0, 1, lambda t: t.clone())
+    lens = [np.diff(NumpyShard(bundle, 0, 3).comm_bounds)]
+    assert len(set(lens[0].tolist())) > 1                 # the pieces differ in length
+    ctx = mp.get_context("spawn")
+    port = 29700 + os.getpid() % 1000
+    procs = [ctx.Process(target=_worker, args=(r, 3, port, bundle, str(tmp_path))) for r in range(3)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(300)
+        assert p.exitcode == 0
+    for r in range(3):
+        np.testing.assert_array_equal(np.load(tmp_path / f"dy{r}.npy"), dy1)
+        np.testing.assert_array_equal(np.load(tmp_path / f"y{r}.npy"), y1)
